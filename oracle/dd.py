@@ -1,0 +1,159 @@
+"""Overlapping subdomains, coarse space and the additive Schwarz preconditioner.
+
+Oracle (test infrastructure only).
+
+Paper:
+  * Sec. 3.1, Eq. 3.1: local spaces with zero tangential trace on the subdomain
+    boundary; I^h(Omega_l) = DOFs whose edge lies in Omega_l; R^l selects them.
+  * Sec. 3.2, Eq. 3.2: coarse restriction (R^0)_pj = psi_j^h(w_p^H).
+  * Sec. 3.3, Eq. 3.3: A^l = R^l A (R^l)^T (minors for l >= 1; coarse Galerkin
+    matrix for l = 0); Eq. 3.4: B^{-1} = sum_{l=0}^N (R^l)^T (A^l)^{-1} R^l.
+    The one-level variant omits l = 0 (Sec. 6.2).
+  * Sec. 6.1: overlapping subdomains are grown from a non-overlapping partition.
+
+Readings:
+  * subdomains are cube-aligned boxes: core boxes of `core` cells per axis
+    (box i covers cells [core*i, min(core*(i+1), n))), each widened by `overlap`
+    cells on every side and clipped to the unit cube. Local DOFs are the
+    interior edges with both ends in the box and not lying on a box face
+    (PEC on the subdomain boundary, Eq. 3.1). Subdomain id l = ix + N (iy + N iz).
+  * coarse mesh: a Kuhn mesh with m cells per side, m dividing n, so it is nested
+    in the fine mesh. psi_j(w) = int_{e_j} w . tau ds; w_p^H is linear on the coarse
+    tetrahedron holding e_j, so the midpoint rule is exact:
+    (R^0)_pj = w_p^H(midpoint_j) . (x_high - x_low).
+  * local and coarse solves: sparse LU with partial pivoting (scipy SuperLU),
+    like the paper's MUMPS direct solves (Sec. 6.1).
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .mesh import KuhnMesh, vertex_ijk, DIRS, LOCAL_EDGES
+from . import fem
+
+
+def subdomain_boxes(n, core, overlap):
+    """List of vertex-index boxes (lo[3], hi[3]) in subdomain order."""
+    N = -(-n // core)
+    spans = []
+    for i in range(N):
+        lo = max(core * i - overlap, 0)
+        hi = min(min(core * (i + 1), n) + overlap, n)
+        spans.append((lo, hi))
+    boxes = []
+    for iz in range(N):
+        for iy in range(N):
+            for ix in range(N):
+                boxes.append((np.array([spans[ix][0], spans[iy][0], spans[iz][0]]),
+                              np.array([spans[ix][1], spans[iy][1], spans[iz][1]])))
+    return boxes
+
+
+def local_dofs(mesh, lo, hi):
+    """Sorted global DOFs of the box [lo, hi] (vertex indices), Eq. 3.1 reading."""
+    a = vertex_ijk(mesh.dof_edges[:, 0], mesh.n)
+    b = vertex_ijk(mesh.dof_edges[:, 1], mesh.n)
+    inside = np.all((a >= lo) & (a <= hi) & (b >= lo) & (b <= hi), axis=1)
+    on_face = np.zeros_like(inside)
+    for ax in range(3):
+        for val in (lo[ax], hi[ax]):
+            on_face |= (a[:, ax] == val) & (b[:, ax] == val)
+    return np.nonzero(inside & ~on_face)[0]
+
+
+def restriction(idx, n_dof):
+    """R^l as a sparse 0/1 matrix (Eq. 3.1)."""
+    return sp.csr_matrix((np.ones(len(idx)), (np.arange(len(idx)), idx)),
+                         shape=(len(idx), n_dof))
+
+
+def coarse_restriction(fine: KuhnMesh, coarse: KuhnMesh):
+    """R^0 [n_c, n] of Eq. 3.2 on nested Kuhn meshes (midpoint rule, exact)."""
+    n, m = fine.n, coarse.n
+    assert n % m == 0, "coarse mesh must be nested (m divides n)"
+    H = 1.0 / m
+    xa = fine.coords(fine.dof_edges[:, 0])
+    xb = fine.coords(fine.dof_edges[:, 1])
+    mid = 0.5 * (xa + xb)
+    t = xb - xa
+    s = mid / H
+    cube = np.clip(np.floor(s).astype(np.int64), 0, m - 1)
+    loc = s - cube
+    # Kuhn simplex of the coarse cube holding the midpoint: local coordinates in
+    # decreasing order give its vertex path (ties: any containing simplex).
+    perm = np.argsort(-loc, axis=1, kind="stable")
+    eye = np.eye(3, dtype=np.int64)
+    path = [cube]
+    for k in range(3):
+        path.append(path[-1] + eye[perm[:, k]])
+    path = np.stack(path, axis=1)  # [n, 4, 3] coarse grid indices
+    P = path * H
+    G, _ = fem.bary_gradients(P)  # [n, 4, 3]
+    Mx = np.ones((fine.n_dof, 4, 4))
+    Mx[:, :, 1:] = P
+    rhs = np.concatenate([np.ones((fine.n_dof, 1)), mid], axis=1)
+    lam = np.linalg.solve(np.transpose(Mx, (0, 2, 1)), rhs[:, :, None])[:, :, 0]
+    vid = path[:, :, 0] + (m + 1) * (path[:, :, 1] + (m + 1) * path[:, :, 2])
+    lut = np.full(7 * (m + 1) ** 3, -1, dtype=np.int64)
+    lut[coarse.dof_key] = np.arange(coarse.n_dof)
+    rows, cols, vals = [], [], []
+    for (p, q) in LOCAL_EDGES:
+        lo, hi = vid[:, p], vid[:, q]
+        dvec = vertex_ijk(hi, m) - vertex_ijk(lo, m)
+        dirs = np.full(fine.n_dof, -1, dtype=np.int64)
+        for k, dv in enumerate(DIRS):
+            dirs[np.all(dvec == dv, axis=1)] = k
+        assert np.all(dirs >= 0)
+        dof = lut[7 * lo + dirs]
+        w = lam[:, p, None] * G[:, q] - lam[:, q, None] * G[:, p]
+        val = np.einsum("ji,ji->j", w, t)
+        keep = (dof >= 0) & (val != 0.0)
+        rows.append(dof[keep])
+        cols.append(np.nonzero(keep)[0])
+        vals.append(val[keep])
+    R0 = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                       shape=(coarse.n_dof, fine.n_dof)).tocsr()
+    R0.sum_duplicates()
+    return R0
+
+
+class Schwarz:
+    """One- or two-level additive Schwarz preconditioner of Eq. 3.4."""
+
+    def __init__(self, mesh, A_prec, core, overlap, coarse_m=0, k=None, xi_prec=None):
+        self.mesh = mesh
+        self.boxes = subdomain_boxes(mesh.n, core, overlap)
+        self.idx = [local_dofs(mesh, lo, hi) for lo, hi in self.boxes]
+        self.A_prec = A_prec.tocsr()
+        self.lus = None
+        self.coarse = None
+        if coarse_m:
+            cm = KuhnMesh(coarse_m)
+            Kc, Mc = fem.assemble_KM(cm)
+            self.coarse_mesh = cm
+            self.R0 = coarse_restriction(mesh, cm)
+            self.A0 = fem.a_xi(Kc, Mc, k, xi_prec)  # Galerkin matrix on Q_H (Eq. 3.3, l = 0)
+
+    def minor(self, l):
+        """A^l = R^l A (R^l)^T (Eq. 3.3) as a sparse matrix."""
+        i = self.idx[l]
+        return self.A_prec[i][:, i]
+
+    def factor(self, subset=None):
+        ls = range(len(self.idx)) if subset is None else subset
+        self.lus = {l: spla.splu(self.minor(l).tocsc()) for l in ls}
+        if hasattr(self, "A0"):
+            self.coarse = spla.splu(self.A0.tocsc())
+
+    def local_solve(self, l, r_l):
+        return self.lus[l].solve(r_l)
+
+    def apply(self, v, levels=(1, 0)):
+        """z = sum_l (R^l)^T (A^l)^{-1} R^l v (Eq. 3.4). v [n] or [n, R]."""
+        z = np.zeros_like(v, dtype=np.complex128)
+        if 1 in levels:
+            for l, i in enumerate(self.idx):
+                z[i] += self.local_solve(l, v[i])
+        if 0 in levels and self.coarse is not None:
+            z += self.R0.T @ self.coarse.solve(self.R0 @ v)
+        return z

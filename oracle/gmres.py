@@ -1,0 +1,93 @@
+"""Right-preconditioned restarted GMRES (modified Gram-Schmidt, Givens rotations).
+
+Oracle (test infrastructure only).
+
+Paper: Sec. 6.1 -- the right-preconditioned system A B^{-1} u = b, x = B^{-1} u,
+is solved by GMRES; stopping on a relative residual reduction; at most 200
+iterations. Sec. 5.2 recalls GMRES as the minimal-residual Krylov method.
+
+Readings:
+  * initial guess x0 = 0 (the paper uses a random x0), so the relative residual
+    is ||b - A x|| / ||b|| in the Euclidean norm (right preconditioning leaves the
+    residual unpreconditioned);
+  * restart length m (0 = unrestarted); at a restart x is formed and the true
+    residual b - A x is recomputed;
+  * Arnoldi by modified Gram-Schmidt; the small least-squares problem by complex
+    Givens rotations (Saad, Iterative Methods, Alg. 6.9 and Prop. 6.9).
+"""
+import numpy as np
+
+
+def givens(a, b):
+    """Complex rotation (c real, s complex) with [c s; -conj(s) c] [a; b] = [r; 0]."""
+    if b == 0:
+        return 1.0, 0.0 + 0.0j
+    if a == 0:
+        return 0.0, np.conj(b) / abs(b)
+    t = np.hypot(abs(a), abs(b))
+    c = abs(a) / t
+    s = (a / abs(a)) * np.conj(b) / t
+    return c, s
+
+
+def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=None):
+    """Solve A x = b with right preconditioner B^{-1}.
+
+    matvec(v) = A v, precond(v) = B^{-1} v for 1-D complex vectors.
+    Returns (x, iterations, final relative true residual, converged)."""
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros(n, dtype=np.complex128), 0, 0.0, True
+    m = restart if restart > 0 else max_it
+    its = 0
+    r = b - matvec(x) if np.any(x) else b.copy()
+    beta = np.linalg.norm(r)
+    if beta / bnorm <= tol:
+        return x, 0, beta / bnorm, True
+    while True:
+        V = np.zeros((m + 1, n), dtype=np.complex128)
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta
+        V[0] = r / beta
+        j_done = 0
+        converged = False
+        for j in range(m):
+            w = matvec(precond(V[j]))
+            for i in range(j + 1):  # modified Gram-Schmidt
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] != 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):  # previous rotations on the new column
+                hi, hi1 = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * hi + sn[i] * hi1
+                H[i + 1, j] = -np.conj(sn[i]) * hi + cs[i] * hi1
+            cs[j], sn[j] = givens(H[j, j], H[j + 1, j])
+            H[j, j] = cs[j] * H[j, j] + sn[j] * H[j + 1, j]
+            H[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(sn[j]) * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            j_done = j + 1
+            if history is not None:
+                history.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) / bnorm <= tol or its >= max_it:
+                converged = abs(g[j + 1]) / bnorm <= tol
+                break
+        k = j_done
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])  # upper-triangular back substitution
+        x = x + precond(V[:k].T @ y)
+        r = b - matvec(x)
+        beta = np.linalg.norm(r)
+        rel = beta / bnorm
+        if rel <= tol:
+            return x, its, rel, True
+        if its >= max_it:
+            return x, its, rel, False

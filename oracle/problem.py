@@ -1,0 +1,50 @@
+"""build / factor / solve on the CPU, mirroring the library's three calls.
+
+Oracle (test infrastructure only). Composes mesh, fem, dd and gmres; see their
+docstrings for the passages of the paper each step follows.
+"""
+import numpy as np
+
+from .mesh import KuhnMesh
+from . import fem, dd, gmres as _gmres
+
+
+class Problem:
+    """curl curl E - (k^2 + i xi_prob) E = F, PEC, preconditioned by AS built from
+    A_{xi_prec} (Sec. 6.2: B^{-1}_{xi_prec} preconditions A_{xi_prob})."""
+
+    def __init__(self, n, k, xi_prob, xi_prec, core, overlap, coarse_m=0):
+        self.mesh = KuhnMesh(n)
+        self.k, self.xi_prob, self.xi_prec = k, xi_prob, xi_prec
+        self.K, self.M = fem.assemble_KM(self.mesh)
+        self.A = fem.a_xi(self.K, self.M, k, xi_prob)
+        self.A_prec = fem.a_xi(self.K, self.M, k, xi_prec)
+        self.dd = dd.Schwarz(self.mesh, self.A_prec, core, overlap, coarse_m, k, xi_prec)
+
+    @property
+    def n_dof(self):
+        return self.mesh.n_dof
+
+    def factor(self, subset=None):
+        self.dd.factor(subset)
+
+    def load_vector(self, centres, pol, width, q=3):
+        """f for bump parameters centres [R, B, 3], pol [R, B, 3]; returns [n, R]."""
+        return fem.load_vector(self.mesh, fem.bump_field(centres, pol, width), q)
+
+    def solve(self, rhs, tol=1e-6, restart=0, max_it=200, history=None):
+        """rhs [n] or [n, R]; each column solved independently."""
+        rhs = np.asarray(rhs, dtype=np.complex128)
+        single = rhs.ndim == 1
+        B = rhs[:, None] if single else rhs
+        xs, stats = [], []
+        for r in range(B.shape[1]):
+            hist = [] if history is not None else None
+            x, its, rel, ok = _gmres.gmres(lambda v: self.A @ v, self.dd.apply, B[:, r],
+                                           tol, restart, max_it, history=hist)
+            if history is not None:
+                history.append(hist)
+            xs.append(x)
+            stats.append((its, rel, ok))
+        X = np.stack(xs, axis=1)
+        return (X[:, 0] if single else X), stats

@@ -1,0 +1,161 @@
+"""Pins for oracle.dd: local DOF counts (closed form), the cover property, minors equal
+the Galerkin matrix of the box with PEC on its boundary (Eq. 3.3 remark), coarse
+interpolation commutes with gradients and gives the coarse Galerkin matrix, R^0 = I when
+the meshes coincide, idempotent local projections (Lemma 5.1), and B^{-1} = A^{-1} for a
+single subdomain."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.mesh import KuhnMesh, count_interior_edges, vertex_ijk
+from oracle import fem, dd
+
+
+@pytest.mark.parametrize("n,core,overlap", [(10, 5, 1), (12, 5, 1), (9, 4, 2), (6, 3, 0)])
+def test_local_counts_and_cover(n, core, overlap):
+    m = KuhnMesh(n)
+    boxes = dd.subdomain_boxes(n, core, overlap)
+    assert len(boxes) == (-(-n // core)) ** 3
+    cover = np.zeros(m.n_dof, dtype=int)
+    for lo, hi in boxes:
+        idx = dd.local_dofs(m, lo, hi)
+        a, b, c = (hi - lo).tolist()
+        assert len(idx) == count_interior_edges(a, b, c)
+        assert np.all(np.diff(idx) > 0)
+        cover[idx] += 1
+    if overlap > 0:
+        assert cover.min() >= 1  # I^h = union of I^h(Omega_l) (Sec. 3.1)
+    assert cover.max() <= 8
+
+
+def test_subdomain_sizes_40():
+    # 8 x 8 x 8 boxes of 5^3 cells + 1-cell overlap on 40^3 cells: boxes of 6 or 7 cells
+    boxes = dd.subdomain_boxes(40, 5, 1)
+    sizes = [count_interior_edges(*(hi - lo).tolist()) for lo, hi in boxes]
+    assert len(boxes) == 512 and max(sizes) == 1981 and min(sizes) == 1206
+    assert sum(sizes) == 902664
+
+
+def _box_matrix(a, h, k, xi):
+    """Galerkin matrix of an a^3 Kuhn box of cell size h with PEC on its boundary."""
+    mb = KuhnMesh(a)
+    K, M = fem.assemble_KM(mb)
+    s = mb.h / h  # K scales like 1/h, M like h
+    return fem.a_xi(K * s, M / s, k, xi)
+
+
+@pytest.mark.parametrize("l", [0, 13, 26])
+def test_minor_is_box_galerkin_matrix(l):
+    """A^l = R^l A (R^l)^T is the Galerkin matrix of the problem on Omega_l with PEC
+    on its boundary (Eq. 3.3 and the remark after it)."""
+    n, k, xi = 15, 3.0, 2.0
+    m = KuhnMesh(n)
+    K, M = fem.assemble_KM(m)
+    A = fem.a_xi(K, M, k, xi)
+    S = dd.Schwarz(m, A, 5, 1)
+    lo, hi = S.boxes[l]
+    a = (hi - lo)
+    if not np.all(a == a[0]):
+        pytest.skip("non-cubic box")
+    Ab = _box_matrix(int(a[0]), m.h, k, xi)
+    Al = S.minor(l)
+    assert abs(Al - Ab).max() < 1e-12 * abs(Ab).max()
+
+
+def _nodal_prolongation(fine, coarse, phi_c):
+    """Values at fine vertices of the coarse P1 function phi_c (barycentric interpolation
+    in the coarse Kuhn simplex holding each fine vertex)."""
+    m = coarse.n
+    H = 1.0 / m
+    x = fine.coords(np.arange((fine.n + 1) ** 3))
+    s = x / H
+    cube = np.clip(np.floor(s + 1e-12).astype(int), 0, m - 1)
+    loc = s - cube
+    out = np.empty(x.shape[0])
+    for i in range(x.shape[0]):
+        perm = np.argsort(-loc[i], kind="stable")
+        lam = [1 - loc[i][perm[0]], loc[i][perm[0]] - loc[i][perm[1]],
+               loc[i][perm[1]] - loc[i][perm[2]], loc[i][perm[2]]]
+        v = cube[i].copy()
+        vals = [phi_c[v[0] + (m + 1) * (v[1] + (m + 1) * v[2])]]
+        for ax in perm:
+            v[ax] += 1
+            vals.append(phi_c[v[0] + (m + 1) * (v[1] + (m + 1) * v[2])])
+        out[i] = np.dot(lam, vals)
+    return out
+
+
+@pytest.mark.parametrize("n,m", [(4, 2), (6, 2), (6, 3)])
+def test_coarse_commutes_with_gradient(n, m):
+    """(R^0)^T G_c phi = G_f P phi: the coarse gradient interpolates exactly."""
+    fine, coarse = KuhnMesh(n), KuhnMesh(m)
+    R0 = dd.coarse_restriction(fine, coarse)
+    rng = np.random.default_rng(1)
+    phi = rng.standard_normal((m + 1) ** 3) * fem.interior_vertices(coarse)
+    lhs = R0.T @ (fem.discrete_gradient(coarse) @ phi)
+    rhs = fem.discrete_gradient(fine) @ _nodal_prolongation(fine, coarse, phi)
+    assert np.abs(lhs - rhs).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,m", [(4, 2), (6, 3), (8, 2)])
+def test_coarse_galerkin(n, m):
+    """R^0 A_h (R^0)^T equals the matrix assembled on the coarse mesh (nested spaces)."""
+    fine, coarse = KuhnMesh(n), KuhnMesh(m)
+    R0 = dd.coarse_restriction(fine, coarse)
+    Kf, Mf = fem.assemble_KM(fine)
+    Kc, Mc = fem.assemble_KM(coarse)
+    Af, Ac = fem.a_xi(Kf, Mf, 2.0, 1.0), fem.a_xi(Kc, Mc, 2.0, 1.0)
+    G = R0 @ Af @ R0.T
+    assert abs(G - Ac).max() < 1e-12 * abs(Ac).max()
+
+
+def test_coarse_identity():
+    m = KuhnMesh(3)
+    R0 = dd.coarse_restriction(m, KuhnMesh(3))
+    assert abs(R0 - sp.identity(m.n_dof)).max() < 1e-14
+
+
+def test_local_projection_idempotent():
+    """P_l = (R^l)^T (A^l)^{-1} R^l A is a projection when xi_prob = xi_prec (Lemma 5.1)."""
+    n = 10
+    m = KuhnMesh(n)
+    K, M = fem.assemble_KM(m)
+    A = fem.a_xi(K, M, 4.0, 4.0)
+    S = dd.Schwarz(m, A, 5, 1)
+    S.factor()
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal(m.n_dof) + 1j * rng.standard_normal(m.n_dof)
+    for l in (0, 5):
+        i = S.idx[l]
+
+        def P(u):
+            z = np.zeros_like(u)
+            z[i] = S.local_solve(l, (A @ u)[i])
+            return z
+        p1 = P(v)
+        assert np.abs(P(p1) - p1).max() < 1e-10 * np.abs(p1).max()
+
+
+def test_single_subdomain_is_exact_inverse():
+    m = KuhnMesh(4)
+    K, M = fem.assemble_KM(m)
+    A = fem.a_xi(K, M, 3.0, 3.0)
+    S = dd.Schwarz(m, A, 4, 0)
+    assert len(S.idx) == 1 and len(S.idx[0]) == m.n_dof
+    S.factor()
+    x = np.arange(m.n_dof) * (1 + 0.5j)
+    assert np.abs(S.apply(A @ x) - x).max() < 1e-10 * np.abs(x).max()
+
+
+def test_as_complex_symmetric():
+    """B^{-1} is complex symmetric (sum of R^T (A^l)^{-1} R with symmetric A^l)."""
+    m = KuhnMesh(10)
+    K, M = fem.assemble_KM(m)
+    A = fem.a_xi(K, M, 5.0, 5.0)
+    S = dd.Schwarz(m, A, 5, 1, coarse_m=5, k=5.0, xi_prec=5.0)
+    S.factor()
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(m.n_dof) + 1j * rng.standard_normal(m.n_dof)
+    v = rng.standard_normal(m.n_dof) + 1j * rng.standard_normal(m.n_dof)
+    a, b = u @ S.apply(v), v @ S.apply(u)
+    assert abs(a - b) < 1e-10 * abs(a)
