@@ -1,0 +1,201 @@
+/*
+ * mxas.h -- C ABI of the GB300 additive-Schwarz / GMRES solver for the lowest-order
+ * Nedelec discretisation of  curl curl E - (k^2 + i xi) E = F  on the unit cube with
+ * PEC boundary conditions (Bonazzoli, Dolean, Graham, Spence, Tournier,
+ * arXiv:1711.03789).
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are interleaved (re, im) pairs: double2 ("c128") or float2
+ *     ("c64"). A block of right-hand sides is stored right-hand side by right-hand
+ *     side: element (i, r) of an n x nrhs block is at index r * n + i.
+ *   - Pointers to vectors may be host or device memory; the library asks the CUDA
+ *     runtime which (cudaPointerGetAttributes) and copies through the handle's stream.
+ *     Host pointers are read before the call returns; results are in place when it
+ *     returns (the call synchronises the handle's stream).
+ *   - Ownership: the library owns the handle and every device buffer it allocates;
+ *     the caller owns every pointer it passes and may free it when the call returns.
+ *   - Errors: every int-returning call returns MX_OK (0) or a negative MX_E* code and
+ *     never throws; mx_last_error() gives a message for the calling thread.
+ *   - Threads: one handle must not be used by two threads at once; different handles
+ *     are independent.
+ */
+#ifndef MXAS_H
+#define MXAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MX_API __attribute__((visibility("default")))
+#else
+#define MX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MX_OK 0
+#define MX_EINVAL (-1)        /* bad argument or descriptor */
+#define MX_ENOMEM (-2)        /* device allocation failed or over the memory budget */
+#define MX_ENOTFACTORED (-3)  /* mx_solve / mx_precond before mx_factor */
+#define MX_ESINGULAR (-4)     /* a zero or tiny pivot in a local or coarse LU */
+#define MX_ENOCONV (-5)       /* GMRES reached max_it; x and stats are still filled */
+#define MX_ETIMEOUT (-6)      /* a bounded device wait expired */
+#define MX_ECUDA (-7)         /* a CUDA runtime error; see mx_last_error() */
+
+/* Mesh: the unit cube split into n_cells^3 cubes, each cut into 6 Kuhn tetrahedra
+ * (Sec. 2.2; uniform mesh and Kuhn split are this library's reading). */
+typedef struct { int n_cells; } mx_mesh_desc;
+
+/* Overlapping subdomains (Sec. 3.1, Sec. 6.1): boxes of core_cells^3 cells widened by
+ * overlap_cells on each side, clipped to the cube. */
+typedef struct { int core_cells; int overlap_cells; } mx_dd_desc;
+
+/* Coarse space (Sec. 3.2): a Kuhn mesh of n_cells^3 cells; n_cells must divide the
+ * fine n_cells (nested meshes). n_cells = 0 gives the one-level preconditioner. */
+typedef struct { int n_cells; } mx_coarse_desc;
+
+/* Precision of the local factors and local solves. FP64 is always used for the
+ * outer residual, the Arnoldi process, Givens rotations and the coarse factorisation. */
+typedef enum { MX_PLAIN_FP64 = 0, MX_MIXED = 1 } mx_precision;
+
+typedef struct mx_problem* mx_handle;
+
+typedef struct {
+  int64_t n_dof;        /* PEC-interior edges of the fine mesh */
+  int64_t nnz;          /* nonzeros of A (CSR) */
+  int32_t n_sub;        /* number of subdomains N */
+  int32_t max_local;    /* largest subdomain size n_l */
+  int64_t sum_local;    /* sum of n_l */
+  int64_t n_coarse;     /* coarse DOFs (0 for one level) */
+  int64_t nnz_r0;       /* nonzeros of R^0 */
+  int64_t factor_bytes; /* device bytes held by local + coarse factors */
+  int32_t coarse_band;  /* half-bandwidth of the coarse matrix */
+  int32_t precision;
+} mx_problem_info;
+
+typedef struct {
+  int32_t iterations;   /* GMRES iterations (Arnoldi steps) over all restarts */
+  int32_t converged;    /* 1 when ||b - A x|| / ||b|| <= tol in FP64 */
+  double rel_residual;  /* final true relative residual ||b - A x||_2 / ||b||_2 */
+  double rel_estimate;  /* last least-squares residual estimate |g_{j+1}| / ||b|| */
+} mx_rhs_stats;
+
+typedef struct {
+  double build_ms, factor_ms, solve_ms;   /* device time of the last calls */
+  int64_t solve_launches;                 /* kernels launched by the last mx_solve */
+  int32_t restarts;
+  int32_t max_iterations;
+} mx_timing;
+
+/* Library version string. */
+MX_API const char* mx_version(void);
+
+/* Route every device allocation of the library through alloc/release (for instance a
+ * framework's caching allocator); ctx is passed back unchanged. NULL restores cudaMalloc /
+ * cudaFree. Must not be changed while a handle holds memory from the previous hooks. */
+MX_API int mx_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*release)(void* p, void* ctx),
+                     void* ctx);
+
+/* Store the local factors as full dense matrices (half-bandwidth n_l - 1) instead of the
+ * band (both give the same factors: no-pivot LU creates no fill outside the band). Takes
+ * effect at the next mx_factor. For comparison runs. */
+MX_API int mx_set_dense_local(mx_handle h, int dense);
+
+/* Message of the last error on the calling thread ("" if none). */
+MX_API const char* mx_last_error(void);
+
+/* Assemble the problem (Sec. 2.2, Eq. 2.2; Sec. 3, Eq. 3.1-3.3):
+ * Kuhn mesh and PEC-interior edge numbering, CSR K and M (real FP64) with
+ * A_xi = K - (k^2 + i xi) M, subdomain index lists, and (two-level) the coarse mesh,
+ * its Galerkin matrix A^0_{xi_prec} and the restriction R^0 of Eq. 3.2.
+ * The preconditioner uses xi_prec, the operator xi_prob (Sec. 6.2).
+ * Returns MX_EINVAL for n_cells < 1, core_cells < 1, overlap_cells < 0, k <= 0,
+ * xi_prec == 0 (local matrices are only guaranteed invertible for xi != 0, Sec. 3.3)
+ * or a coarse n_cells that does not divide the fine one. *out is set on success only. */
+MX_API int mx_build_problem(const mx_mesh_desc* mesh, double k, double xi_prob, double xi_prec,
+                     const mx_dd_desc* dd, const mx_coarse_desc* coarse, int precision,
+                     mx_handle* out);
+
+/* Change xi_prob of the operator (the factors depend on xi_prec only). */
+MX_API int mx_set_xi_prob(mx_handle h, double xi_prob);
+
+/* Run all device work of this handle on the given cudaStream_t (NULL = legacy default). */
+MX_API int mx_set_stream(mx_handle h, void* stream);
+
+/* Factor the preconditioner (Eq. 3.3-3.4): extract every local minor
+ * A^l = R^l A_{xi_prec} (R^l)^T and LU-factor all of them in one batch without
+ * pivoting (coercivity, Lemma 2.2, keeps every pivot nonzero), c64 in MX_MIXED and c128
+ * in MX_PLAIN_FP64; LU-factor the coarse matrix A^0 in FP64 (band-limited).
+ * Returns MX_ESINGULAR when a pivot modulus falls below 1e-30 times the matrix scale. */
+MX_API int mx_factor(mx_handle h);
+
+/* Load vectors f_i = int F . w_i (Sec. 2.2) for nrhs right-hand sides with
+ * F(x) = sum_b pol_b exp(-|x - c_b|^2 / width^2):
+ * centres [nrhs][nbumps][3] (host), pol [nrhs][nbumps][3] complex (host, interleaved),
+ * f [nrhs][n_dof] c128 (host or device). Quadrature: conical-product Gauss-Legendre,
+ * 3 points per direction, on every tetrahedron. */
+MX_API int mx_load_vector(mx_handle h, int nrhs, int nbumps, const double* centres,
+                   const double* pol, double width, void* f);
+
+/* Solve A_{xi_prob} x = b for nrhs right-hand sides by right-preconditioned GMRES
+ * (Sec. 6.1) with the additive Schwarz preconditioner B^{-1} of Eq. 3.4, restarted
+ * every `restart` iterations (0 = unrestarted), x0 = 0, stopping per right-hand side when
+ * the FP64 relative residual ||b - A x|| / ||b|| <= tol or after max_it iterations.
+ * rhs, x: [nrhs][n_dof] c128, host or device. stats: nrhs entries (host) or NULL.
+ * Returns MX_ENOCONV if any right-hand side did not converge (x is still the last
+ * iterate). */
+MX_API int mx_solve(mx_handle h, const void* rhs, int nrhs, double tol, int restart, int max_it,
+             void* x, mx_rhs_stats* stats);
+
+/* Number of unknowns (PEC-interior edges). */
+MX_API int64_t mx_num_dofs(mx_handle h);
+
+/* Sizes of the assembled problem. */
+MX_API int mx_info(mx_handle h, mx_problem_info* out);
+
+/* Device timings of the last build / factor / solve. */
+MX_API int mx_timings(mx_handle h, mx_timing* out);
+
+/* Free the handle and all its device memory. NULL is ignored. */
+MX_API void mx_destroy(mx_handle h);
+
+/* ---- Steps of the path, exposed for verification and composition ---------------- */
+
+/* Integer mesh data (Sec. 2.2), host outputs:
+ * dof_key [n_dof]: 7 * v_low + d of each DOF (v vertex id, d direction index),
+ * tet2dof [6 n^3][6]: DOF of each local edge (01,02,03,12,13,23) of each tetrahedron,
+ * -1 for PEC edges. Either pointer may be NULL. */
+MX_API int mx_get_mesh(mx_handle h, int32_t* dof_key, int32_t* tet2dof);
+
+/* Subdomain index sets I^h(Omega_l) (Eq. 3.1), host outputs: offsets [n_sub + 1],
+ * lists [sum_local] (sorted global DOFs of each subdomain, concatenated);
+ * inverse map inv_ptr [n_dof + 1], inv_pos [sum_local] (positions into `lists`, in
+ * increasing subdomain order). Any pointer may be NULL. */
+MX_API int mx_get_subdomains(mx_handle h, int64_t* offsets, int32_t* lists, int32_t* inv_ptr,
+                      int32_t* inv_pos);
+
+/* CSR of K and M (which = 0 fine, 1 coarse), host outputs rowptr [rows + 1],
+ * col [nnz], K [nnz], M [nnz] (FP64). Any pointer may be NULL. */
+MX_API int mx_get_csr(mx_handle h, int which, int32_t* rowptr, int32_t* col, double* K, double* M);
+
+/* R^0 of Eq. 3.2 as CSR [n_coarse x n_dof], host outputs. */
+MX_API int mx_get_coarse_restriction(mx_handle h, int32_t* rowptr, int32_t* col, double* val);
+
+/* y = A_{xi_prob} x (FP64), x and y [nrhs][n_dof] c128, host or device. */
+MX_API int mx_spmv(mx_handle h, const void* x, void* y, int nrhs);
+
+/* z = B^{-1} v (Eq. 3.4) with the factored preconditioner; levels: bit 0 = local
+ * solves (l >= 1), bit 1 = coarse solve (l = 0). v, z [nrhs][n_dof] c128. */
+MX_API int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels);
+
+/* Copy the packed factor of subdomain l (after mx_factor) or its minor A^l (before),
+ * column-major n_l x n_l, c128 (host). Unit lower L below the diagonal, U on and above. */
+MX_API int mx_get_local(mx_handle h, int l, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MXAS_H */

@@ -1,0 +1,21 @@
+"""GB300 (sm_103a) additive-Schwarz preconditioned GMRES for the lowest-order Nedelec
+discretisation of curl curl E - (k^2 + i xi) E = F on the unit cube with PEC boundary
+conditions (Bonazzoli, Dolean, Graham, Spence, Tournier, arXiv:1711.03789).
+
+This package is a thin ctypes binding of the C ABI declared in include/mxas.h: every
+function has the name of the C entry point and only marshals arguments; all work runs in
+the CUDA kernels of libmxas.so. Importing fails loudly if the library has not been built
+(python -c "import __graft_entry__ as g; g.build()").
+
+Vectors are complex128 arrays of shape [nrhs, n_dof] (one right-hand side per row), as
+numpy arrays (host) or torch tensors (host or CUDA).
+"""
+from ._lib import (  # noqa: F401
+    MX_OK, MX_EINVAL, MX_ENOMEM, MX_ENOTFACTORED, MX_ESINGULAR, MX_ENOCONV, MX_ETIMEOUT, MX_ECUDA,
+    MX_PLAIN_FP64, MX_MIXED, MxError, lib, lib_path,
+    mx_version, mx_last_error, mx_build_problem, mx_set_xi_prob, mx_set_stream, mx_set_dense_local,
+    mx_factor, mx_load_vector, mx_solve, mx_num_dofs, mx_info, mx_timings, mx_destroy,
+    mx_get_mesh, mx_get_subdomains, mx_get_csr, mx_get_coarse_restriction, mx_spmv, mx_precond,
+    mx_get_local, mx_set_allocator, use_torch_allocator,
+)
+from .problem import Problem  # noqa: F401

@@ -1,0 +1,416 @@
+// C ABI of the library (declared in include/mxas.h). Every entry point catches all
+// exceptions, records a message for mx_last_error() and returns an MX_E* code.
+#include <cstring>
+
+#include "problem.cuh"
+
+namespace mx {
+const char* last_error();
+void set_allocator(alloc_fn a, free_fn f, void* ctx);
+
+Problem::~Problem() { free_workspace(*this); }
+
+// ---- layout helpers -----------------------------------------------------------------
+// user layout [nrhs][n] <-> solver layout [n][nrhs]
+__global__ void k_to_internal(int64_t n, int nrhs, int r0, int nr, const double2* user, double2* in) {
+  const int64_t work = n * nr;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nr);
+    const int64_t i = t / nr;
+    in[t] = user[(int64_t)(r0 + r) * n + i];
+  }
+}
+__global__ void k_to_user(int64_t n, int nrhs, int r0, int nr, const double2* in, double2* user) {
+  const int64_t work = n * nr;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nr);
+    const int64_t i = t / nr;
+    user[(int64_t)(r0 + r) * n + i] = in[t];
+  }
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller buffer of `bytes`: the pointer itself if it is device memory,
+// else a device copy (in) / a device staging buffer (out).
+struct DevView {
+  const void* user;
+  bool device;
+  DevBuf<unsigned char> tmp;
+  void* p;
+  DevView(const void* u, size_t bytes, bool copy_in, cudaStream_t s) : user(u) {
+    device = is_device_ptr(u);
+    if (device) {
+      p = const_cast<void*>(u);
+    } else {
+      tmp.alloc(bytes);
+      p = tmp.p;
+      if (copy_in) MX_CUDA(cudaMemcpyAsync(p, u, bytes, cudaMemcpyHostToDevice, s));
+    }
+  }
+  void copy_out(size_t bytes, cudaStream_t s) {
+    if (!device) MX_CUDA(cudaMemcpyAsync(const_cast<void*>(user), p, bytes, cudaMemcpyDeviceToHost, s));
+  }
+};
+
+struct EventTimer {
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  explicit EventTimer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  double stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~EventTimer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+template <typename F>
+static int guard(F&& f) {
+  try {
+    f();
+    set_last_error("");
+    return MX_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return MX_ECUDA;
+  } catch (...) {
+    set_last_error("unknown error");
+    return MX_ECUDA;
+  }
+}
+
+static void check_status(Problem& P) {
+  int32_t st[4] = {0, 0, 0, 0};
+  MX_CUDA(cudaMemcpyAsync(st, P.status.p, 16, cudaMemcpyDeviceToHost, P.stream));
+  MX_CUDA(cudaStreamSynchronize(P.stream));
+  MX_REQUIRE(st[0] == 0, MX_ESINGULAR, std::to_string(st[0]) + " zero or non-finite local pivots");
+  MX_REQUIRE(st[1] == 0, MX_ESINGULAR, std::to_string(st[1]) + " zero or non-finite coarse pivots");
+}
+
+}  // namespace mx
+
+using namespace mx;
+
+extern "C" {
+
+const char* mx_version(void) { return "mxas 0.1 (sm_103a)"; }
+
+const char* mx_last_error(void) { return mx::last_error(); }
+
+int mx_set_allocator(void* (*alloc)(size_t, void*), void (*release)(void*, void*), void* ctx) {
+  return guard([&] { set_allocator(alloc, release, ctx); });
+}
+
+int mx_build_problem(const mx_mesh_desc* mesh, double k, double xi_prob, double xi_prec, const mx_dd_desc* dd,
+                     const mx_coarse_desc* coarse, int precision, mx_handle* out) {
+  return guard([&] {
+    MX_REQUIRE(mesh && dd && out, MX_EINVAL, "null descriptor");
+    MX_REQUIRE(mesh->n_cells >= 1 && mesh->n_cells <= 256, MX_EINVAL, "n_cells must be in 1..256");
+    MX_REQUIRE(dd->core_cells >= 1, MX_EINVAL, "core_cells must be >= 1");
+    MX_REQUIRE(dd->overlap_cells >= 0 && dd->overlap_cells <= 6 * dd->core_cells, MX_EINVAL,
+               "overlap_cells must be in 0..6*core_cells");
+    MX_REQUIRE(k > 0 && std::isfinite(k), MX_EINVAL, "k must be > 0");
+    MX_REQUIRE(xi_prec != 0 && std::isfinite(xi_prec) && std::isfinite(xi_prob), MX_EINVAL,
+               "xi_prec must be nonzero and finite");
+    MX_REQUIRE(precision == MX_MIXED || precision == MX_PLAIN_FP64, MX_EINVAL, "unknown precision");
+    const int cm = coarse ? coarse->n_cells : 0;
+    MX_REQUIRE(cm >= 0 && (cm == 0 || mesh->n_cells % cm == 0), MX_EINVAL,
+               "coarse n_cells must divide the fine n_cells");
+    auto P = new Problem();
+    try {
+      P->n = mesh->n_cells;
+      P->k = k;
+      P->xi_prob = xi_prob;
+      P->xi_prec = xi_prec;
+      P->core = dd->core_cells;
+      P->overlap = dd->overlap_cells;
+      P->coarse_m = cm;
+      P->precision = precision;
+      P->status.alloc(4);
+      MX_CUDA(cudaMemsetAsync(P->status.p, 0, 16, P->stream));
+      EventTimer t(P->stream);
+      build_mesh(P->fine, P->n, P->stream);
+      MX_REQUIRE(P->fine.n_dof > 0, MX_EINVAL, "mesh has no interior edge");
+      assemble_KM(P->fine, P->A, P->stream);
+      build_subdomains(*P);
+      if (cm) {
+        build_mesh(P->coarse, cm, P->stream);
+        MX_REQUIRE(P->coarse.n_dof > 0, MX_EINVAL, "coarse mesh has no interior edge (use n_cells >= 2)");
+        assemble_KM(P->coarse, P->Ac, P->stream);
+        build_coarse_restriction(*P);
+        P->n_c = P->coarse.n_dof;
+      }
+      P->timing.build_ms = t.stop();
+    } catch (...) {
+      delete P;
+      throw;
+    }
+    *out = reinterpret_cast<mx_handle>(P);
+  });
+}
+
+int mx_set_xi_prob(mx_handle h, double xi_prob) {
+  return guard([&] {
+    MX_REQUIRE(h && std::isfinite(xi_prob), MX_EINVAL, "bad handle or xi_prob");
+    reinterpret_cast<Problem*>(h)->xi_prob = xi_prob;
+  });
+}
+
+int mx_set_stream(mx_handle h, void* stream) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    reinterpret_cast<Problem*>(h)->stream = reinterpret_cast<cudaStream_t>(stream);
+  });
+}
+
+int mx_set_dense_local(mx_handle h, int dense) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    P.dense_local = dense != 0;
+    P.minors_ready = false;
+    P.factored = false;
+  });
+}
+
+int mx_factor(mx_handle h) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    MX_CUDA(cudaMemsetAsync(P.status.p, 0, 16, P.stream));
+    EventTimer t(P.stream);
+    extract_minors(P);
+    factor_local(P);
+    factor_coarse(P);
+    P.timing.factor_ms = t.stop();
+    check_status(P);
+  });
+}
+
+int mx_load_vector(mx_handle h, int nrhs, int nbumps, const double* centres, const double* pol, double width,
+                   void* f) {
+  return guard([&] {
+    MX_REQUIRE(h && centres && pol && f, MX_EINVAL, "null argument");
+    MX_REQUIRE(nrhs >= 1 && nbumps >= 1 && width > 0, MX_EINVAL, "bad sizes");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    const size_t bytes = (size_t)nrhs * P.fine.n_dof * sizeof(double2);
+    DevView out(f, bytes, false, P.stream);
+    load_vector(P, nrhs, nbumps, centres, pol, width, reinterpret_cast<double2*>(out.p));
+    out.copy_out(bytes, P.stream);
+    MX_CUDA(cudaStreamSynchronize(P.stream));
+  });
+}
+
+int mx_solve(mx_handle h, const void* rhs, int nrhs, double tol, int restart, int max_it, void* x,
+             mx_rhs_stats* stats) {
+  int rc = MX_OK;
+  int g = guard([&] {
+    MX_REQUIRE(h && rhs && x, MX_EINVAL, "null argument");
+    MX_REQUIRE(nrhs >= 1 && tol > 0 && restart >= 0 && max_it >= 1, MX_EINVAL, "bad solve arguments");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    MX_REQUIRE(P.factored, MX_ENOTFACTORED, "mx_solve before mx_factor");
+    const int64_t n = P.fine.n_dof;
+    const size_t bytes = (size_t)nrhs * n * sizeof(double2);
+    EventTimer t(P.stream);
+    DevView in(rhs, bytes, true, P.stream);
+    DevView out(x, bytes, false, P.stream);
+    const int batch = 32;
+    DevBuf<double2> bi((size_t)n * std::min(nrhs, batch)), xi((size_t)n * std::min(nrhs, batch));
+    int64_t launches = 0;
+    int maxit = 0, restarts = 0;
+    for (int r0 = 0; r0 < nrhs; r0 += batch) {
+      const int nr = std::min(batch, nrhs - r0);
+      k_to_internal<<<grid_for(n * nr, 256), 256, 0, P.stream>>>(n, nrhs, r0, nr, (const double2*)in.p, bi.p);
+      MX_CHECK_LAUNCH();
+      const int c = gmres_solve(P, bi.p, xi.p, nr, tol, restart, max_it, stats ? stats + r0 : nullptr);
+      if (c != MX_OK) rc = c;
+      k_to_user<<<grid_for(n * nr, 256), 256, 0, P.stream>>>(n, nrhs, r0, nr, xi.p, (double2*)out.p);
+      MX_CHECK_LAUNCH();
+      launches += P.timing.solve_launches + 2;
+      maxit = std::max(maxit, P.timing.max_iterations);
+      restarts += P.timing.restarts;
+    }
+    out.copy_out(bytes, P.stream);
+    P.timing.solve_ms = t.stop();
+    P.timing.solve_launches = launches;
+    P.timing.max_iterations = maxit;
+    P.timing.restarts = restarts;
+  });
+  if (g != MX_OK) return g;
+  if (rc != MX_OK) set_last_error("GMRES did not reach the tolerance for every right-hand side");
+  return rc;
+}
+
+int64_t mx_num_dofs(mx_handle h) { return h ? reinterpret_cast<Problem*>(h)->fine.n_dof : 0; }
+
+int mx_info(mx_handle h, mx_problem_info* out) {
+  return guard([&] {
+    MX_REQUIRE(h && out, MX_EINVAL, "null argument");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    std::memset(out, 0, sizeof(*out));
+    out->n_dof = P.fine.n_dof;
+    out->nnz = P.A.nnz;
+    out->n_sub = P.n_sub;
+    out->max_local = P.max_local;
+    out->sum_local = P.sum_local;
+    out->n_coarse = P.coarse_m ? P.coarse.n_dof : 0;
+    out->nnz_r0 = P.R0.nnz;
+    out->factor_bytes = (int64_t)P.factors.bytes() + (int64_t)P.A0.bytes() + (int64_t)P.A0f.bytes();
+    out->coarse_band = P.coarse_band;
+    out->precision = P.precision;
+  });
+}
+
+int mx_timings(mx_handle h, mx_timing* out) {
+  return guard([&] {
+    MX_REQUIRE(h && out, MX_EINVAL, "null argument");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    out->build_ms = P.timing.build_ms;
+    out->factor_ms = P.timing.factor_ms;
+    out->solve_ms = P.timing.solve_ms;
+    out->solve_launches = P.timing.solve_launches;
+    out->restarts = P.timing.restarts;
+    out->max_iterations = P.timing.max_iterations;
+  });
+}
+
+void mx_destroy(mx_handle h) {
+  if (!h) return;
+  auto* P = reinterpret_cast<Problem*>(h);
+  cudaStreamSynchronize(P->stream);
+  delete P;
+}
+
+int mx_get_mesh(mx_handle h, int32_t* dof_key, int32_t* tet2dof) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    if (dof_key) MX_CUDA(cudaMemcpy(dof_key, P.fine.dof_key.p, P.fine.n_dof * 4, cudaMemcpyDeviceToHost));
+    if (tet2dof) MX_CUDA(cudaMemcpy(tet2dof, P.fine.tet2dof.p, P.fine.tet2dof.bytes(), cudaMemcpyDeviceToHost));
+  });
+}
+
+int mx_get_subdomains(mx_handle h, int64_t* offsets, int32_t* lists, int32_t* inv_ptr, int32_t* inv_pos) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    if (offsets) std::memcpy(offsets, P.h_offsets.data(), (P.n_sub + 1) * 8);
+    if (lists) MX_CUDA(cudaMemcpy(lists, P.lists.p, P.sum_local * 4, cudaMemcpyDeviceToHost));
+    if (inv_ptr) MX_CUDA(cudaMemcpy(inv_ptr, P.inv_ptr.p, (P.fine.n_dof + 1) * 4, cudaMemcpyDeviceToHost));
+    if (inv_pos) MX_CUDA(cudaMemcpy(inv_pos, P.inv_pos.p, P.sum_local * 4, cudaMemcpyDeviceToHost));
+  });
+}
+
+int mx_get_csr(mx_handle h, int which, int32_t* rowptr, int32_t* col, double* K, double* M) {
+  return guard([&] {
+    MX_REQUIRE(h && (which == 0 || which == 1), MX_EINVAL, "bad arguments");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    CsrKM& A = which == 0 ? P.A : P.Ac;
+    MX_REQUIRE(which == 0 || P.coarse_m, MX_EINVAL, "no coarse space");
+    if (rowptr) MX_CUDA(cudaMemcpy(rowptr, A.rowptr.p, (A.rows + 1) * 4, cudaMemcpyDeviceToHost));
+    if (col) MX_CUDA(cudaMemcpy(col, A.col.p, A.nnz * 4, cudaMemcpyDeviceToHost));
+    if (K) MX_CUDA(cudaMemcpy(K, A.K.p, A.nnz * 8, cudaMemcpyDeviceToHost));
+    if (M) MX_CUDA(cudaMemcpy(M, A.M.p, A.nnz * 8, cudaMemcpyDeviceToHost));
+  });
+}
+
+int mx_get_coarse_restriction(mx_handle h, int32_t* rowptr, int32_t* col, double* val) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    MX_REQUIRE(P.coarse_m, MX_EINVAL, "no coarse space");
+    if (rowptr) MX_CUDA(cudaMemcpy(rowptr, P.R0.rowptr.p, (P.R0.rows + 1) * 4, cudaMemcpyDeviceToHost));
+    if (col) MX_CUDA(cudaMemcpy(col, P.R0.col.p, P.R0.nnz * 4, cudaMemcpyDeviceToHost));
+    if (val) MX_CUDA(cudaMemcpy(val, P.R0.val.p, P.R0.nnz * 8, cudaMemcpyDeviceToHost));
+  });
+}
+
+int mx_spmv(mx_handle h, const void* x, void* y, int nrhs) {
+  return guard([&] {
+    MX_REQUIRE(h && x && y && nrhs >= 1, MX_EINVAL, "bad arguments");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    const int64_t n = P.fine.n_dof;
+    const size_t bytes = (size_t)nrhs * n * sizeof(double2);
+    DevView in(x, bytes, true, P.stream);
+    DevView out(y, bytes, false, P.stream);
+    DevBuf<double2> a((size_t)n * nrhs), b((size_t)n * nrhs);
+    k_to_internal<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, (const double2*)in.p, a.p);
+    spmv(P, P.xi_prob, a.p, 0, b.p, nrhs, P.stream);
+    k_to_user<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, b.p, (double2*)out.p);
+    MX_CHECK_LAUNCH();
+    out.copy_out(bytes, P.stream);
+    MX_CUDA(cudaStreamSynchronize(P.stream));
+  });
+}
+
+int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels) {
+  return guard([&] {
+    MX_REQUIRE(h && v && z && nrhs >= 1 && nrhs <= 32 && levels >= 1 && levels <= 3, MX_EINVAL, "bad arguments");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    MX_REQUIRE(P.factored, MX_ENOTFACTORED, "mx_precond before mx_factor");
+    const int64_t n = P.fine.n_dof;
+    const size_t bytes = (size_t)nrhs * n * sizeof(double2);
+    DevView in(v, bytes, true, P.stream);
+    DevView out(z, bytes, false, P.stream);
+    DevBuf<double2> a((size_t)n * nrhs), b((size_t)n * nrhs);
+    k_to_internal<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, (const double2*)in.p, a.p);
+    precond_apply(P, a.p, b.p, 0, nrhs, levels);
+    k_to_user<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, b.p, (double2*)out.p);
+    MX_CHECK_LAUNCH();
+    out.copy_out(bytes, P.stream);
+    MX_CUDA(cudaStreamSynchronize(P.stream));
+  });
+}
+
+int mx_get_local(mx_handle h, int l, double* out) {
+  return guard([&] {
+    MX_REQUIRE(h && out, MX_EINVAL, "null argument");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    MX_REQUIRE(l >= 0 && l < P.n_sub, MX_EINVAL, "subdomain index out of range");
+    if (!P.factored && !P.minors_ready) extract_minors(P);
+    const int nl = P.h_nl[l], b = P.h_band[l], ld = P.h_ld[l];
+    const bool mixed = P.precision == MX_MIXED;
+    const size_t esz = mixed ? 8 : 16;
+    std::vector<unsigned char> band((size_t)ld * nl * esz);
+    MX_CUDA(cudaMemcpy(band.data(), P.factors.p + (size_t)P.h_mat_off[l] * esz, band.size(), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, (size_t)nl * nl * 16);
+    for (int j = 0; j < nl; ++j)
+      for (int i = std::max(0, j - b); i <= std::min(nl - 1, j + b); ++i) {
+        const size_t src = (size_t)j * ld + (b + i - j);
+        double re, im;
+        if (mixed) {
+          const float* f = reinterpret_cast<const float*>(band.data()) + 2 * src;
+          re = f[0];
+          im = f[1];
+        } else {
+          const double* d = reinterpret_cast<const double*>(band.data()) + 2 * src;
+          re = d[0];
+          im = d[1];
+        }
+        out[2 * ((size_t)j * nl + i)] = re;
+        out[2 * ((size_t)j * nl + i) + 1] = im;
+      }
+  });
+}
+
+}  // extern "C"

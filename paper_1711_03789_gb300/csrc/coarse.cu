@@ -1,0 +1,199 @@
+// Coarse level of the two-level preconditioner (Sec. 3.2-3.3, Eq. 3.4 with l = 0):
+// the Galerkin matrix A^0_{xi_prec} assembled on the coarse Kuhn mesh, its FP64 LU
+// (band-limited, no pivoting: A^0 is invertible for xi != 0 by coercivity, Sec. 3.3),
+// and the coarse solve y = (A^0)^{-1} R^0 v.
+//
+// The coarse solve runs as one cooperative kernel: the band triangular sweeps proceed in
+// blocks of CB columns; every block of the grid solves the small diagonal triangle
+// redundantly, then updates its share of the rows inside the band, and a grid-wide
+// barrier separates the steps. In MX_MIXED the sweep uses a c64 copy of the FP64
+// factors (the preconditioner only needs to be a fixed linear map; the outer FGMRES
+// recurrence stays in FP64); in MX_PLAIN_FP64 it uses the FP64 factors.
+#include <cooperative_groups.h>
+
+#include "problem.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mx {
+
+constexpr int CB = 32;
+
+// bandwidth of the coarse CSR pattern
+__global__ void k_csr_band(int64_t rows, const int32_t* rowptr, const int32_t* col, int32_t* out) {
+  int bmax = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) bmax = max(bmax, abs((int)(col[e] - i)));
+  atomicMax(out, bmax);
+}
+
+__global__ void k_coarse_fill(int64_t rows, const int32_t* rowptr, const int32_t* col, const double* K,
+                              const double* M, double sr, double si, int b, int ld, double2* A) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      A[bidx(0, ld, b, (int)i, col[e])] = make_double2(K[e] - sr * M[e], -si * M[e]);
+}
+
+__global__ void k_to_c64(int64_t n, const double2* a, float2* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = to_c64(a[i]);
+}
+
+void factor_coarse(Problem& P) {
+  if (!P.coarse_m) return;
+  cudaStream_t s = P.stream;
+  const int64_t nc = P.coarse.n_dof;
+  P.n_c = nc;
+  DevBuf<int32_t> bw(1);
+  MX_CUDA(cudaMemsetAsync(bw.p, 0, 4, s));
+  k_csr_band<<<grid_for(nc, 256), 256, 0, s>>>(nc, P.Ac.rowptr.p, P.Ac.col.p, bw.p);
+  MX_CHECK_LAUNCH();
+  int b = 0;
+  MX_CUDA(cudaMemcpyAsync(&b, bw.p, 4, cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  P.coarse_band = b;
+  P.ld_c = (2 * b + 1 + 3) & ~3;
+  P.A0.alloc(P.ld_c * nc);
+  MX_CUDA(cudaMemsetAsync(P.A0.p, 0, P.A0.bytes(), s));
+  k_coarse_fill<<<grid_for(nc, 256), 256, 0, s>>>(nc, P.Ac.rowptr.p, P.Ac.col.p, P.Ac.K.p, P.Ac.M.p,
+                                                  P.k * P.k, P.xi_prec, b, (int)P.ld_c, P.A0.p);
+  MX_CHECK_LAUNCH();
+  const int32_t meta[3] = {(int32_t)nc, b, (int32_t)P.ld_c};
+  const int64_t zero = 0;
+  P.c_meta.alloc(3);
+  P.c_off.alloc(1);
+  MX_CUDA(cudaMemcpyAsync(P.c_meta.p, meta, 12, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemcpyAsync(P.c_off.p, &zero, 8, cudaMemcpyHostToDevice, s));
+  BandBatch B{1, P.c_meta.p, P.c_meta.p + 1, P.c_meta.p + 2, P.c_off.p};
+  band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s);
+  if (P.precision == MX_MIXED) {
+    P.A0f.alloc(P.A0.n);
+    k_to_c64<<<grid_for(P.A0.n, 256), 256, 0, s>>>(P.A0.n, P.A0.p, P.A0f.p);
+    MX_CHECK_LAUNCH();
+  }
+  MX_CUDA(cudaStreamSynchronize(s));
+}
+
+// r0[q][p] = sum_j R^0_pj v[q][j]  (FP64 accumulation), written as T2
+template <typename T2>
+__global__ void k_coarse_restrict(int64_t nc, int64_t n, int nrhs, const int32_t* rowptr, const int32_t* col,
+                                  const double* val, const void* v, int vtype, T2* r0) {
+  const int64_t work = nc * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t % nrhs);
+    const int64_t p = t / nrhs;
+    double2 acc = make_double2(0, 0);
+    for (int32_t e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+      const int64_t idx = (int64_t)col[e] * nrhs + q;
+      double2 x;
+      if (vtype == 0) x = reinterpret_cast<const double2*>(v)[idx];
+      else x = to_c128(reinterpret_cast<const float2*>(v)[idx]);
+      acc.x += val[e] * x.x;
+      acc.y += val[e] * x.y;
+    }
+    r0[p * nrhs + q] = conv<T2>(acc);
+  }
+}
+
+// Band triangular sweeps on r [n][nrhs] (in place): forward with unit lower L, backward
+// with upper U. Grid-wide barriers between column blocks.
+template <typename T2>
+__global__ void k_coarse_sweep(int n, int b, int ld, const T2* F, T2* r, int nrhs) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ unsigned char smem_raw[];
+  T2* x = reinterpret_cast<T2*>(smem_raw);  // [CB][nrhs]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nblk = (n + CB - 1) / CB;
+  // forward
+  for (int blk = 0; blk < nblk; ++blk) {
+    const int c0 = blk * CB, c1 = min(n, c0 + CB);
+    for (int t = tid; t < (c1 - c0) * nrhs; t += nt) x[t] = r[(int64_t)c0 * nrhs + t];
+    __syncthreads();
+    for (int k = c0; k < c1 - 1; ++k) {
+      for (int t = tid; t < (c1 - k - 1) * nrhs; t += nt) {
+        const int i = k + 1 + t / nrhs, q = t % nrhs;
+        if (i - k <= b) {
+          T2 v = x[(i - c0) * nrhs + q];
+          cfms(v, F[bidx(0, ld, b, i, k)], x[(k - c0) * nrhs + q]);
+          x[(i - c0) * nrhs + q] = v;
+        }
+      }
+      __syncthreads();
+    }
+    if (blockIdx.x == 0)
+      for (int t = tid; t < (c1 - c0) * nrhs; t += nt) r[(int64_t)c0 * nrhs + t] = x[t];
+    const int r1 = min(n, c1 + b);
+    const int64_t work = (int64_t)(r1 - c1) * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)nt + tid; t < work; t += (int64_t)gridDim.x * nt) {
+      const int i = c1 + (int)(t / nrhs), q = (int)(t % nrhs);
+      T2 acc = r[(int64_t)i * nrhs + q];
+      for (int k = max(c0, i - b); k < c1; ++k) cfms(acc, F[bidx(0, ld, b, i, k)], x[(k - c0) * nrhs + q]);
+      r[(int64_t)i * nrhs + q] = acc;
+    }
+    grid.sync();
+  }
+  // backward
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int c0 = blk * CB, c1 = min(n, c0 + CB);
+    for (int t = tid; t < (c1 - c0) * nrhs; t += nt) x[t] = r[(int64_t)c0 * nrhs + t];
+    __syncthreads();
+    for (int k = c1 - 1; k >= c0; --k) {
+      for (int q = tid; q < nrhs; q += nt) x[(k - c0) * nrhs + q] = cmul(x[(k - c0) * nrhs + q], crcp(F[bidx(0, ld, b, k, k)]));
+      __syncthreads();
+      for (int t = tid; t < (k - c0) * nrhs; t += nt) {
+        const int i = c0 + t / nrhs, q = t % nrhs;
+        if (k - i <= b) {
+          T2 v = x[(i - c0) * nrhs + q];
+          cfms(v, F[bidx(0, ld, b, i, k)], x[(k - c0) * nrhs + q]);
+          x[(i - c0) * nrhs + q] = v;
+        }
+      }
+      __syncthreads();
+    }
+    if (blockIdx.x == 0)
+      for (int t = tid; t < (c1 - c0) * nrhs; t += nt) r[(int64_t)c0 * nrhs + t] = x[t];
+    const int r0 = max(0, c0 - b);
+    const int64_t work = (int64_t)(c0 - r0) * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)nt + tid; t < work; t += (int64_t)gridDim.x * nt) {
+      const int i = r0 + (int)(t / nrhs), q = (int)(t % nrhs);
+      T2 acc = r[(int64_t)i * nrhs + q];
+      for (int k = c0; k < min(c1, i + b + 1); ++k) cfms(acc, F[bidx(0, ld, b, i, k)], x[(k - c0) * nrhs + q]);
+      r[(int64_t)i * nrhs + q] = acc;
+    }
+    grid.sync();
+  }
+}
+
+template <typename T2>
+static void sweep(Problem& P, T2* F, T2* r, int nrhs) {
+  const int n = (int)P.n_c, b = P.coarse_band, ld = (int)P.ld_c;
+  const size_t smem = (size_t)CB * nrhs * sizeof(T2);
+  MX_REQUIRE(smem <= 48 * 1024, MX_EINVAL, "too many right-hand sides for the coarse sweep");
+  int per_sm = 0;
+  MX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_sweep<T2>, 256, smem));
+  MX_REQUIRE(per_sm > 0, MX_ECUDA, "coarse sweep kernel cannot be resident");
+  const int64_t work = (int64_t)std::min(b, n) * nrhs;
+  int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, std::max<int64_t>(1, (work + 255) / 256));
+  grid = std::max(1, std::min(grid, sm_count()));
+  void* args[] = {(void*)&n, (void*)&b, (void*)&ld, (void*)&F, (void*)&r, (void*)&nrhs};
+  MX_CUDA(cudaLaunchCooperativeKernel((void*)k_coarse_sweep<T2>, grid, 256, args, smem, P.stream));
+}
+
+void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
+  cudaStream_t s = P.stream;
+  const int64_t nc = P.n_c;
+  if (P.precision == MX_MIXED) {
+    float2* r = reinterpret_cast<float2*>(yc);  // c64 view of the workspace
+    k_coarse_restrict<float2><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(nc, P.fine.n_dof, nrhs, P.R0.rowptr.p,
+                                                                       P.R0.col.p, P.R0.val.p, v, vtype, r);
+    MX_CHECK_LAUNCH();
+    sweep<float2>(P, P.A0f.p, r, nrhs);
+  } else {
+    k_coarse_restrict<double2><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(nc, P.fine.n_dof, nrhs, P.R0.rowptr.p,
+                                                                        P.R0.col.p, P.R0.val.p, v, vtype, yc);
+    MX_CHECK_LAUNCH();
+    sweep<double2>(P, P.A0.p, yc, nrhs);
+  }
+}
+
+}  // namespace mx

@@ -1,0 +1,623 @@
+// Operator, preconditioner apply and batched right-preconditioned GMRES (Sec. 6.1).
+//
+// Vectors inside the solver are stored [n][nrhs] (right-hand side index fastest) so the
+// gathers of the SpMV, the restriction and the scatter read one contiguous segment per
+// DOF. The right-preconditioned iteration is run in its flexible form: z_j = B^{-1} v_j is
+// stored (c64 in MX_MIXED, c128 in MX_PLAIN_FP64), w = A z_j is formed in FP64, so the
+// Arnoldi relation A Z_m = V_{m+1} H_m holds for the stored z_j whatever the precision
+// of the preconditioner; x = x0 + Z_m y. Arnoldi is classical Gram-Schmidt with a second
+// pass when the norm drops below 1/sqrt(2) of its value before orthogonalisation
+// (Daniel-Gragg-Kaufman-Stewart criterion), in FP64 with fixed-order reductions. The
+// least-squares problem is updated by complex Givens rotations; the stopping test uses
+// the FP64 true residual ||b - A x|| / ||b|| at every restart and at the end.
+#include "problem.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace mx {
+
+// ---- SpMV ---------------------------------------------------------------------------
+// y[i][r] = sum_e (K_e - s M_e) x[col_e][r],  s = k^2 + i xi
+template <typename XT>
+__global__ void k_spmv(int64_t rows, int nrhs, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ K, const double* __restrict__ M, double sr, double si,
+                       const XT* __restrict__ x, double2* __restrict__ y) {
+  const int64_t work = rows * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nrhs);
+    const int64_t i = t / nrhs;
+    double2 kx = make_double2(0, 0), mx_ = make_double2(0, 0);
+    const int32_t e1 = rowptr[i + 1];
+    for (int32_t e = rowptr[i]; e < e1; ++e) {
+      const double2 xv = to_c128(x[(int64_t)col[e] * nrhs + r]);
+      const double k = K[e], m = M[e];
+      kx.x = fma(k, xv.x, kx.x);
+      kx.y = fma(k, xv.y, kx.y);
+      mx_.x = fma(m, xv.x, mx_.x);
+      mx_.y = fma(m, xv.y, mx_.y);
+    }
+    // K x - (sr + i si) M x
+    y[t] = make_double2(kx.x - sr * mx_.x + si * mx_.y, kx.y - sr * mx_.y - si * mx_.x);
+  }
+}
+
+void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int nrhs, cudaStream_t s) {
+  const int64_t work = P.A.rows * nrhs;
+  const double sr = P.k * P.k, si = xi;
+  if (xtype == 0)
+    k_spmv<double2><<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, P.A.K.p,
+                                                                    P.A.M.p, sr, si, (const double2*)x, y);
+  else
+    k_spmv<float2><<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, P.A.K.p,
+                                                                   P.A.M.p, sr, si, (const float2*)x, y);
+  MX_CHECK_LAUNCH();
+}
+
+// ---- preconditioner: scatter-add of local solutions (+ coarse prolongation) ---------
+// z[i][r] = sum_{q in inv(i)} loc[q][r] + sum_{p} (R^0)^T_{ip} y0[p][r]   (Eq. 3.4)
+template <typename LT, typename CT, typename ZT>
+__global__ void k_scatter(int64_t n, int nrhs, const int32_t* __restrict__ inv_ptr, const int32_t* __restrict__ inv_pos,
+                          const LT* __restrict__ loc, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tcol,
+                          const double* __restrict__ tval, const CT* __restrict__ y0, int use_local, ZT* __restrict__ z) {
+  const int64_t work = n * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nrhs);
+    const int64_t i = t / nrhs;
+    double2 acc = make_double2(0, 0);
+    if (use_local)
+      for (int32_t q = inv_ptr[i]; q < inv_ptr[i + 1]; ++q) {
+        const int32_t pos = inv_pos[q];
+        if (pos < 0) continue;
+        const double2 v = to_c128(loc[(int64_t)pos * nrhs + r]);
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+    if (tptr)
+      for (int32_t e = tptr[i]; e < tptr[i + 1]; ++e) {
+        const double2 v = to_c128(y0[(int64_t)tcol[e] * nrhs + r]);
+        acc.x = fma(tval[e], v.x, acc.x);
+        acc.y = fma(tval[e], v.y, acc.y);
+      }
+    z[t] = conv<ZT>(acc);
+  }
+}
+
+struct Workspace {
+  int nrhs = 0, m = 0;
+  int64_t n = 0;
+  size_t zsz = 0;
+  DevBuf<double2> V;              // (m+1) [n][nrhs]
+  DevBuf<unsigned char> Z;        // m [n][nrhs] of c64 / c128
+  DevBuf<double2> w, b, x, r;     // [n][nrhs]
+  DevBuf<unsigned char> loc;      // [sum_local][nrhs] local solutions
+  DevBuf<double2> yc;             // [n_c][nrhs]
+  DevBuf<double2> H;              // [m][m+1][nrhs]   column j, row i
+  DevBuf<double> cs;              // [m][nrhs]
+  DevBuf<double2> sn;             // [m][nrhs]
+  DevBuf<double2> g;              // [m+1][nrhs]
+  DevBuf<double2> y;              // [m][nrhs]
+  DevBuf<double2> hpart;          // [nblk][m+2][nrhs] partial dot products
+  DevBuf<double2> h2;             // [m+2][nrhs] reduced dots of the current pass
+  DevBuf<double> npart;           // [nblk][nrhs]
+  DevBuf<double> bnorm, wnorm0;   // [nrhs]
+  DevBuf<int32_t> active;         // [nrhs] 1 while the right-hand side iterates
+  DevBuf<int32_t> flags;          // [4]: 0 any active, 1 any reorth
+  DevBuf<double> est;             // [nrhs] residual estimate / ||b||
+  int32_t* h_flags = nullptr;     // pinned
+  double* h_small = nullptr;      // pinned [3 * nrhs]
+  int nblk = 0;
+  ~Workspace() {
+    if (h_flags) cudaFreeHost(h_flags);
+    if (h_small) cudaFreeHost(h_small);
+  }
+};
+
+void free_workspace(Problem& P) {
+  delete P.ws;
+  P.ws = nullptr;
+}
+
+static Workspace& workspace(Problem& P, int nrhs, int m) {
+  const int64_t n = P.fine.n_dof;
+  const size_t zsz = P.precision == MX_MIXED ? sizeof(float2) : sizeof(double2);
+  Workspace* W = P.ws;
+  if (W && W->nrhs == nrhs && W->m >= m && W->n == n) return *W;
+  delete W;
+  W = P.ws = new Workspace();
+  W->nrhs = nrhs;
+  W->m = m;
+  W->n = n;
+  W->zsz = zsz;
+  const int64_t nv = n * nrhs;
+  W->V.alloc((size_t)(m + 1) * nv);
+  W->Z.alloc((size_t)m * nv * zsz);
+  W->w.alloc(nv);
+  W->b.alloc(nv);
+  W->x.alloc(nv);
+  W->r.alloc(nv);
+  W->loc.alloc((size_t)P.sum_local * nrhs * zsz);
+  if (P.coarse_m) W->yc.alloc((size_t)P.n_c * nrhs);
+  W->H.alloc((size_t)m * (m + 1) * nrhs);
+  W->cs.alloc((size_t)m * nrhs);
+  W->sn.alloc((size_t)m * nrhs);
+  W->g.alloc((size_t)(m + 1) * nrhs);
+  W->y.alloc((size_t)m * nrhs);
+  W->nblk = 2 * sm_count();
+  W->hpart.alloc((size_t)W->nblk * (m + 2) * nrhs);
+  W->h2.alloc((size_t)(m + 2) * nrhs);
+  W->npart.alloc((size_t)W->nblk * nrhs);
+  W->bnorm.alloc(nrhs);
+  W->wnorm0.alloc(nrhs);
+  W->active.alloc(nrhs);
+  W->flags.alloc(4);
+  W->est.alloc(nrhs);
+  MX_CUDA(cudaHostAlloc(&W->h_flags, 16, cudaHostAllocDefault));
+  MX_CUDA(cudaHostAlloc(&W->h_small, sizeof(double) * 3 * nrhs, cudaHostAllocDefault));
+  return *W;
+}
+
+void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, int levels) {
+  Workspace& W = workspace(P, nrhs, P.ws ? std::max(P.ws->m, 1) : 1);
+  cudaStream_t s = P.stream;
+  const bool mixed = P.precision == MX_MIXED;
+  if (levels & 1) local_solves(P, v, 0, W.loc.p, nrhs);
+  const bool coarse = (levels & 2) && P.coarse_m;
+  if (coarse) coarse_solve(P, v, 0, W.yc.p, nrhs);
+  const int64_t work = P.fine.n_dof * nrhs;
+  const int32_t* tp = coarse ? P.R0T.rowptr.p : nullptr;
+  const unsigned grid = grid_for(work, 256, 152LL * 32);
+#define MX_SCATTER(LT, CT, ZT)                                                                            \
+  k_scatter<LT, CT, ZT><<<grid, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p, (const LT*)W.loc.p, tp, \
+                                             P.R0T.col.p, P.R0T.val.p, (const CT*)W.yc.p, levels & 1, (ZT*)z)
+  if (mixed) {
+    if (ztype == 0) MX_SCATTER(float2, float2, double2);
+    else MX_SCATTER(float2, float2, float2);
+  } else {
+    if (ztype == 0) MX_SCATTER(double2, double2, double2);
+    else MX_SCATTER(double2, double2, float2);
+  }
+#undef MX_SCATTER
+  MX_CHECK_LAUNCH();
+}
+
+// ---- Arnoldi kernels ----------------------------------------------------------------
+// Partial dots: block `blk` owns rows [x0, x1). Warp w handles basis indices i = w, w+8,
+// ...; lanes are (xl, r) with r fastest (RP = nrhs rounded up to a power of two <= 32,
+// XL = 32 / RP rows per warp step). Index i == nvec - 1 + extra uses w itself (its norm).
+// hpart[blk][i][r] = sum_{x in block} conj(V_i[x][r]) w[x][r]
+template <int RP>
+__global__ void __launch_bounds__(256) k_dots(int64_t n, int nrhs, int nvec, int with_norm, const double2* __restrict__ V,
+                                              const double2* __restrict__ w, const int32_t* __restrict__ active,
+                                              double2* __restrict__ hpart) {
+  constexpr int XL = 32 / RP;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = lane % RP, xl = lane / RP;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t x0 = blockIdx.x * chunk, x1 = min(n, x0 + chunk);
+  const int total = nvec + with_norm;
+  const int64_t nv = n * nrhs;
+  const bool on = r < nrhs && active[min(r, nrhs - 1)];
+  for (int i = warp; i < total; i += 8) {
+    const double2* Vi = (i < nvec) ? V + (int64_t)i * nv : w;
+    double ax = 0, ay = 0;
+    if (on)
+      for (int64_t x = x0 + xl; x < x1; x += XL) {
+        const double2 a = Vi[x * nrhs + r];
+        const double2 c = w[x * nrhs + r];
+        ax = fma(a.x, c.x, ax);
+        ax = fma(a.y, c.y, ax);
+        ay = fma(a.x, c.y, ay);
+        ay = fma(-a.y, c.x, ay);
+      }
+#pragma unroll
+    for (int o = RP; o < 32; o <<= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (xl == 0 && r < nrhs) hpart[((int64_t)blockIdx.x * (total) + i) * nrhs + r] = make_double2(ax, ay);
+  }
+}
+
+// h[i][r] = sum_blk hpart[blk][i][r] in block order (deterministic)
+__global__ void k_reduce_dots(int nblk, int total, int nrhs, const double2* hpart, double2* h) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total * nrhs; t += gridDim.x * blockDim.x) {
+    double ax = 0, ay = 0;
+    for (int b = 0; b < nblk; ++b) {
+      const double2 v = hpart[(int64_t)b * total * nrhs + t];
+      ax += v.x;
+      ay += v.y;
+    }
+    h[t] = make_double2(ax, ay);
+  }
+}
+
+// w[x][r] -= sum_{i < nvec} V_i[x][r] h[i][r]; npart[blk][r] = sum over the block of |w|^2
+template <int RP>
+__global__ void __launch_bounds__(256) k_orth_update(int64_t n, int nrhs, int nvec, const double2* __restrict__ V,
+                                                     const double2* __restrict__ h, const int32_t* __restrict__ active,
+                                                     double2* __restrict__ w, double* __restrict__ npart) {
+  constexpr int XL = 32 / RP;
+  __shared__ double sh[8][RP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = lane % RP, xl = lane / RP;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t x0 = blockIdx.x * chunk, x1 = min(n, x0 + chunk);
+  const int64_t nv = n * nrhs;
+  const bool on = r < nrhs && active[min(r, nrhs - 1)];
+  double nrm = 0;
+  if (on)
+    for (int64_t x = x0 + warp * XL + xl; x < x1; x += 8 * XL) {
+      double2 acc = w[x * nrhs + r];
+      for (int i = 0; i < nvec; ++i) {
+        const double2 a = V[(int64_t)i * nv + x * nrhs + r];
+        const double2 c = h[i * nrhs + r];
+        acc.x = fma(-a.x, c.x, acc.x);
+        acc.x = fma(a.y, c.y, acc.x);
+        acc.y = fma(-a.x, c.y, acc.y);
+        acc.y = fma(-a.y, c.x, acc.y);
+      }
+      w[x * nrhs + r] = acc;
+      nrm = fma(acc.x, acc.x, nrm);
+      nrm = fma(acc.y, acc.y, nrm);
+    }
+#pragma unroll
+  for (int o = RP; o < 32; o <<= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if (xl == 0) sh[warp][r] = nrm;
+  __syncthreads();
+  if (threadIdx.x < RP && threadIdx.x < nrhs) {
+    double s = 0;
+    for (int wq = 0; wq < 8; ++wq) s += sh[wq][threadIdx.x];
+    npart[(int64_t)blockIdx.x * nrhs + threadIdx.x] = s;
+  }
+}
+
+// After pass p: store h (accumulated over passes) into column j of H, the new norm,
+// and decide whether a second pass is needed (DGKS, eta = 1/sqrt(2)).
+__global__ void k_arnoldi_finish(int nblk, int nrhs, int j, int m, int pass, const double2* h2, const double* npart,
+                                 double2* H, double* wnorm0, int32_t* active, int32_t* flags) {
+  const int r = threadIdx.x;
+  if (r == 0 && pass == 0) flags[1] = 0;
+  __syncthreads();
+  if (r >= nrhs) return;
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += npart[(int64_t)b * nrhs + r];
+  const double nw = sqrt(s);
+  if (!active[r]) return;
+  double2* Hc = H + (int64_t)j * (m + 1) * nrhs;
+  for (int i = 0; i <= j; ++i) {
+    const double2 v = h2[i * nrhs + r];
+    if (pass == 0) Hc[i * nrhs + r] = v;
+    else Hc[i * nrhs + r] = make_double2(Hc[i * nrhs + r].x + v.x, Hc[i * nrhs + r].y + v.y);
+  }
+  if (pass == 0) wnorm0[r] = sqrt(h2[(j + 1) * nrhs + r].x);  // ||w|| before orthogonalisation
+  Hc[(j + 1) * nrhs + r] = make_double2(nw, 0.0);
+  if (pass == 0 && nw < 0.7071067811865476 * wnorm0[r]) atomicOr(&flags[1], 1);
+}
+
+// v_{j+1} = w / h_{j+1,j}
+__global__ void k_normalize(int64_t nv, int nrhs, int j, int m, const double2* H, const int32_t* active,
+                            const double2* w, double2* vnext) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nrhs);
+    const double hn = H[((int64_t)j * (m + 1) + j + 1) * nrhs + r].x;
+    const double inv = (hn > 0 && active[r]) ? 1.0 / hn : 0.0;
+    vnext[t] = make_double2(w[t].x * inv, w[t].y * inv);
+  }
+}
+
+// Givens update of column j for every active right-hand side (one thread each).
+__global__ void k_givens(int nrhs, int j, int m, double tol, const double* bnorm, double2* H, double* cs,
+                         double2* sn, double2* g, int32_t* active, double* est, int32_t* flags) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs || !active[r]) return;
+  double2* Hc = H + (int64_t)j * (m + 1) * nrhs;
+  for (int i = 0; i < j; ++i) {
+    const double c = cs[i * nrhs + r];
+    const double2 s = sn[i * nrhs + r];
+    const double2 a = Hc[i * nrhs + r], b = Hc[(i + 1) * nrhs + r];
+    // [c s; -conj(s) c] [a; b]
+    Hc[i * nrhs + r] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+    Hc[(i + 1) * nrhs + r] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+  }
+  const double2 a = Hc[j * nrhs + r], b = Hc[(j + 1) * nrhs + r];
+  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+  double c;
+  double2 s;
+  if (bb == 0) { c = 1; s = make_double2(0, 0); }
+  else if (aa == 0) { c = 0; s = make_double2(b.x / bb, -b.y / bb); }
+  else {
+    const double t = hypot(aa, bb);
+    c = aa / t;
+    const double2 ph = make_double2(a.x / aa, a.y / aa);  // a / |a|
+    // s = (a/|a|) conj(b) / t
+    s = make_double2((ph.x * b.x + ph.y * b.y) / t, (ph.y * b.x - ph.x * b.y) / t);
+  }
+  cs[j * nrhs + r] = c;
+  sn[j * nrhs + r] = s;
+  Hc[j * nrhs + r] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+  Hc[(j + 1) * nrhs + r] = make_double2(0, 0);
+  const double2 gj = g[j * nrhs + r];
+  // g_{j+1} = -conj(s) g_j ; g_j = c g_j
+  g[(j + 1) * nrhs + r] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+  g[j * nrhs + r] = make_double2(c * gj.x, c * gj.y);
+  const double2 gn = g[(j + 1) * nrhs + r];
+  est[r] = hypot(gn.x, gn.y) / bnorm[r];
+}
+
+// y = R^{-1} g for the first k columns (R upper triangular in H after the rotations).
+__global__ void k_backsolve(int nrhs, int m, const int32_t* kcols, const double2* H, const double2* g, double2* y) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int k = kcols[r];
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = g[i * nrhs + r];
+    for (int c = i + 1; c < k; ++c) {
+      const double2 h = H[((int64_t)c * (m + 1) + i) * nrhs + r];
+      const double2 yc = y[c * nrhs + r];
+      s.x -= h.x * yc.x - h.y * yc.y;
+      s.y -= h.x * yc.y + h.y * yc.x;
+    }
+    const double2 d = H[((int64_t)i * (m + 1) + i) * nrhs + r];
+    const double dd = d.x * d.x + d.y * d.y;
+    y[i * nrhs + r] = make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
+  }
+}
+
+// x[x][r] += sum_{i < k_r} Z_i[x][r] y_i[r]
+template <typename ZT>
+__global__ void k_update_x(int64_t n, int nrhs, const int32_t* kcols, const ZT* Z, const double2* y, double2* x) {
+  const int64_t nv = n * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nrhs);
+    const int k = kcols[r];
+    double2 acc = x[t];
+    for (int i = 0; i < k; ++i) {
+      const double2 z = to_c128(Z[(int64_t)i * nv + t]);
+      const double2 c = y[i * nrhs + r];
+      acc.x = fma(z.x, c.x, acc.x);
+      acc.x = fma(-z.y, c.y, acc.x);
+      acc.y = fma(z.x, c.y, acc.y);
+      acc.y = fma(z.y, c.x, acc.y);
+    }
+    x[t] = acc;
+  }
+}
+
+// r = b - A x (A x already in r); npart[blk][r] = partial |r|^2
+__global__ void k_residual(int64_t n, int nrhs, const double2* b, double2* r, double* npart) {
+  __shared__ double sh[256];
+  const int64_t nv = n * nrhs;
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x) * nrhs;
+  const int64_t t0 = blockIdx.x * chunk, t1 = min(nv, t0 + chunk);
+  // thread owns right-hand side q = threadIdx.x % nrhs when nrhs divides 256
+  double acc = 0;
+  const int q = threadIdx.x % nrhs;
+  const int lanes = 256 / nrhs;
+  const int li = threadIdx.x / nrhs;
+  if (li < lanes)
+    for (int64_t t = t0 + (int64_t)li * nrhs + q; t < t1; t += (int64_t)lanes * nrhs) {
+      const double2 v = make_double2(b[t].x - r[t].x, b[t].y - r[t].y);
+      r[t] = v;
+      acc = fma(v.x, v.x, acc);
+      acc = fma(v.y, v.y, acc);
+    }
+  sh[threadIdx.x] = (li < lanes) ? acc : 0.0;
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double s = 0;
+    for (int l = 0; l < lanes; ++l) s += sh[l * nrhs + threadIdx.x];
+    npart[(int64_t)blockIdx.x * nrhs + threadIdx.x] = s;
+  }
+}
+
+// norms from partials; restart set-up: v0 = r / beta, g = (beta, 0, ...)
+__global__ void k_restart(int nblk, int nrhs, int m, const double* npart, const double* bnorm, double tol,
+                          int32_t* active, double* beta_out, double2* g) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += npart[(int64_t)b * nrhs + r];
+  const double beta = sqrt(s);
+  beta_out[r] = beta;
+  for (int i = 0; i <= m; ++i) g[i * nrhs + r] = make_double2(0, 0);
+  g[r] = make_double2(beta, 0);
+  active[r] = (beta > tol * bnorm[r]) ? 1 : 0;
+}
+
+__global__ void k_scale_v0(int64_t nv, int nrhs, const double* beta, const int32_t* active, const double2* r, double2* v0) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t % nrhs);
+    const double inv = (active[q] && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
+    v0[t] = make_double2(r[t].x * inv, r[t].y * inv);
+  }
+}
+
+__global__ void k_copy_norm(int nrhs, const double* beta, double* bnorm) {
+  const int r = threadIdx.x;
+  if (r < nrhs) bnorm[r] = beta[r];
+}
+
+template <int RP>
+static void launch_dots(Workspace& W, int64_t n, int nvec, int with_norm, const double2* V, cudaStream_t s) {
+  k_dots<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, with_norm, V, W.w.p, W.active.p, W.hpart.p);
+}
+template <int RP>
+static void launch_update(Workspace& W, int64_t n, int nvec, cudaStream_t s) {
+  k_orth_update<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, W.V.p, W.h2.p, W.active.p, W.w.p, W.npart.p);
+}
+
+static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s) {
+  const int nr = W.nrhs;
+  if (nr <= 1) launch_dots<1>(W, n, nvec, with_norm, W.V.p, s);
+  else if (nr <= 2) launch_dots<2>(W, n, nvec, with_norm, W.V.p, s);
+  else if (nr <= 4) launch_dots<4>(W, n, nvec, with_norm, W.V.p, s);
+  else if (nr <= 8) launch_dots<8>(W, n, nvec, with_norm, W.V.p, s);
+  else if (nr <= 16) launch_dots<16>(W, n, nvec, with_norm, W.V.p, s);
+  else launch_dots<32>(W, n, nvec, with_norm, W.V.p, s);
+  MX_CHECK_LAUNCH();
+  const int total = nvec + with_norm;
+  k_reduce_dots<<<grid_for((int64_t)total * nr, 128), 128, 0, s>>>(W.nblk, total, nr, W.hpart.p, W.h2.p);
+  MX_CHECK_LAUNCH();
+}
+
+static void orth_update(Workspace& W, int64_t n, int nvec, cudaStream_t s) {
+  const int nr = W.nrhs;
+  if (nr <= 1) launch_update<1>(W, n, nvec, s);
+  else if (nr <= 2) launch_update<2>(W, n, nvec, s);
+  else if (nr <= 4) launch_update<4>(W, n, nvec, s);
+  else if (nr <= 8) launch_update<8>(W, n, nvec, s);
+  else if (nr <= 16) launch_update<16>(W, n, nvec, s);
+  else launch_update<32>(W, n, nvec, s);
+  MX_CHECK_LAUNCH();
+}
+
+static void true_residual(Problem& P, Workspace& W, cudaStream_t s) {
+  spmv(P, P.xi_prob, W.x.p, 0, W.r.p, W.nrhs, s);
+  k_residual<<<W.nblk, 256, 0, s>>>(W.n, W.nrhs, W.b.p, W.r.p, W.npart.p);
+  MX_CHECK_LAUNCH();
+}
+
+int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, int restart, int max_it,
+                mx_rhs_stats* stats) {
+  MX_REQUIRE(P.factored, MX_ENOTFACTORED, "mx_solve before mx_factor");
+  MX_REQUIRE(nrhs >= 1 && nrhs <= 32, MX_EINVAL, "nrhs must be in 1..32 per batch");
+  MX_REQUIRE(max_it >= 1, MX_EINVAL, "max_it must be >= 1");
+  cudaStream_t s = P.stream;
+  const int m = restart > 0 ? std::min(restart, max_it) : max_it;
+  Workspace& W = workspace(P, nrhs, m);
+  const int64_t n = P.fine.n_dof, nv = n * nrhs;
+  const bool mixed = P.precision == MX_MIXED;
+  const int ztype = mixed ? 1 : 0;
+  const size_t zsz = W.zsz;
+  int64_t launches = 0;
+  std::vector<int32_t> its(nrhs, 0), done(nrhs, 0), kcols(nrhs, 0);
+  std::vector<double> rel(nrhs, 1.0), estv(nrhs, 1.0), bn(nrhs, 0.0);
+  DevBuf<int32_t> dk(nrhs);
+  DevBuf<double> beta(nrhs);
+
+  MX_CUDA(cudaMemcpyAsync(W.b.p, b, nv * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  MX_CUDA(cudaMemsetAsync(W.x.p, 0, nv * sizeof(double2), s));
+  // ||b||: residual of x = 0
+  MX_CUDA(cudaMemsetAsync(W.r.p, 0, nv * sizeof(double2), s));
+  k_residual<<<W.nblk, 256, 0, s>>>(n, nrhs, W.b.p, W.r.p, W.npart.p);
+  MX_CUDA(cudaMemsetAsync(W.active.p, 0, nrhs * 4, s));
+  k_restart<<<1, 32, 0, s>>>(W.nblk, nrhs, m, W.npart.p, W.bnorm.p, -1.0, W.active.p, beta.p, W.g.p);
+  k_copy_norm<<<1, 32, 0, s>>>(nrhs, beta.p, W.bnorm.p);
+  launches += 3;
+  MX_CHECK_LAUNCH();
+  MX_CUDA(cudaMemcpyAsync(bn.data(), W.bnorm.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  // zero right-hand sides converge at once with x = 0
+  std::vector<int32_t> act(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    act[r] = bn[r] > 0;
+    if (!act[r]) { done[r] = 1; rel[r] = 0; estv[r] = 0; }
+  }
+  MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
+  k_scale_v0<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p);
+  MX_CHECK_LAUNCH();
+  ++launches;
+
+  int total_its = 0, restarts = 0;
+  const unsigned gv = grid_for(nv, 256);
+  while (std::any_of(act.begin(), act.end(), [](int32_t a) { return a != 0; })) {
+    std::vector<int32_t> start_active = act;
+    for (int j = 0; j < m; ++j) {
+      unsigned char* zj = W.Z.p + (size_t)j * nv * zsz;
+      // z_j = B^{-1} v_j ; w = A z_j
+      precond_apply(P, W.V.p + (int64_t)j * nv, zj, ztype, nrhs, 3);
+      launches += 1 + (P.coarse_m ? 2 : 0) + 1;
+      spmv(P, P.xi_prob, zj, ztype, W.w.p, nrhs, s);
+      ++launches;
+      // Arnoldi: classical Gram-Schmidt, second pass when needed
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+          MX_CUDA(cudaMemcpyAsync(W.h_flags, W.flags.p, 8, cudaMemcpyDeviceToHost, s));
+          MX_CUDA(cudaStreamSynchronize(s));
+          if (!W.h_flags[1]) break;
+        }
+        dots(W, n, j + 1, pass == 0 ? 1 : 0, s);
+        orth_update(W, n, j + 1, s);
+        k_arnoldi_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, pass, W.h2.p, W.npart.p, W.H.p, W.wnorm0.p,
+                                          W.active.p, W.flags.p);
+        MX_CHECK_LAUNCH();
+        launches += 4;
+      }
+      k_normalize<<<gv, 256, 0, s>>>(nv, nrhs, j, m, W.H.p, W.active.p, W.w.p, W.V.p + (int64_t)(j + 1) * nv);
+      k_givens<<<1, 32, 0, s>>>(nrhs, j, m, tol, W.bnorm.p, W.H.p, W.cs.p, W.sn.p, W.g.p, W.active.p, W.est.p,
+                                W.flags.p);
+      MX_CHECK_LAUNCH();
+      launches += 2;
+      MX_CUDA(cudaMemcpyAsync(W.h_small, W.est.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
+      MX_CUDA(cudaStreamSynchronize(s));
+      ++total_its;
+      bool any = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!act[r]) continue;
+        its[r] += 1;
+        kcols[r] = j + 1;
+        estv[r] = W.h_small[r];
+        if (estv[r] <= tol || its[r] >= max_it) act[r] = 0;  // stop this right-hand side
+        any = any || act[r];
+      }
+      MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
+      if (!any) break;
+    }
+    // x += Z y for the right-hand sides that ran in this cycle
+    for (int r = 0; r < nrhs; ++r) if (!start_active[r]) kcols[r] = 0;
+    MX_CUDA(cudaMemcpyAsync(dk.p, kcols.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
+    k_backsolve<<<1, 32, 0, s>>>(nrhs, m, dk.p, W.H.p, W.g.p, W.y.p);
+    if (mixed) k_update_x<float2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const float2*)W.Z.p, W.y.p, W.x.p);
+    else k_update_x<double2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const double2*)W.Z.p, W.y.p, W.x.p);
+    MX_CHECK_LAUNCH();
+    true_residual(P, W, s);
+    launches += 4;
+    // restart set-up for every right-hand side that is not finished
+    k_restart<<<1, 32, 0, s>>>(W.nblk, nrhs, m, W.npart.p, W.bnorm.p, tol, W.active.p, beta.p, W.g.p);
+    MX_CHECK_LAUNCH();
+    ++launches;
+    MX_CUDA(cudaMemcpyAsync(W.h_small, beta.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
+    MX_CUDA(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (done[r]) { act[r] = 0; continue; }
+      rel[r] = W.h_small[r] / bn[r];
+      if (rel[r] <= tol || its[r] >= max_it) {
+        done[r] = 1;
+        act[r] = 0;
+      } else {
+        act[r] = 1;
+        any = true;
+      }
+    }
+    if (!any) break;
+    ++restarts;
+    MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
+    k_scale_v0<<<gv, 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p);
+    MX_CHECK_LAUNCH();
+    ++launches;
+  }
+  MX_CUDA(cudaMemcpyAsync(x, W.x.p, nv * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  int rc = MX_OK;
+  int maxits = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    const bool ok = rel[r] <= tol;
+    if (!ok) rc = MX_ENOCONV;
+    maxits = std::max(maxits, its[r]);
+    if (stats) {
+      stats[r].iterations = its[r];
+      stats[r].converged = ok ? 1 : 0;
+      stats[r].rel_residual = rel[r];
+      stats[r].rel_estimate = estv[r];
+    }
+  }
+  P.timing.solve_launches = launches;
+  P.timing.restarts = restarts;
+  P.timing.max_iterations = maxits;
+  (void)total_its;
+  return rc;
+}
+
+}  // namespace mx

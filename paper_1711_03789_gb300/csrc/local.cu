@@ -1,0 +1,527 @@
+// Local subdomain matrices A^l = R^l A_{xi_prec} (R^l)^T (Eq. 3.3), their batched LU
+// factorisation and the local solves of the additive Schwarz preconditioner (Eq. 3.4).
+//
+// Storage. In the vertex-major DOF order each minor is banded with half-bandwidth b_l
+// (a few hundred for 5^3-cell boxes, against n_l ~ 2000). LU without pivoting creates no
+// fill outside the band of a banded matrix, so the band-limited factorisation below
+// produces exactly the factors of the dense no-pivot LU; the entries it skips are exact
+// zeros. Matrices are stored LAPACK-band style: element (i, j), |i - j| <= b, at
+//   off_l + j * ldab_l + (b_l + i - j),   ldab_l = 2 b_l + 1 rounded up to a multiple of 4,
+// so every column's band is contiguous. Coercivity (Lemma 2.2) keeps every pivot of the
+// no-pivot LU away from zero for xi_prec != 0 (Sec. 3.3).
+//
+// Factorisation: right-looking blocked LU over the band, NB columns per step, three
+// kernels per step for the whole batch (diagonal block, panels, trailing update).
+// Local solves: forward/backward substitution on the band with a sliding window of the
+// right-hand side block in shared memory; the gather R^l v is fused into the window load.
+#include "problem.cuh"
+
+namespace mx {
+
+constexpr int NB = LU_NB;  // columns per factorisation step
+
+// ---- bandwidth and extraction ---------------------------------------------------------
+__device__ inline int find_sub(const int64_t* offsets, int n_sub, int64_t q) {
+  int lo = 0, hi = n_sub - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct ExtractArgs {
+  int n_sub;
+  int64_t sum_local;
+  const int64_t* offsets;
+  const int32_t* lists;
+  const int32_t* inv_ptr;
+  const int32_t* inv_pos;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* K;
+  const double* M;
+  double sr, si;  // s = k^2 + i xi_prec
+  int32_t* band;  // [n_sub] (bandwidth pass)
+  const int32_t* ld;
+  const int64_t* moff;
+  void* out;
+};
+
+template <typename T2, bool WRITE>
+__global__ void k_extract(ExtractArgs a) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < a.sum_local;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int l = find_sub(a.offsets, a.n_sub, q);
+    const int64_t lo = a.offsets[l], hi = a.offsets[l + 1];
+    const int i = (int)(q - lo);
+    const int32_t g = a.lists[q];
+    int bmax = 0;
+    int bw = 0;
+    int ldl = 0;
+    int64_t off = 0;
+    if (WRITE) { bw = a.band[l]; ldl = a.ld[l]; off = a.moff[l]; }
+    for (int32_t e = a.rowptr[g]; e < a.rowptr[g + 1]; ++e) {
+      const int32_t c = a.col[e];
+      int j = -1;
+      for (int32_t t = a.inv_ptr[c]; t < a.inv_ptr[c + 1]; ++t) {
+        const int32_t p = a.inv_pos[t];
+        if (p >= lo && p < hi) { j = (int)(p - lo); break; }
+      }
+      if (j < 0) continue;
+      if (!WRITE) {
+        bmax = max(bmax, abs(i - j));
+      } else {
+        const double re = a.K[e] - a.sr * a.M[e];
+        const double im = -a.si * a.M[e];
+        T2* A = reinterpret_cast<T2*>(a.out);
+        A[bidx(off, ldl, bw, i, j)] = conv<T2>(make_double2(re, im));
+      }
+    }
+    if (!WRITE) atomicMax(&a.band[l], bmax);
+  }
+}
+
+// ---- batched band LU ----------------------------------------------------------------
+// Status words: status[0] = number of zero / non-finite pivots met.
+template <typename T2>
+__global__ void k_lu_diag(BandBatch B, T2* A, int k0, int32_t* status) {
+  __shared__ T2 s[NB][NB + 1];
+  const int m = blockIdx.x;
+  const int n = B.n[m], b = B.b[m], ld = B.ld[m];
+  const int64_t off = B.off[m];
+  if (k0 >= n) return;
+  const int kb = min(NB, n - k0);
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int i = t % NB, j = t / NB;
+    T2 v = czero<T2>();
+    if (i < kb && j < kb && abs(i - j) <= b) v = A[bidx(off, ld, b, k0 + i, k0 + j)];
+    s[i][j] = v;
+  }
+  __syncthreads();
+  for (int k = 0; k < kb; ++k) {
+    const T2 piv = s[k][k];
+    const auto p2 = cabs2(piv);
+    if (threadIdx.x == 0 && !(p2 > 0 && p2 < INFINITY)) atomicAdd(status, 1);
+    const T2 inv = crcp(piv);
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < kb; i += blockDim.x) s[i][k] = cmul(s[i][k], inv);
+    __syncthreads();
+    const int w = kb - k - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int i = k + 1 + t % w, j = k + 1 + t / w;
+      T2 v = s[i][j];
+      cfms(v, s[i][k], s[k][j]);
+      s[i][j] = v;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
+    const int i = t % kb, j = t / kb;
+    if (abs(i - j) <= b) A[bidx(off, ld, b, k0 + i, k0 + j)] = s[i][j];
+  }
+}
+
+// Panels: rows below the block get L21 = A21 U11^{-1}; columns right of it get
+// U12 = L11^{-1} A12. blockIdx.y < row chunks: rows; else columns.
+template <typename T2>
+__global__ void k_lu_panel(BandBatch B, T2* A, int k0) {
+  __shared__ T2 s[NB][NB + 1];
+  const int m = blockIdx.x;
+  const int n = B.n[m], b = B.b[m], ld = B.ld[m];
+  const int64_t off = B.off[m];
+  if (k0 >= n) return;
+  const int kb = min(NB, n - k0);
+  const int k1 = k0 + kb;
+  const int span = min(n, k1 + b) - k1;  // rows / columns within the band of the block
+  if (span <= 0) return;
+  const int chunks = (span + blockDim.x - 1) / blockDim.x;
+  if ((int)blockIdx.y >= 2 * chunks) return;
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int i = t % NB, j = t / NB;
+    T2 v = czero<T2>();
+    if (i < kb && j < kb && abs(i - j) <= b) v = A[bidx(off, ld, b, k0 + i, k0 + j)];
+    s[i][j] = v;
+  }
+  __syncthreads();
+  const bool rows = (int)blockIdx.y < chunks;
+  const int idx = ((rows ? blockIdx.y : blockIdx.y - chunks) * blockDim.x) + threadIdx.x;
+  if (idx >= span) return;
+  T2 x[NB];
+  if (rows) {
+    const int i = k1 + idx;
+    for (int k = 0; k < kb; ++k) x[k] = (i - (k0 + k) <= b) ? A[bidx(off, ld, b, i, k0 + k)] : czero<T2>();
+    for (int k = 0; k < kb; ++k) {  // x U11 = a
+      T2 v = x[k];
+      for (int j = 0; j < k; ++j) cfms(v, x[j], s[j][k]);
+      x[k] = cmul(v, crcp(s[k][k]));
+    }
+    for (int k = 0; k < kb; ++k)
+      if (i - (k0 + k) <= b) A[bidx(off, ld, b, i, k0 + k)] = x[k];
+  } else {
+    const int j = k1 + idx;
+    for (int k = 0; k < kb; ++k) x[k] = (j - (k0 + k) <= b) ? A[bidx(off, ld, b, k0 + k, j)] : czero<T2>();
+    for (int k = 0; k < kb; ++k) {  // L11 y = a (unit lower)
+      T2 v = x[k];
+      for (int j2 = 0; j2 < k; ++j2) cfms(v, s[k][j2], x[j2]);
+      x[k] = v;
+    }
+    for (int k = 0; k < kb; ++k)
+      if (j - (k0 + k) <= b) A[bidx(off, ld, b, k0 + k, j)] = x[k];
+  }
+}
+
+// Trailing update A22 -= L21 U12 over the band window, 64 x 64 tiles, 256 threads with
+// 4 x 4 outputs each. blockIdx.y enumerates tiles of the (span x span) window.
+template <typename T2>
+__global__ void __launch_bounds__(256) k_lu_update(BandBatch B, T2* A, int k0) {
+  __shared__ T2 sl[NB][64 + 1];
+  __shared__ T2 su[NB][64 + 1];
+  const int m = blockIdx.x;
+  const int n = B.n[m], b = B.b[m], ld = B.ld[m];
+  const int64_t off = B.off[m];
+  if (k0 >= n) return;
+  const int kb = min(NB, n - k0);
+  const int k1 = k0 + kb;
+  const int span = min(n, k1 + b) - k1;
+  if (span <= 0) return;
+  const int tiles = (span + 63) / 64;
+  if ((int)blockIdx.y >= tiles * tiles) return;
+  const int ti = blockIdx.y % tiles, tj = blockIdx.y / tiles;
+  const int i0 = k1 + 64 * ti, j0 = k1 + 64 * tj;
+  // skip tiles entirely outside the band
+  if (i0 - (j0 + 63) > b || j0 - (i0 + 63) > b) return;
+  for (int t = threadIdx.x; t < NB * 64; t += blockDim.x) {
+    const int r = t % 64, k = t / 64;
+    const int i = i0 + r, kk = k0 + k;
+    sl[k][r] = (k < kb && i < n && i - kk <= b) ? A[bidx(off, ld, b, i, kk)] : czero<T2>();
+    const int j = j0 + r;
+    su[k][r] = (k < kb && j < n && j - kk <= b) ? A[bidx(off, ld, b, kk, j)] : czero<T2>();
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = czero<T2>();
+  for (int k = 0; k < kb; ++k) {
+    T2 lv[4], uv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) lv[a] = sl[k][tx + 16 * a];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) uv[c] = su[k][ty + 16 * c];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cfma(acc[a][c], lv[a], uv[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = j0 + ty + 16 * c;
+    if (j >= n) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = i0 + tx + 16 * a;
+      if (i >= n || abs(i - j) > b) continue;
+      T2* p = A + bidx(off, ld, b, i, j);
+      *p = csub(*p, acc[a][c]);
+    }
+  }
+}
+
+template <typename T2>
+void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s) {
+  const int chunks = (max_span + 255) / 256;
+  const int tiles = (max_span + 63) / 64;
+  for (int k0 = 0; k0 < max_n; k0 += NB) {
+    k_lu_diag<T2><<<B.count, 256, 0, s>>>(B, A, k0, status);
+    MX_CHECK_LAUNCH();
+    if (max_span > 0) {
+      k_lu_panel<T2><<<dim3(B.count, 2 * chunks), 256, 0, s>>>(B, A, k0);
+      MX_CHECK_LAUNCH();
+      k_lu_update<T2><<<dim3(B.count, tiles * tiles), 256, 0, s>>>(B, A, k0);
+      MX_CHECK_LAUNCH();
+    }
+  }
+}
+
+template void band_lu<double2>(const BandBatch&, double2*, int, int, int32_t*, cudaStream_t);
+template void band_lu<float2>(const BandBatch&, float2*, int, int, int32_t*, cudaStream_t);
+
+// ---- host: extraction and factorisation -------------------------------------------
+static int round4(int x) { return (x + 3) & ~3; }
+
+void extract_minors(Problem& P) {
+  cudaStream_t s = P.stream;
+  const size_t esz = P.precision == MX_MIXED ? sizeof(float2) : sizeof(double2);
+  ExtractArgs a{};
+  a.n_sub = P.n_sub;
+  a.sum_local = P.sum_local;
+  a.offsets = P.offsets.p;
+  a.lists = P.lists.p;
+  a.inv_ptr = P.inv_ptr.p;
+  a.inv_pos = P.inv_pos.p;
+  a.rowptr = P.A.rowptr.p;
+  a.col = P.A.col.p;
+  a.K = P.A.K.p;
+  a.M = P.A.M.p;
+  a.sr = P.k * P.k;
+  a.si = P.xi_prec;
+  DevBuf<int32_t> band(P.n_sub);
+  MX_CUDA(cudaMemsetAsync(band.p, 0, band.bytes(), s));
+  a.band = band.p;
+  k_extract<float2, false><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a);
+  MX_CHECK_LAUNCH();
+  P.h_band.assign(P.n_sub, 0);
+  MX_CUDA(cudaMemcpyAsync(P.h_band.data(), band.p, band.bytes(), cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  P.h_ld.assign(P.n_sub, 0);
+  P.h_mat_off.assign(P.n_sub + 1, 0);
+  for (int l = 0; l < P.n_sub; ++l) {
+    if (P.dense_local) P.h_band[l] = P.h_nl[l] - 1;
+    P.h_ld[l] = round4(2 * P.h_band[l] + 1);
+    P.h_mat_off[l + 1] = P.h_mat_off[l] + (int64_t)P.h_ld[l] * P.h_nl[l];
+  }
+  P.band.alloc(P.n_sub);
+  P.ld.alloc(P.n_sub);
+  P.mat_off.alloc(P.n_sub + 1);
+  MX_CUDA(cudaMemcpyAsync(P.band.p, P.h_band.data(), P.n_sub * 4, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemcpyAsync(P.ld.p, P.h_ld.data(), P.n_sub * 4, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemcpyAsync(P.mat_off.p, P.h_mat_off.data(), (P.n_sub + 1) * 8, cudaMemcpyHostToDevice, s));
+  const int64_t elems = P.h_mat_off[P.n_sub];
+  P.factors.alloc(elems * esz);
+  MX_CUDA(cudaMemsetAsync(P.factors.p, 0, P.factors.bytes(), s));
+  a.band = P.band.p;
+  a.ld = P.ld.p;
+  a.moff = P.mat_off.p;
+  a.out = P.factors.p;
+  if (P.precision == MX_MIXED)
+    k_extract<float2, true><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a);
+  else
+    k_extract<double2, true><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a);
+  MX_CHECK_LAUNCH();
+  MX_CUDA(cudaStreamSynchronize(s));
+  P.minors_ready = true;
+  P.factored = false;
+}
+
+void factor_local(Problem& P) {
+  if (!P.minors_ready) extract_minors(P);
+  BandBatch B{P.n_sub, P.nl.p, P.band.p, P.ld.p, P.mat_off.p};
+  int max_span = 0;
+  for (int l = 0; l < P.n_sub; ++l) max_span = std::max(max_span, std::min(P.h_band[l], P.h_nl[l]));
+  if (P.precision == MX_MIXED)
+    band_lu<float2>(B, reinterpret_cast<float2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream);
+  else
+    band_lu<double2>(B, reinterpret_cast<double2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream);
+  MX_CUDA(cudaStreamSynchronize(P.stream));
+  P.minors_ready = false;
+  P.factored = true;
+}
+
+// ---- local solves -------------------------------------------------------------------
+// One block per (subdomain, group of G right-hand sides). The window holds WIN rows of
+// the right-hand side block (slot = row % WIN, WIN >= b + NB). Forward: unit lower L;
+// backward: upper U. Rows leaving the forward window are the intermediate y, written to
+// `out` and read back by the backward sweep, which overwrites them with z_l.
+struct SolveArgs {
+  int n_sub, nrhs;
+  int64_t n_dof;
+  const int64_t* offsets;  // positions of subdomain rows
+  const int32_t* lists;
+  const int32_t* nl;
+  const int32_t* band;
+  const int32_t* ld;
+  const int64_t* moff;
+  const void* factors;
+  const void* v;  // [n][nrhs] c128 or c64 (right-hand side index fastest)
+  int vtype;
+  void* out;      // [sum_local][nrhs] of T2
+  int win;        // window rows
+};
+
+template <typename T2>
+__device__ inline T2 load_v(const void* v, int vtype, int64_t idx) {
+  if (vtype == 0) return conv<T2>(reinterpret_cast<const double2*>(v)[idx]);
+  const float2 f = reinterpret_cast<const float2*>(v)[idx];
+  return conv<T2>(make_double2(f.x, f.y));
+}
+
+template <typename T2, int G>
+__global__ void __launch_bounds__(256) k_local_solve(SolveArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  T2* W = reinterpret_cast<T2*>(smem_raw);  // [win][G]
+  const int groups = (a.nrhs + G - 1) / G;
+  const int l = blockIdx.x / groups;
+  const int g0 = (blockIdx.x % groups) * G;
+  const int gn = min(G, a.nrhs - g0);
+  const int n = a.nl[l], b = a.band[l], ld = a.ld[l];
+  const int64_t off = a.moff[l], pos0 = a.offsets[l];
+  const T2* F = reinterpret_cast<const T2*>(a.factors);
+  T2* out = reinterpret_cast<T2*>(a.out);
+  const int win = a.win;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  // ---- forward sweep: L y = R^l v
+  for (int t = tid; t < min(n, win) * G; t += nt) {
+    const int i = t / G, g = t % G;
+    W[(i % win) * G + g] = (g < gn) ? load_v<T2>(a.v, a.vtype, (int64_t)a.lists[pos0 + i] * a.nrhs + g0 + g) : czero<T2>();
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += NB) {
+    const int c1 = min(c0 + NB, n);
+    // diagonal block (unit lower), column by column
+    for (int k = c0; k < c1 - 1; ++k) {
+      for (int t = tid; t < (c1 - k - 1) * G; t += nt) {
+        const int i = k + 1 + t / G, g = t % G;
+        if (i - k <= b) {
+          T2 v = W[(i % win) * G + g];
+          cfms(v, F[bidx(off, ld, b, i, k)], W[(k % win) * G + g]);
+          W[(i % win) * G + g] = v;
+        }
+      }
+      __syncthreads();
+    }
+    // rows below the block within the band
+    const int r1 = min(n, c1 + b);
+    for (int i = c1 + tid; i < r1; i += nt) {
+      T2 acc[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) acc[g] = W[(i % win) * G + g];
+      const int kstart = max(c0, i - b);
+      for (int k = kstart; k < c1; ++k) {
+        const T2 lik = F[bidx(off, ld, b, i, k)];
+#pragma unroll
+        for (int g = 0; g < G; ++g) cfms(acc[g], lik, W[(k % win) * G + g]);
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) W[(i % win) * G + g] = acc[g];
+    }
+    __syncthreads();
+    // retire rows c0..c1-1 (y), load rows entering the window
+    for (int t = tid; t < (c1 - c0) * G; t += nt) {
+      const int i = c0 + t / G, g = t % G;
+      const T2 y = W[(i % win) * G + g];
+      if (g < gn) out[(pos0 + i) * a.nrhs + g0 + g] = y;
+      const int inew = i + win;
+      if (inew < n)
+        W[(inew % win) * G + g] = (g < gn) ? load_v<T2>(a.v, a.vtype, (int64_t)a.lists[pos0 + inew] * a.nrhs + g0 + g) : czero<T2>();
+    }
+    __syncthreads();
+  }
+
+  // ---- backward sweep: U z = y, blocks from the bottom
+  const int nblk = (n + NB - 1) / NB;
+  const int top0 = max(0, n - win);
+  for (int t = tid; t < (n - top0) * G; t += nt) {
+    const int i = top0 + t / G, g = t % G;
+    W[(i % win) * G + g] = (g < gn) ? out[(pos0 + i) * a.nrhs + g0 + g] : czero<T2>();
+  }
+  __syncthreads();
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int c0 = blk * NB, c1 = min(c0 + NB, n);
+    for (int k = c1 - 1; k >= c0; --k) {
+      // x_k = r_k / U_kk, then r_i -= U_ik x_k for c0 <= i < k
+      if (tid < G) {
+        const T2 d = F[bidx(off, ld, b, k, k)];
+        W[(k % win) * G + tid] = cmul(W[(k % win) * G + tid], crcp(d));
+      }
+      __syncthreads();
+      for (int t = tid; t < (k - c0) * G; t += nt) {
+        const int i = c0 + t / G, g = t % G;
+        if (k - i <= b) {
+          T2 v = W[(i % win) * G + g];
+          cfms(v, F[bidx(off, ld, b, i, k)], W[(k % win) * G + g]);
+          W[(i % win) * G + g] = v;
+        }
+      }
+      __syncthreads();
+    }
+    // rows above the block within the band
+    const int r0 = max(0, c0 - b);
+    for (int i = r0 + tid; i < c0; i += nt) {
+      T2 acc[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) acc[g] = W[(i % win) * G + g];
+      const int kend = min(c1, i + b + 1);
+      for (int k = c0; k < kend; ++k) {
+        const T2 uik = F[bidx(off, ld, b, i, k)];
+#pragma unroll
+        for (int g = 0; g < G; ++g) cfms(acc[g], uik, W[(k % win) * G + g]);
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) W[(i % win) * G + g] = acc[g];
+    }
+    __syncthreads();
+    for (int t = tid; t < (c1 - c0) * G; t += nt) {
+      const int i = c0 + t / G, g = t % G;
+      if (g < gn) out[(pos0 + i) * a.nrhs + g0 + g] = W[(i % win) * G + g];
+      const int inew = i - win;
+      if (inew >= 0)
+        W[(inew % win) * G + g] = (g < gn) ? out[(pos0 + inew) * a.nrhs + g0 + g] : czero<T2>();
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T2, int G>
+static void launch_local_solve(const SolveArgs& a, int win, cudaStream_t s) {
+  const size_t smem = (size_t)win * G * sizeof(T2);
+  static bool configured = false;
+  if (!configured) {
+    MX_CUDA(cudaFuncSetAttribute(k_local_solve<T2, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    configured = true;
+  }
+  MX_REQUIRE(smem <= 227 * 1024, MX_EINVAL, "local solve window exceeds shared memory");
+  const int groups = (a.nrhs + G - 1) / G;
+  k_local_solve<T2, G><<<a.n_sub * groups, 256, smem, s>>>(a);
+  MX_CHECK_LAUNCH();
+}
+
+void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs) {
+  MX_REQUIRE(P.factored, MX_ENOTFACTORED, "local solves before factor");
+  SolveArgs a{};
+  a.n_sub = P.n_sub;
+  a.nrhs = nrhs;
+  a.n_dof = P.fine.n_dof;
+  a.offsets = P.offsets.p;
+  a.lists = P.lists.p;
+  a.nl = P.nl.p;
+  a.band = P.band.p;
+  a.ld = P.ld.p;
+  a.moff = P.mat_off.p;
+  a.factors = P.factors.p;
+  a.v = v;
+  a.vtype = vtype;
+  a.out = loc;
+  int bmax = 0;
+  for (int l = 0; l < P.n_sub; ++l) bmax = std::max(bmax, std::min(P.h_band[l], P.h_nl[l]));
+  a.win = std::min(P.max_local, bmax + NB);
+  const bool mixed = P.precision == MX_MIXED;
+  // right-hand sides per block: the window must fit in shared memory
+  const size_t esz = mixed ? 8 : 16;
+  int G = 1;
+  while (G < nrhs && G < 16) G *= 2;
+  while (G > 1 && (size_t)a.win * G * esz > 100 * 1024) G /= 2;
+  MX_REQUIRE((size_t)a.win * esz <= 200 * 1024, MX_EINVAL, "subdomain bandwidth too large for the local solve window");
+  if (mixed) {
+    switch (G) {
+      case 16: launch_local_solve<float2, 16>(a, a.win, P.stream); break;
+      case 8: launch_local_solve<float2, 8>(a, a.win, P.stream); break;
+      case 4: launch_local_solve<float2, 4>(a, a.win, P.stream); break;
+      case 2: launch_local_solve<float2, 2>(a, a.win, P.stream); break;
+      default: launch_local_solve<float2, 1>(a, a.win, P.stream); break;
+    }
+  } else {
+    switch (G) {
+      case 16: launch_local_solve<double2, 16>(a, a.win, P.stream); break;
+      case 8: launch_local_solve<double2, 8>(a, a.win, P.stream); break;
+      case 4: launch_local_solve<double2, 4>(a, a.win, P.stream); break;
+      case 2: launch_local_solve<double2, 2>(a, a.win, P.stream); break;
+      default: launch_local_solve<double2, 1>(a, a.win, P.stream); break;
+    }
+  }
+}
+
+}  // namespace mx

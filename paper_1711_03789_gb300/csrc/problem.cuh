@@ -1,0 +1,143 @@
+// Internal state of one assembled problem and the declarations of the kernels'
+// host launchers, grouped by step of the path.
+#pragma once
+
+#include "common.cuh"
+
+namespace mx {
+
+// Kuhn mesh of the unit cube with n cells per side and its PEC-interior edge DOFs
+// (Sec. 2.2). Edge (v, d) runs from vertex v to v + DIRS[d]; its key is 7 v + d.
+struct MeshDev {
+  int n = 0;
+  int64_t n_dof = 0;
+  DevBuf<int32_t> edge_dof;  // [(n+1)^3 * 7]  DOF of edge key, -1 if PEC or absent
+  DevBuf<int32_t> dof_key;   // [n_dof]
+  DevBuf<int32_t> tet2dof;   // [6 n^3 * 6]
+};
+
+// Real CSR with the curl-curl (K) and mass (M) values on one pattern.
+struct CsrKM {
+  int64_t rows = 0, cols = 0, nnz = 0;
+  DevBuf<int32_t> rowptr, col;
+  DevBuf<double> K, M;
+};
+
+// Plain CSR with one real value per entry (R^0 and its transpose).
+struct CsrR {
+  int64_t rows = 0, cols = 0, nnz = 0;
+  DevBuf<int32_t> rowptr, col;
+  DevBuf<double> val;
+};
+
+struct Timing {
+  double build_ms = 0, factor_ms = 0, solve_ms = 0;
+  int64_t solve_launches = 0;
+  int restarts = 0, max_iterations = 0;
+};
+
+struct Workspace;  // solve buffers (krylov.cu)
+
+// A batch of band matrices (LAPACK band layout, see local.cu).
+constexpr int LU_NB = 32;
+struct BandBatch {
+  int count;
+  const int32_t* n;    // [count]
+  const int32_t* b;    // [count] half-bandwidth
+  const int32_t* ld;   // [count] leading dimension (>= 2 b + 1)
+  const int64_t* off;  // [count] element offsets
+};
+
+__host__ __device__ inline int64_t bidx(int64_t off, int ld, int b, int i, int j) {
+  return off + (int64_t)j * ld + (b + i - j);
+}
+
+struct Problem {
+  // parameters
+  int n = 0, core = 0, overlap = 0, coarse_m = 0, precision = MX_MIXED;
+  double k = 0, xi_prob = 0, xi_prec = 0;
+  cudaStream_t stream = nullptr;
+
+  // fine and coarse meshes and matrices
+  MeshDev fine, coarse;
+  CsrKM A, Ac;  // A_xi = K - (k^2 + i xi) M
+
+  // subdomains (Eq. 3.1): boxes, sorted index lists, inverse map DOF -> positions
+  int n_sub = 0, n_per_axis = 0;
+  std::vector<int32_t> box;        // [n_sub][6] lo xyz, hi xyz (vertex indices)
+  std::vector<int64_t> h_offsets;  // [n_sub + 1]
+  std::vector<int32_t> h_nl;       // [n_sub]
+  int max_local = 0;
+  int64_t sum_local = 0;
+  DevBuf<int64_t> offsets;         // [n_sub + 1]
+  DevBuf<int32_t> nl;              // [n_sub]
+  DevBuf<int32_t> lists;           // [sum_local]
+  DevBuf<int32_t> inv_ptr;         // [n_dof + 1]
+  DevBuf<int32_t> inv_pos;         // [sum_local]
+
+  // local factors: dense column-major n_l x n_l with leading dimension ld_l,
+  // element type float2 (mixed) or double2 (plain), matrix l at mat_off[l] elements.
+  bool dense_local = false;        // force b_l = n_l - 1 (full dense storage)
+  std::vector<int32_t> h_band;     // [n_sub] half-bandwidths
+  DevBuf<int32_t> band;
+  std::vector<int64_t> h_mat_off;  // [n_sub + 1]
+  std::vector<int32_t> h_ld;
+  DevBuf<int64_t> mat_off;
+  DevBuf<int32_t> ld;
+  DevBuf<unsigned char> factors;
+  bool factored = false;
+  bool minors_ready = false;
+
+  // coarse space (Eq. 3.2): R^0 [n_c x n], its transpose, dense A^0 and its LU (FP64),
+  // and a c64 copy of the factors for the mixed-precision coarse solve.
+  CsrR R0, R0T;
+  int64_t n_c = 0;
+  int coarse_band = 0;
+  int64_t ld_c = 0;
+  DevBuf<double2> A0;     // band storage [n_c * ld_c], LU in place after factor
+  DevBuf<float2> A0f;     // c64 copy of the factors (mixed)
+  DevBuf<int32_t> c_meta; // n, b, ld of the coarse band matrix (device)
+  DevBuf<int64_t> c_off;
+  DevBuf<int32_t> status; // [4] device error words: 0 local pivot, 1 coarse pivot, 2 timeout
+
+  Workspace* ws = nullptr;
+  Timing timing;
+
+  ~Problem();
+};
+
+// ---- mesh.cu ------------------------------------------------------------------------
+void build_mesh(MeshDev& m, int n, cudaStream_t s);
+void build_subdomains(Problem& P);
+
+// ---- assemble.cu --------------------------------------------------------------------
+void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s);
+void load_vector(const Problem& P, int nrhs, int nbumps, const double* h_centres,
+                 const double* h_pol, double width, double2* f /* [nrhs][n] device */);
+void build_coarse_restriction(Problem& P);
+
+// ---- local.cu -----------------------------------------------------------------------
+void extract_minors(Problem& P);
+void factor_local(Problem& P);
+template <typename T2>
+void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s);
+// z_l = (A^l)^{-1} R^l v for every l, written at the subdomain positions of `loc`
+// (element type of the factors), v [nrhs][n] c128 or c64 (vtype 0: c128, 1: c64).
+void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs);
+
+// ---- coarse.cu ----------------------------------------------------------------------
+void factor_coarse(Problem& P);
+// y = (A^0)^{-1} R^0 v: coarse_rhs [nrhs][n_c] c128 workspace
+void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs);
+
+// ---- krylov.cu ----------------------------------------------------------------------
+// y = A_{xi} x; x c128 or c64 [nrhs][n] (xtype 0/1), y c128
+void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int nrhs,
+          cudaStream_t s);
+// z = B^{-1} v into z [nrhs][n] c128 (ztype 0) or c64 (ztype 1)
+void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, int levels);
+int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, int restart,
+                int max_it, mx_rhs_stats* stats);
+void free_workspace(Problem& P);
+
+}  // namespace mx

@@ -1,0 +1,227 @@
+"""GPU parity: every step of the path through the C ABI against the CPU oracle.
+
+Integer work (mesh, DOF numbering, subdomain lists, inverse map, CSR patterns) must be
+bit-exact; FP64 values within a few ulps of the matrix scale; mixed-precision results
+within bounds derived from c64 rounding; GMRES solutions within 1e-8 (plain) of the
+oracle when both run to a 1e-10 relative residual."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle.mesh import KuhnMesh
+from oracle import fem, dd
+from oracle.problem import Problem as OracleProblem
+
+pytestmark = pytest.mark.gpu
+
+mx = pytest.importorskip("paper_1711_03789_gb300")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _handle(n, k, xp, xq, core, ov, cm=0, prec=mx.MX_PLAIN_FP64):
+    return mx.Problem(n, k, xp, xq, core, ov, cm, prec)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 10])
+def test_mesh_integers_bit_exact(n):
+    with _handle(n, 2.0, 1.0, 1.0, max(1, n), 0) as P:
+        key, t2d = mx.mx_get_mesh(P.h, n)
+    m = KuhnMesh(n)
+    assert np.array_equal(key, m.dof_key.astype(np.int32))
+    assert np.array_equal(t2d, m.tet2dof.astype(np.int32))
+
+
+@pytest.mark.parametrize("n,core,ov", [(10, 5, 1), (12, 5, 1), (9, 4, 2), (6, 3, 0), (7, 7, 0)])
+def test_subdomain_lists_bit_exact(n, core, ov):
+    with _handle(n, 2.0, 1.0, 1.0, core, ov) as P:
+        off, lists, iptr, ipos = mx.mx_get_subdomains(P.h)
+    m = KuhnMesh(n)
+    boxes = dd.subdomain_boxes(n, core, ov)
+    assert len(off) == len(boxes) + 1
+    exp = [dd.local_dofs(m, lo, hi) for lo, hi in boxes]
+    for l, e in enumerate(exp):
+        assert np.array_equal(lists[off[l]:off[l + 1]], e.astype(np.int32)), l
+    # inverse map: positions of each DOF in increasing subdomain order
+    want = [[] for _ in range(m.n_dof)]
+    for l, e in enumerate(exp):
+        for j, g in enumerate(e):
+            want[g].append(off[l] + j)
+    assert np.array_equal(np.diff(iptr), [len(w) for w in want])
+    assert np.array_equal(ipos, np.concatenate([np.array(w, dtype=np.int32) for w in want]))
+
+
+@pytest.mark.parametrize("n", [2, 6, 10])
+def test_assembly(n):
+    with _handle(n, 2.0, 1.0, 1.0, n, 0) as P:
+        rowptr, col, K, M = mx.mx_get_csr(P.h)
+    m = KuhnMesh(n)
+    Ko, Mo = fem.assemble_KM(m)
+    assert np.array_equal(rowptr, Ko.indptr) and np.array_equal(col, Ko.indices)
+    assert np.array_equal(Mo.indptr, Ko.indptr) and np.array_equal(Mo.indices, Ko.indices)
+    assert np.abs(K - Ko.data).max() <= 1e-14 * np.abs(Ko.data).max()
+    assert np.abs(M - Mo.data).max() <= 1e-14 * np.abs(Mo.data).max()
+
+
+@pytest.mark.parametrize("n,m", [(4, 2), (6, 3), (10, 5), (8, 2)])
+def test_coarse_restriction(n, m):
+    with _handle(n, 2.0, 1.0, 1.0, n, 0, cm=m) as P:
+        rp, col, val = mx.mx_get_coarse_restriction(P.h)
+        rpc, colc, Kc, Mc = mx.mx_get_csr(P.h, 1)
+    R0 = dd.coarse_restriction(KuhnMesh(n), KuhnMesh(m))
+    R0.data[np.abs(R0.data) < 1e-13] = 0.0  # rounding residue where the exact entry is 0
+    R0.eliminate_zeros()
+    assert np.array_equal(rp, R0.indptr) and np.array_equal(col, R0.indices)
+    assert np.abs(val - R0.data).max() <= 1e-14
+    Ko, Mo = fem.assemble_KM(KuhnMesh(m))
+    assert np.array_equal(colc, Ko.indices)
+    assert np.abs(Kc - Ko.data).max() <= 1e-14 * np.abs(Ko.data).max()
+
+
+@pytest.mark.parametrize("n,nrhs", [(4, 1), (10, 3)])
+def test_load_vector(n, nrhs):
+    c, p = inputs.bump_batch(11, nrhs)
+    with _handle(n, 2.0, 1.0, 1.0, n, 0) as P:
+        f = P.load_vector(c, p, 0.1)
+        fd = torch.zeros((nrhs, P.n_dof), dtype=torch.complex128, device="cuda")
+        P.load_vector(c, p, 0.1, out=fd)
+    fo = fem.load_vector(KuhnMesh(n), fem.bump_field(c, p, 0.1))
+    assert np.abs(f.T - fo).max() <= 1e-13 * np.abs(fo).max()
+    assert np.array_equal(fd.cpu().numpy(), f)
+
+
+@pytest.mark.parametrize("n,nrhs,xi", [(5, 1, 0.0), (10, 4, 3.0), (12, 16, -2.0)])
+def test_spmv(n, nrhs, xi):
+    k = 3.0
+    x = inputs.random_complex(5, (nrhs, KuhnMesh(n).n_dof))
+    with _handle(n, k, xi, 1.0, 5, 1) as P:
+        y = P.spmv(x)
+        yd = P.spmv(torch.from_numpy(x).cuda()).cpu().numpy()
+    Ko, Mo = fem.assemble_KM(KuhnMesh(n))
+    A = fem.a_xi(Ko, Mo, k, xi)
+    ye = (A @ x.T).T
+    assert np.abs(y - ye).max() <= 1e-13 * np.abs(ye).max()
+    assert np.array_equal(y, yd)
+
+
+@pytest.mark.parametrize("prec", [mx.MX_PLAIN_FP64, mx.MX_MIXED])
+def test_local_minor_and_factor(prec):
+    n, k, xi = 10, 4.0, 4.0
+    m = KuhnMesh(n)
+    Ko, Mo = fem.assemble_KM(m)
+    A = fem.a_xi(Ko, Mo, k, xi)
+    S = dd.Schwarz(m, A, 5, 1)
+    with _handle(n, k, 0.0, xi, 5, 1, prec=prec) as P:
+        nl = [len(i) for i in S.idx]
+        minors = {l: mx.mx_get_local(P.h, l, nl[l]) for l in (0, 3, 7)}
+        P.factor()
+        factors = {l: mx.mx_get_local(P.h, l, nl[l]) for l in (0, 3, 7)}
+    tol_a = 4e-15 if prec == mx.MX_PLAIN_FP64 else 1e-7
+    tol_lu = 1e-12 if prec == mx.MX_PLAIN_FP64 else 2e-5
+    for l in minors:
+        Al = S.minor(l).toarray()
+        scale = np.abs(Al).max()
+        assert np.abs(minors[l] - Al).max() <= tol_a * scale
+        F = factors[l]
+        L = np.tril(F, -1) + np.eye(F.shape[0])
+        U = np.triu(F)
+        assert np.abs(L @ U - Al).max() <= tol_lu * scale
+
+
+@pytest.mark.parametrize("prec,levels,nrhs", [(mx.MX_PLAIN_FP64, 1, 1), (mx.MX_PLAIN_FP64, 3, 3),
+                                              (mx.MX_MIXED, 1, 2), (mx.MX_MIXED, 3, 16),
+                                              (mx.MX_PLAIN_FP64, 2, 2)])
+def test_preconditioner_apply(prec, levels, nrhs):
+    n, k, xi = 10, 5.0, 5.0
+    O = OracleProblem(n, k, 0.0, xi, 5, 1, coarse_m=5)
+    O.factor()
+    v = inputs.random_complex(9, (nrhs, O.n_dof))
+    lv = tuple(x for x, bit in ((1, 1), (0, 2)) if levels & bit)
+    ze = O.dd.apply(v.T, levels=lv).T
+    with _handle(n, k, 0.0, xi, 5, 1, cm=5, prec=prec) as P:
+        P.factor()
+        z = P.precond(v, levels=levels)
+    tol = 1e-11 if prec == mx.MX_PLAIN_FP64 else 1e-4
+    err = np.linalg.norm(z - ze) / np.linalg.norm(ze)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec,cm,nrhs", [(mx.MX_PLAIN_FP64, 0, 1), (mx.MX_PLAIN_FP64, 5, 2),
+                                          (mx.MX_MIXED, 0, 1), (mx.MX_MIXED, 5, 3)])
+def test_gmres_matches_oracle(prec, cm, nrhs):
+    """Config-1 problem (10^3 cells, k = xi = 6, 2x2x2 subdomains): both sides to 1e-10."""
+    n, k = 10, 6.0
+    c, p = inputs.bump_batch(1, nrhs)
+    O = OracleProblem(n, k, k, k, 5, 1, coarse_m=cm)
+    O.factor()
+    fo = O.load_vector(c, p, 0.1)
+    xo, ost = O.solve(fo, tol=1e-10, restart=0, max_it=300)
+    with _handle(n, k, k, k, 5, 1, cm=cm, prec=prec) as P:
+        P.factor()
+        f = P.load_vector(c, p, 0.1)
+        x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
+    assert rc == mx.MX_OK
+    for r in range(nrhs):
+        assert st[r]["converged"]
+        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
+        assert err <= 1e-8, (r, err)
+        res = np.linalg.norm(fo[:, r] - O.A @ x[r]) / np.linalg.norm(fo[:, r])
+        assert res <= 1.05e-10, res
+        if prec == mx.MX_PLAIN_FP64:
+            assert abs(st[r]["iterations"] - ost[r][0]) <= 1, (st[r], ost[r])
+
+
+def test_restarted_gmres():
+    n, k = 10, 6.0
+    c, p = inputs.bump_batch(2, 2)
+    O = OracleProblem(n, k, k, k, 5, 1)
+    O.factor()
+    fo = O.load_vector(c, p, 0.1)
+    xo, ost = O.solve(fo, tol=1e-9, restart=20, max_it=400)
+    with _handle(n, k, k, k, 5, 1) as P:
+        P.factor()
+        x, st, rc = P.solve(fo.T.copy(), tol=1e-9, restart=20, max_it=400)
+    assert rc == mx.MX_OK
+    for r in range(2):
+        assert np.linalg.norm(x[r] - xo[:, r]) <= 1e-7 * np.linalg.norm(xo[:, r])
+        assert abs(st[r]["iterations"] - ost[r][0]) <= 2
+
+
+def test_single_subdomain_one_iteration():
+    """One subdomain covering the cube with xi_prob = xi_prec: B^{-1} = A^{-1}."""
+    n, k = 4, 3.0
+    with _handle(n, k, k, k, 4, 0) as P:
+        P.factor()
+        b = inputs.random_complex(3, (1, P.n_dof))
+        x, st, rc = P.solve(b, tol=1e-10, max_it=10)
+    assert rc == mx.MX_OK and st[0]["iterations"] == 1
+
+
+def test_zero_rhs_and_errors():
+    with _handle(4, 3.0, 3.0, 3.0, 2, 1) as P:
+        with pytest.raises(mx.MxError) as e:
+            P.solve(np.ones((1, P.n_dof), dtype=np.complex128))
+        assert e.value.code == mx.MX_ENOTFACTORED
+        P.factor()
+        x, st, rc = P.solve(np.zeros((2, P.n_dof), dtype=np.complex128))
+        assert rc == mx.MX_OK and np.all(x == 0) and st[0]["iterations"] == 0
+
+
+def test_nonconvergence_reports_enoconv():
+    n, k = 10, 6.0
+    with _handle(n, k, 0.0, k, 5, 1) as P:
+        P.factor()
+        b = inputs.random_complex(4, (1, P.n_dof))
+        x, st, rc = P.solve(b, tol=1e-14, max_it=3)
+    assert rc == mx.MX_ENOCONV and st[0]["iterations"] == 3 and not st[0]["converged"]
+    assert np.isfinite(x).all()
+
+
+def test_single_dof_mesh():
+    with _handle(1, 2.0, 1.0, 1.0, 1, 0) as P:
+        assert P.n_dof == 1
+        P.factor()
+        x, st, rc = P.solve(np.array([[1.0 + 1.0j]]), tol=1e-12)
+        A = fem.a_xi(*fem.assemble_KM(KuhnMesh(1)), 2.0, 1.0).toarray()
+        assert abs(x[0, 0] - (1 + 1j) / A[0, 0]) < 1e-14
