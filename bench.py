@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark: GMRES time-to-1e-6 of the two-level additive Schwarz preconditioned
+lowest-order Nedelec solver at k = 30 on 60^3 cells (1,479,780 unknowns), mixed-precision
+local factors, 16 right-hand sides, FGMRES(200).
+
+One step = the whole path on one batch: mesh + assembly + subdomain and coarse index
+maps (build), local minors + batched band LU + coarse FP64 LU (factor), load vectors of
+the 16 seeded right-hand sides, and the batched GMRES solve to a 1e-6 FP64 relative
+residual. `value` is seconds per step with every input resident on the device (the
+load vectors are written straight into device memory); `e2e` repeats the step through
+the same C ABI with host buffers (load vectors read back to the host, right-hand sides
+copied in and solutions copied out inside the timed region).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica (different right-hand-side
+seeds): the path has no exchange step, so there is no collective on the data path.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GMRES time-to-1e-6 at k=30 (mixed vs FP64 form, same GB300); p50/p99 latency"
+
+WORKLOADS = {
+    # k = 30, 60^3 cells, 12^3 subdomains of 5^3 core cells + 1-cell overlap, 12^3 coarse mesh
+    # xi_prob = xi_prec = k^2: the absorptive regime of the paper's theory (Sec. 6.2). With
+    # xi_prob = 0 and xi_prec in {k, k^1.5} GMRES does not reach 1e-6 within 400 iterations
+    # (run with --xi-prob 0 --xi-prec k1.5), as in the paper's Table 3 for xi = k.
+    "maxwell60_k30_2lvl": dict(n=60, k=30.0, xi_prob="k2", xi_prec="k2", core=5, overlap=1, coarse=12,
+                               nrhs=16, restart=200, max_it=600, tol=1e-6, ref_iterations=35),
+    # k = 20, 40^3 cells, 8^3 subdomains, one level, one right-hand side
+    "maxwell40_k20_1lvl": dict(n=40, k=20.0, xi_prob=20.0, xi_prec="k", core=5, overlap=1, coarse=0,
+                               nrhs=1, restart=100, max_it=600, tol=1e-6, ref_iterations=600),
+    # k = 20 two-level with a 10^3 coarse mesh and a batch of right-hand sides
+    "maxwell40_k20_2lvl": dict(n=40, k=20.0, xi_prob=20.0, xi_prec="k", core=5, overlap=1, coarse=10,
+                               nrhs=32, restart=100, max_it=600, tol=1e-6, ref_iterations=600),
+    # small case: 10^3 cells, k = xi = 6, 2^3 subdomains, unrestarted to 1e-10
+    "maxwell10_k6_1lvl": dict(n=10, k=6.0, xi_prob=6.0, xi_prec="k", core=5, overlap=1, coarse=0,
+                              nrhs=1, restart=0, max_it=300, tol=1e-10, ref_iterations=57),
+}
+
+
+def xi_value(spec, k):
+    if isinstance(spec, (int, float)):
+        return float(spec)
+    return {"k": k, "k1.5": k ** 1.5, "k2": k * k}[spec]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return dict(hbm_gbs=p["hbm_gbs"], source="measured", bf16=p.get("bf16_tflops"))
+    return dict(hbm_gbs=6800.0, source="fallback", bf16=1900.0)
+
+
+# FP64 and FP32 ALU peaks of the GB300 from unit counts and the maximum SM clock:
+# 152 SMs x 2 FP64 FMA / clock x 2 flops x 2.07 GHz; 152 x 128 FP32 FMA x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, W, rank, world):
+    import torch
+    import inputs
+    import paper_1711_03789_gb300 as mx
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    mx.use_torch_allocator(dev)
+    stream = torch.cuda.current_stream()
+    k = W["k"]
+    xp, xq = xi_value(W["xi_prob"], k), xi_value(W["xi_prec"], k)
+    prec = mx.MX_MIXED if args.form == "mixed" else mx.MX_PLAIN_FP64
+    nrhs = W["nrhs"]
+    centres, pol = inputs.bump_batch(1 + 1000 * rank, nrhs)
+
+    def step(host):
+        P = mx.Problem(W["n"], k, xp, xq, W["core"], W["overlap"], W["coarse"], prec, stream=stream.cuda_stream)
+        P.factor()
+        n = P.n_dof
+        if host:
+            f = P.load_vector(centres, pol, 0.1)
+            x = np.empty_like(f)
+        else:
+            f = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
+            P.load_vector(centres, pol, 0.1, out=f)
+            x = torch.empty_like(f)
+        x, stats, rc = P.solve(f, W["tol"], W["restart"], W["max_it"], x=x)
+        t = P.timings()
+        info = P.info()
+        P.close()
+        return stats, t, info
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(dev)
+    mx.mx_profile(1)
+    launches0 = mx.mx_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    phases = []
+    for _ in range(args.steps):
+        stats, t, info = step(False)
+        phases.append(t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = mx.mx_launch_count() - launches0
+    prof = mx.mx_profile_read()
+    mx.mx_profile(0)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    # end to end through the C ABI with host buffers
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 2))
+    for _ in range(e2e_steps):
+        stats_h, _, _ = step(True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000 / e2e_steps
+    e2e_ms = max_over_ranks(e2e_ms, world)
+    return dict(ms=ms, e2e_ms=e2e_ms, stats=stats, stats_host=stats_h, phases=phases, info=info, prof=prof,
+                launches=launches, clocks=clk, xi_prob=xp, xi_prec=xq)
+
+
+def roofline(prof, peak):
+    """Dominant kernel by device time; its achieved rate against the roof it is closest to."""
+    name, p = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    sec = p["ms"] / 1e3
+    if sec <= 0:
+        return None
+    gbs = p["bytes"] / sec / 1e9
+    tfl = p["flops"] / sec / 1e12
+    fp64_kernels = {"arnoldi_dots", "arnoldi_update", "spmv", "coarse_lu", "update_x", "residual"}
+    alu_peak = FP64_PEAK_TFLOPS if (name in fp64_kernels or p.get("fp64")) else FP32_PEAK_TFLOPS
+    f_hbm = gbs / peak["hbm_gbs"]
+    f_alu = tfl / alu_peak
+    total_ms = sum(v["ms"] for v in prof.values())
+    base = {"kernel": name, "launches": p["launches"], "avg_launch_ms": p["ms"] / max(1, p["launches"]),
+            "share_of_device_time": p["ms"] / total_ms if total_ms else None, "traffic": None}
+    if f_hbm >= f_alu:
+        base.update({"bound": "hbm", "achieved": gbs, "peak": peak["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
+                     "peak_source": f"{peak['source']} copy bandwidth"})
+    else:
+        base.update({"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": f_alu,
+                     "peak_source": "FP64 unit count x max clock" if alu_peak == FP64_PEAK_TFLOPS
+                     else "FP32 unit count x max clock", "hbm_frac": f_hbm})
+    return base
+
+
+def cpu_baseline(W, iterations, budget_s=20.0):
+    """The oracle on a bounded sample of the workload, scaled to one step.
+
+    Times (single-threaded SciPy): the oracle's mesh + assembly + subdomain lists on a
+    20^3-cell mesh (scaled by unknowns), the factorisation and one solve of S sampled
+    5^3+overlap subdomain minors (scaled to all subdomains and right-hand sides), and one
+    SpMV plus one MGS Arnoldi step at the mean Krylov index (scaled by unknowns); the
+    step time is build + factor + iterations x per-iteration cost."""
+    from oracle.mesh import KuhnMesh
+    from oracle import fem, dd
+    import scipy.sparse.linalg as spla
+
+    t_start = time.perf_counter()
+    n, k = W["n"], W["k"]
+    xq = xi_value(W["xi_prec"], k)
+    xp = xi_value(W["xi_prob"], k)
+    nrhs = W["nrhs"]
+    ns = min(n, 20)
+    t0 = time.perf_counter()
+    m = KuhnMesh(ns)
+    K, M = fem.assemble_KM(m)
+    boxes = dd.subdomain_boxes(ns, W["core"], W["overlap"])
+    idx = [dd.local_dofs(m, lo, hi) for lo, hi in boxes]
+    t_build_s = time.perf_counter() - t0
+    from oracle.mesh import count_interior_edges
+    n_full = count_interior_edges(n)
+    scale_dof = n_full / m.n_dof
+    A_prec = fem.a_xi(K, M, k, xq)
+    A = fem.a_xi(K, M, k, xp)
+    # subdomain sample: the largest boxes
+    order = np.argsort([-len(i) for i in idx])
+    sample = [int(l) for l in order[:4]]
+    t0 = time.perf_counter()
+    lus = [spla.splu(A_prec[idx[l]][:, idx[l]].tocsc()) for l in sample]
+    t_fac = (time.perf_counter() - t0) / len(sample)
+    rhs = np.ones((len(idx[sample[0]]), nrhs), dtype=np.complex128)
+    t0 = time.perf_counter()
+    for lu in lus:
+        lu.solve(rhs)
+    t_sol = (time.perf_counter() - t0) / len(sample)
+    N = -(-n // W["core"])
+    n_sub = N ** 3
+    v = np.ones((m.n_dof, nrhs), dtype=np.complex128)
+    t0 = time.perf_counter()
+    A @ v
+    t_spmv = (time.perf_counter() - t0) * scale_dof
+    jm = min(iterations, W["restart"] or iterations) / 2
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((int(max(1, jm)), m.n_dof)) + 0j
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    w = rng.standard_normal(m.n_dof) + 0j
+    t0 = time.perf_counter()
+    for vi in V:
+        h = np.vdot(vi, w)
+        w = w - h * vi
+    t_arn = (time.perf_counter() - t0) * scale_dof * nrhs
+    per_it = n_sub * t_sol + t_spmv + t_arn
+    step = t_build_s * scale_dof + n_sub * t_fac + iterations * per_it
+    return {"value": step, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle build on {ns}^3 cells scaled by unknowns; splu factor+solve of {len(sample)} of "
+                       f"{n_sub} subdomain minors scaled to all, {nrhs} rhs; SpMV and one MGS Arnoldi step at "
+                       f"j={int(jm)} scaled by unknowns; x {iterations} iterations; "
+                       f"{time.perf_counter() - t_start:.1f} s of CPU work"),
+            "per_iteration_s": per_it}
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="maxwell60_k30_2lvl", choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--xi-prec", default=None, help="k, k1.5, k2 or a number")
+    ap.add_argument("--xi-prob", default=None, help="0, k, k1.5, k2 or a number")
+    ap.add_argument("--restart", type=int, default=None)
+    ap.add_argument("--max-it", type=int, default=None)
+    ap.add_argument("--nrhs", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    W = dict(WORKLOADS[args.workload])
+    if args.xi_prec:
+        W["xi_prec"] = args.xi_prec if args.xi_prec in ("k", "k1.5", "k2") else float(args.xi_prec)
+    if args.xi_prob:
+        W["xi_prob"] = args.xi_prob if args.xi_prob in ("k", "k1.5", "k2") else float(args.xi_prob)
+    if args.restart is not None:
+        W["restart"] = args.restart
+    if args.max_it:
+        W["max_it"] = args.max_it
+    if args.nrhs:
+        W["nrhs"] = args.nrhs
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    config = {"workload": args.workload, "n_cells": W["n"], "k": W["k"], "xi_prob": W["xi_prob"],
+              "xi_prec": W["xi_prec"], "subdomain_core_cells": W["core"], "overlap_cells": W["overlap"],
+              "coarse_cells": W["coarse"], "nrhs_per_gpu": W["nrhs"], "gmres_restart": W["restart"],
+              "max_it": W["max_it"], "tol": W["tol"], "form": args.form,
+              "l2": "inputs larger than L2 (factors and Krylov basis > 129 MB)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        cb = cpu_baseline(W, W["ref_iterations"])
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["value"] * 1e3,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic (seeded Gaussian-bump right-hand sides)", "config": config,
+                "cpu_baseline": dict(cb, value=cb["value"]),
+                "e2e": {"value": cb["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "note": f"oracle extrapolated from a bounded sample assuming {W['ref_iterations']} iterations; "
+                        f"{time.perf_counter() - t0:.1f} s wall"}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    r = run_ours(args, W, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    iters = max(s["iterations"] for s in r["stats"])
+    conv = all(s["converged"] for s in r["stats"])
+    n_dof = r["info"]["n_dof"]
+    nrhs = W["nrhs"]
+    pk = peaks()
+    roof = roofline(r["prof"], pk)
+    ph = r["phases"][-1]
+    line = {
+        "metric": METRIC,
+        "value": r["ms"] / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r["ms"],
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 factors / f64 Krylov" if args.form == "mixed" else "f64",
+        "data": "synthetic (seeded Gaussian-bump right-hand sides, generated Kuhn mesh)",
+        "config": config,
+        "converged": conv,
+        "iterations": iters,
+        "rel_residual_max": max(s["rel_residual"] for s in r["stats"]),
+        "phases_ms": {"build": ph["build_ms"], "factor": ph["factor_ms"], "solve": ph["solve_ms"]},
+        "gmres_s": ph["solve_ms"] / 1e3,
+        "rhs_per_s": world * nrhs / (r["ms"] / 1e3),
+        "n_dof": n_dof,
+        "factor_bytes": r["info"]["factor_bytes"],
+        "e2e": {"value": r["e2e_ms"] / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n_dof * nrhs,
+                "d2h_bytes_per_step": 2 * 16 * n_dof * nrhs},
+        "gpu_launches": r["launches"] // args.steps,
+        "roofline": roof,
+        "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
+                    for k, v in sorted(r["prof"].items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
+        "clocks": r["clocks"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W, iters)
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -194,6 +194,24 @@ MX_API int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels)
  * column-major n_l x n_l, c128 (host). Unit lower L below the diagonal, U on and above. */
 MX_API int mx_get_local(mx_handle h, int l, double* out);
 
+/* ---- Instrumentation ----------------------------------------------------------------- */
+
+/* Number of kernel launches made by the library since it was loaded (all handles). */
+MX_API int64_t mx_launch_count(void);
+
+/* Enable (1) or disable (0) per-kernel device timing and clear the accumulators. When
+ * enabled, each step of the path is bracketed by CUDA events on the handle's stream;
+ * the events add about a microsecond of host time per step. */
+MX_API int mx_profile(int enable);
+
+/* Resolve pending events (synchronises) and copy, per kernel id, the accumulated device
+ * milliseconds, launches, algorithmic bytes and flops (any pointer may be NULL; arrays
+ * hold at least the returned count of entries). Returns the number of kernel ids. */
+MX_API int mx_profile_read(double* ms, int64_t* launches, double* bytes, double* flops);
+
+/* Name of kernel id `id` ("" if out of range). */
+MX_API const char* mx_profile_name(int id);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,10 @@ _sig = {
     "mx_spmv": (C.c_int, [H, P, P, C.c_int]),
     "mx_precond": (C.c_int, [H, P, P, C.c_int, C.c_int]),
     "mx_get_local": (C.c_int, [H, C.c_int, P]),
+    "mx_launch_count": (C.c_int64, []),
+    "mx_profile": (C.c_int, [C.c_int]),
+    "mx_profile_read": (C.c_int, [P, P, P, P]),
+    "mx_profile_name": (C.c_char_p, [C.c_int]),
 }
 for _n, (_r, _a) in _sig.items():
     _f = getattr(lib, _n)
@@ -260,6 +264,32 @@ def mx_get_local(h, l, n_l):
     out = np.empty((n_l, n_l), dtype=np.complex128)  # column-major content
     _check(lib.mx_get_local(h, int(l), _ptr(out)))
     return out.T.copy()  # row-major [i, j]
+
+
+def mx_launch_count():
+    return int(lib.mx_launch_count())
+
+
+def mx_profile(enable):
+    _check(lib.mx_profile(int(bool(enable))))
+
+
+def mx_profile_name(i):
+    return lib.mx_profile_name(int(i)).decode()
+
+
+def mx_profile_read():
+    """{kernel name: dict(ms, launches, bytes, flops)} accumulated since mx_profile(1)."""
+    n = 64
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    by = np.zeros(n)
+    fl = np.zeros(n)
+    k = lib.mx_profile_read(_ptr(ms), _ptr(cnt), _ptr(by), _ptr(fl))
+    if k < 0:
+        _check(k)
+    return {mx_profile_name(i): dict(ms=float(ms[i]), launches=int(cnt[i]), bytes=float(by[i]), flops=float(fl[i]))
+            for i in range(k)}
 
 
 _keep = []

@@ -7,6 +7,9 @@
 namespace mx {
 const char* last_error();
 void set_allocator(alloc_fn a, free_fn f, void* ctx);
+void prof_reset(bool on);
+void prof_read(double* ms, int64_t* launches, double* bytes, double* flops);
+int64_t launch_count();
 
 Problem::~Problem() { free_workspace(*this); }
 
@@ -240,11 +243,11 @@ int mx_solve(mx_handle h, const void* rhs, int nrhs, double tol, int restart, in
     int maxit = 0, restarts = 0;
     for (int r0 = 0; r0 < nrhs; r0 += batch) {
       const int nr = std::min(batch, nrhs - r0);
-      k_to_internal<<<grid_for(n * nr, 256), 256, 0, P.stream>>>(n, nrhs, r0, nr, (const double2*)in.p, bi.p);
+      MX_LAUNCH(k_to_internal<<<grid_for(n * nr, 256), 256, 0, P.stream>>>(n, nrhs, r0, nr, (const double2*)in.p, bi.p));
       MX_CHECK_LAUNCH();
       const int c = gmres_solve(P, bi.p, xi.p, nr, tol, restart, max_it, stats ? stats + r0 : nullptr);
       if (c != MX_OK) rc = c;
-      k_to_user<<<grid_for(n * nr, 256), 256, 0, P.stream>>>(n, nrhs, r0, nr, xi.p, (double2*)out.p);
+      MX_LAUNCH(k_to_user<<<grid_for(n * nr, 256), 256, 0, P.stream>>>(n, nrhs, r0, nr, xi.p, (double2*)out.p));
       MX_CHECK_LAUNCH();
       launches += P.timing.solve_launches + 2;
       maxit = std::max(maxit, P.timing.max_iterations);
@@ -354,9 +357,9 @@ int mx_spmv(mx_handle h, const void* x, void* y, int nrhs) {
     DevView in(x, bytes, true, P.stream);
     DevView out(y, bytes, false, P.stream);
     DevBuf<double2> a((size_t)n * nrhs), b((size_t)n * nrhs);
-    k_to_internal<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, (const double2*)in.p, a.p);
+    MX_LAUNCH(k_to_internal<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, (const double2*)in.p, a.p));
     spmv(P, P.xi_prob, a.p, 0, b.p, nrhs, P.stream);
-    k_to_user<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, b.p, (double2*)out.p);
+    MX_LAUNCH(k_to_user<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, b.p, (double2*)out.p));
     MX_CHECK_LAUNCH();
     out.copy_out(bytes, P.stream);
     MX_CUDA(cudaStreamSynchronize(P.stream));
@@ -373,14 +376,28 @@ int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels) {
     DevView in(v, bytes, true, P.stream);
     DevView out(z, bytes, false, P.stream);
     DevBuf<double2> a((size_t)n * nrhs), b((size_t)n * nrhs);
-    k_to_internal<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, (const double2*)in.p, a.p);
+    MX_LAUNCH(k_to_internal<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, (const double2*)in.p, a.p));
     precond_apply(P, a.p, b.p, 0, nrhs, levels);
-    k_to_user<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, b.p, (double2*)out.p);
+    MX_LAUNCH(k_to_user<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, b.p, (double2*)out.p));
     MX_CHECK_LAUNCH();
     out.copy_out(bytes, P.stream);
     MX_CUDA(cudaStreamSynchronize(P.stream));
   });
 }
+
+int mx_profile(int enable) {
+  return guard([&] { prof_reset(enable != 0); });
+}
+
+int mx_profile_read(double* ms, int64_t* launches, double* bytes, double* flops) {
+  int n = K_COUNT;
+  int rc = guard([&] { prof_read(ms, launches, bytes, flops); });
+  return rc == MX_OK ? n : rc;
+}
+
+const char* mx_profile_name(int id) { return kernel_name(id); }
+
+int64_t mx_launch_count(void) { return launch_count(); }
 
 int mx_get_local(mx_handle h, int l, double* out) {
   return guard([&] {

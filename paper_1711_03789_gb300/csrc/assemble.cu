@@ -167,7 +167,7 @@ void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s) {
   A.rows = A.cols = m.n_dof;
   A.rowptr.alloc(m.n_dof + 1);
   a.count = cnt.p;
-  k_assemble<false><<<grid_for(m.n_dof, 128), 128, 0, s>>>(a);
+  MX_LAUNCH(k_assemble<false><<<grid_for(m.n_dof, 128), 128, 0, s>>>(a));
   MX_CHECK_LAUNCH();
   A.nnz = exclusive_scan_i32(cnt.p, A.rowptr.p, m.n_dof, s);
   A.col.alloc(A.nnz);
@@ -177,7 +177,7 @@ void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s) {
   a.col = A.col.p;
   a.K = A.K.p;
   a.M = A.M.p;
-  k_assemble<true><<<grid_for(m.n_dof, 128), 128, 0, s>>>(a);
+  MX_LAUNCH(k_assemble<true><<<grid_for(m.n_dof, 128), 128, 0, s>>>(a));
   MX_CHECK_LAUNCH();
   MX_CUDA(cudaStreamSynchronize(s));
 }
@@ -320,10 +320,10 @@ void load_vector(const Problem& P, int nrhs, int nbumps, const double* h_centres
     a.centres = dc.p + (int64_t)r0 * nbumps * 3;
     a.pol = dp.p + (int64_t)r0 * nbumps * 3;
     a.contrib = contrib.p;
-    k_load_tets<<<grid_for(ntet * nr, 128), 128, 0, s>>>(a);
+    MX_LAUNCH(k_load_tets<<<grid_for(ntet * nr, 128), 128, 0, s>>>(a));
     MX_CHECK_LAUNCH();
-    k_load_gather<<<grid_for(P.fine.n_dof * nr, 256), 256, 0, s>>>(
-        n, P.fine.n_dof, nr, P.fine.dof_key.p, contrib.p, f + (int64_t)r0 * P.fine.n_dof);
+    MX_LAUNCH(k_load_gather<<<grid_for(P.fine.n_dof * nr, 256), 256, 0, s>>>(
+        n, P.fine.n_dof, nr, P.fine.dof_key.p, contrib.p, f + (int64_t)r0 * P.fine.n_dof));
     MX_CHECK_LAUNCH();
   }
   MX_CUDA(cudaStreamSynchronize(s));
@@ -480,28 +480,28 @@ void build_coarse_restriction(Problem& P) {
   P.R0T.rows = nd;
   P.R0T.cols = nc;
   P.R0T.rowptr.alloc(nd + 1);
-  k_r0t<false><<<grid_for(nd, 256), 256, 0, s>>>(n, m, nd, P.fine.dof_key.p, P.coarse.edge_dof.p,
-                                                 cnt.p, nullptr, nullptr, nullptr);
+  MX_LAUNCH(k_r0t<false><<<grid_for(nd, 256), 256, 0, s>>>(n, m, nd, P.fine.dof_key.p, P.coarse.edge_dof.p,
+                                                 cnt.p, nullptr, nullptr, nullptr));
   MX_CHECK_LAUNCH();
   P.R0T.nnz = exclusive_scan_i32(cnt.p, P.R0T.rowptr.p, nd, s);
   P.R0T.col.alloc(P.R0T.nnz);
   P.R0T.val.alloc(P.R0T.nnz);
-  k_r0t<true><<<grid_for(nd, 256), 256, 0, s>>>(n, m, nd, P.fine.dof_key.p, P.coarse.edge_dof.p,
-                                                nullptr, P.R0T.rowptr.p, P.R0T.col.p, P.R0T.val.p);
+  MX_LAUNCH(k_r0t<true><<<grid_for(nd, 256), 256, 0, s>>>(n, m, nd, P.fine.dof_key.p, P.coarse.edge_dof.p,
+                                                nullptr, P.R0T.rowptr.p, P.R0T.col.p, P.R0T.val.p));
   MX_CHECK_LAUNCH();
   P.R0.rows = nc;
   P.R0.cols = nd;
   P.R0.rowptr.alloc(nc + 1);
   const unsigned g = (unsigned)std::min<int64_t>(nc, 4096);
-  k_r0_rows<<<g, 256, 0, s>>>(n, m, nc, P.coarse.dof_key.p, P.fine.edge_dof.p, P.R0T.rowptr.p,
-                              P.R0T.col.p, P.R0T.val.p, cnt.p, nullptr, nullptr, nullptr, 0);
+  MX_LAUNCH(k_r0_rows<<<g, 256, 0, s>>>(n, m, nc, P.coarse.dof_key.p, P.fine.edge_dof.p, P.R0T.rowptr.p,
+                              P.R0T.col.p, P.R0T.val.p, cnt.p, nullptr, nullptr, nullptr, 0));
   MX_CHECK_LAUNCH();
   P.R0.nnz = exclusive_scan_i32(cnt.p, P.R0.rowptr.p, nc, s);
   MX_REQUIRE(P.R0.nnz == P.R0T.nnz, MX_EINVAL, "coarse restriction transpose mismatch");
   P.R0.col.alloc(P.R0.nnz);
   P.R0.val.alloc(P.R0.nnz);
-  k_r0_rows<<<g, 256, 0, s>>>(n, m, nc, P.coarse.dof_key.p, P.fine.edge_dof.p, P.R0T.rowptr.p,
-                              P.R0T.col.p, P.R0T.val.p, nullptr, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, 1);
+  MX_LAUNCH(k_r0_rows<<<g, 256, 0, s>>>(n, m, nc, P.coarse.dof_key.p, P.fine.edge_dof.p, P.R0T.rowptr.p,
+                              P.R0T.col.p, P.R0T.val.p, nullptr, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, 1));
   MX_CHECK_LAUNCH();
   MX_CUDA(cudaStreamSynchronize(s));
 }

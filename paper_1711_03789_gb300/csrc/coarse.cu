@@ -46,7 +46,7 @@ void factor_coarse(Problem& P) {
   P.n_c = nc;
   DevBuf<int32_t> bw(1);
   MX_CUDA(cudaMemsetAsync(bw.p, 0, 4, s));
-  k_csr_band<<<grid_for(nc, 256), 256, 0, s>>>(nc, P.Ac.rowptr.p, P.Ac.col.p, bw.p);
+  MX_LAUNCH(k_csr_band<<<grid_for(nc, 256), 256, 0, s>>>(nc, P.Ac.rowptr.p, P.Ac.col.p, bw.p));
   MX_CHECK_LAUNCH();
   int b = 0;
   MX_CUDA(cudaMemcpyAsync(&b, bw.p, 4, cudaMemcpyDeviceToHost, s));
@@ -55,8 +55,8 @@ void factor_coarse(Problem& P) {
   P.ld_c = (2 * b + 1 + 3) & ~3;
   P.A0.alloc(P.ld_c * nc);
   MX_CUDA(cudaMemsetAsync(P.A0.p, 0, P.A0.bytes(), s));
-  k_coarse_fill<<<grid_for(nc, 256), 256, 0, s>>>(nc, P.Ac.rowptr.p, P.Ac.col.p, P.Ac.K.p, P.Ac.M.p,
-                                                  P.k * P.k, P.xi_prec, b, (int)P.ld_c, P.A0.p);
+  MX_LAUNCH(k_coarse_fill<<<grid_for(nc, 256), 256, 0, s>>>(nc, P.Ac.rowptr.p, P.Ac.col.p, P.Ac.K.p, P.Ac.M.p,
+                                                  P.k * P.k, P.xi_prec, b, (int)P.ld_c, P.A0.p));
   MX_CHECK_LAUNCH();
   const int32_t meta[3] = {(int32_t)nc, b, (int32_t)P.ld_c};
   const int64_t zero = 0;
@@ -65,10 +65,16 @@ void factor_coarse(Problem& P) {
   MX_CUDA(cudaMemcpyAsync(P.c_meta.p, meta, 12, cudaMemcpyHostToDevice, s));
   MX_CUDA(cudaMemcpyAsync(P.c_off.p, &zero, 8, cudaMemcpyHostToDevice, s));
   BandBatch B{1, P.c_meta.p, P.c_meta.p + 1, P.c_meta.p + 2, P.c_off.p};
-  band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s);
+  band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU);
+  const int64_t nq = (nc + CB - 1) / CB;
+  P.c_dinv.alloc(nq * 2 * CB * CB);
+  invert_diag_blocks<double2>(B, P.A0.p, P.c_off.p, P.c_dinv.p, (int)nc, s);
   if (P.precision == MX_MIXED) {
     P.A0f.alloc(P.A0.n);
-    k_to_c64<<<grid_for(P.A0.n, 256), 256, 0, s>>>(P.A0.n, P.A0.p, P.A0f.p);
+    MX_LAUNCH(k_to_c64<<<grid_for(P.A0.n, 256), 256, 0, s>>>(P.A0.n, P.A0.p, P.A0f.p));
+    MX_CHECK_LAUNCH();
+    P.c_dinvf.alloc(P.c_dinv.n);
+    MX_LAUNCH(k_to_c64<<<grid_for(P.c_dinv.n, 256), 256, 0, s>>>(P.c_dinv.n, P.c_dinv.p, P.c_dinvf.p));
     MX_CHECK_LAUNCH();
   }
   MX_CUDA(cudaStreamSynchronize(s));
@@ -98,102 +104,107 @@ __global__ void k_coarse_restrict(int64_t nc, int64_t n, int nrhs, const int32_t
 // Band triangular sweeps on r [n][nrhs] (in place): forward with unit lower L, backward
 // with upper U. Grid-wide barriers between column blocks.
 template <typename T2>
-__global__ void k_coarse_sweep(int n, int b, int ld, const T2* F, T2* r, int nrhs) {
+__global__ void k_coarse_sweep(int n, int b, int ld, const T2* F, const T2* Dinv, T2* r, int nrhs) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ unsigned char smem_raw[];
   T2* x = reinterpret_cast<T2*>(smem_raw);  // [CB][nrhs]
+  __shared__ T2 D[CB][CB + 1];              // diagonal block of the current step
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nblk = (n + CB - 1) / CB;
-  // forward
-  for (int blk = 0; blk < nblk; ++blk) {
-    const int c0 = blk * CB, c1 = min(n, c0 + CB);
-    for (int t = tid; t < (c1 - c0) * nrhs; t += nt) x[t] = r[(int64_t)c0 * nrhs + t];
-    __syncthreads();
-    for (int k = c0; k < c1 - 1; ++k) {
-      for (int t = tid; t < (c1 - k - 1) * nrhs; t += nt) {
-        const int i = k + 1 + t / nrhs, q = t % nrhs;
-        if (i - k <= b) {
-          T2 v = x[(i - c0) * nrhs + q];
-          cfms(v, F[bidx(0, ld, b, i, k)], x[(k - c0) * nrhs + q]);
-          x[(i - c0) * nrhs + q] = v;
+  for (int t = tid; t < CB * nrhs; t += nt) x[t] = czero<T2>();
+  __syncthreads();
+  for (int dir = 0; dir < 2; ++dir) {  // 0: forward (unit lower L), 1: backward (upper U)
+    for (int s = 0; s < nblk; ++s) {
+      const int blk = dir == 0 ? s : nblk - 1 - s;
+      const int c0 = blk * CB, c1 = min(n, c0 + CB), kb = c1 - c0;
+      for (int t = tid; t < kb * nrhs; t += nt) x[t] = r[(int64_t)c0 * nrhs + t];
+      __syncthreads();
+      // every block applies the inverted diagonal block redundantly: x_blk = D r_blk
+      {
+        const T2* Dq = Dinv + (int64_t)blk * 2 * CB * CB + (dir == 0 ? 0 : CB * CB);  // column-major
+        for (int t = tid; t < CB * CB; t += nt) D[t % CB][t / CB] = Dq[t];
+        __syncthreads();
+        T2 out[4];
+        for (int c = 0; c < 4; ++c) {
+          const int t = tid + nt * c;
+          out[c] = czero<T2>();
+          if (t < kb * nrhs) {
+            const int i = t / nrhs, q = t % nrhs;
+            const int k0 = dir == 0 ? 0 : i, k1 = dir == 0 ? i + 1 : kb;
+            for (int k = k0; k < k1; ++k) cfma(out[c], D[i][k], x[k * nrhs + q]);
+          }
+        }
+        __syncthreads();
+        for (int c = 0; c < 4; ++c) {
+          const int t = tid + nt * c;
+          if (t < kb * nrhs) x[t] = out[c];
         }
       }
       __syncthreads();
-    }
-    if (blockIdx.x == 0)
-      for (int t = tid; t < (c1 - c0) * nrhs; t += nt) r[(int64_t)c0 * nrhs + t] = x[t];
-    const int r1 = min(n, c1 + b);
-    const int64_t work = (int64_t)(r1 - c1) * nrhs;
-    for (int64_t t = blockIdx.x * (int64_t)nt + tid; t < work; t += (int64_t)gridDim.x * nt) {
-      const int i = c1 + (int)(t / nrhs), q = (int)(t % nrhs);
-      T2 acc = r[(int64_t)i * nrhs + q];
-      for (int k = max(c0, i - b); k < c1; ++k) cfms(acc, F[bidx(0, ld, b, i, k)], x[(k - c0) * nrhs + q]);
-      r[(int64_t)i * nrhs + q] = acc;
-    }
-    grid.sync();
-  }
-  // backward
-  for (int blk = nblk - 1; blk >= 0; --blk) {
-    const int c0 = blk * CB, c1 = min(n, c0 + CB);
-    for (int t = tid; t < (c1 - c0) * nrhs; t += nt) x[t] = r[(int64_t)c0 * nrhs + t];
-    __syncthreads();
-    for (int k = c1 - 1; k >= c0; --k) {
-      for (int q = tid; q < nrhs; q += nt) x[(k - c0) * nrhs + q] = cmul(x[(k - c0) * nrhs + q], crcp(F[bidx(0, ld, b, k, k)]));
-      __syncthreads();
-      for (int t = tid; t < (k - c0) * nrhs; t += nt) {
-        const int i = c0 + t / nrhs, q = t % nrhs;
-        if (k - i <= b) {
-          T2 v = x[(i - c0) * nrhs + q];
-          cfms(v, F[bidx(0, ld, b, i, k)], x[(k - c0) * nrhs + q]);
-          x[(i - c0) * nrhs + q] = v;
+      if (blockIdx.x == 0)
+        for (int t = tid; t < kb * nrhs; t += nt) r[(int64_t)c0 * nrhs + t] = x[t];
+      // rows inside the band outside the block
+      const int r0 = dir == 0 ? c1 : max(0, c0 - b);
+      const int r1 = dir == 0 ? min(n, c1 + b) : c0;
+      const int64_t work = (int64_t)(r1 - r0) * nrhs;
+      for (int64_t t = blockIdx.x * (int64_t)nt + tid; t < work; t += (int64_t)gridDim.x * nt) {
+        const int i = r0 + (int)(t / nrhs), q = (int)(t % nrhs);
+        T2 acc = r[(int64_t)i * nrhs + q];
+        const int k0 = dir == 0 ? max(c0, i - b) : c0;
+        const int k1 = dir == 0 ? c1 : min(c1, i + b + 1);
+        // fixed trip count, all factor loads issued ahead (out-of-range entries load as 0;
+        // x rows past kb are zero-initialised)
+        T2 f[CB];
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+          const int k = c0 + u;
+          f[u] = (k >= k0 && k < k1) ? F[bidx(0, ld, b, i, k)] : czero<T2>();
         }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) cfms(acc, f[u], x[u * nrhs + q]);
+        r[(int64_t)i * nrhs + q] = acc;
       }
-      __syncthreads();
+      grid.sync();
     }
-    if (blockIdx.x == 0)
-      for (int t = tid; t < (c1 - c0) * nrhs; t += nt) r[(int64_t)c0 * nrhs + t] = x[t];
-    const int r0 = max(0, c0 - b);
-    const int64_t work = (int64_t)(c0 - r0) * nrhs;
-    for (int64_t t = blockIdx.x * (int64_t)nt + tid; t < work; t += (int64_t)gridDim.x * nt) {
-      const int i = r0 + (int)(t / nrhs), q = (int)(t % nrhs);
-      T2 acc = r[(int64_t)i * nrhs + q];
-      for (int k = c0; k < min(c1, i + b + 1); ++k) cfms(acc, F[bidx(0, ld, b, i, k)], x[(k - c0) * nrhs + q]);
-      r[(int64_t)i * nrhs + q] = acc;
-    }
-    grid.sync();
   }
 }
 
 template <typename T2>
-static void sweep(Problem& P, T2* F, T2* r, int nrhs) {
+static void sweep(Problem& P, T2* F, const T2* Dinv, T2* r, int nrhs) {
   const int n = (int)P.n_c, b = P.coarse_band, ld = (int)P.ld_c;
   const size_t smem = (size_t)CB * nrhs * sizeof(T2);
-  MX_REQUIRE(smem <= 48 * 1024, MX_EINVAL, "too many right-hand sides for the coarse sweep");
+  MX_REQUIRE(nrhs <= 32 && smem <= 48 * 1024, MX_EINVAL, "too many right-hand sides for the coarse sweep");
   int per_sm = 0;
   MX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_sweep<T2>, 256, smem));
   MX_REQUIRE(per_sm > 0, MX_ECUDA, "coarse sweep kernel cannot be resident");
   const int64_t work = (int64_t)std::min(b, n) * nrhs;
   int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, std::max<int64_t>(1, (work + 255) / 256));
   grid = std::max(1, std::min(grid, sm_count()));
-  void* args[] = {(void*)&n, (void*)&b, (void*)&ld, (void*)&F, (void*)&r, (void*)&nrhs};
-  MX_CUDA(cudaLaunchCooperativeKernel((void*)k_coarse_sweep<T2>, grid, 256, args, smem, P.stream));
+  void* args[] = {(void*)&n, (void*)&b, (void*)&ld, (void*)&F, (void*)&Dinv, (void*)&r, (void*)&nrhs};
+  const double entries = (double)n * (2.0 * b + 1.0) - (double)b * (b + 1.0);
+  ProfScope ps(K_COARSE_SWEEP, P.stream, 1, sizeof(T2) * (entries + 2.0 * n * nrhs), 8.0 * entries * nrhs);
+  MX_LAUNCH(MX_CUDA(cudaLaunchCooperativeKernel((void*)k_coarse_sweep<T2>, grid, 256, args, smem, P.stream)));
 }
 
 void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
   cudaStream_t s = P.stream;
   const int64_t nc = P.n_c;
-  if (P.precision == MX_MIXED) {
-    float2* r = reinterpret_cast<float2*>(yc);  // c64 view of the workspace
-    k_coarse_restrict<float2><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(nc, P.fine.n_dof, nrhs, P.R0.rowptr.p,
-                                                                       P.R0.col.p, P.R0.val.p, v, vtype, r);
+  // R^0 (12 B per entry) and one gather of v per entry (worst case), output once
+  const double rb = 12.0 * P.R0.nnz + 4.0 * nc + 16.0 * (double)P.R0.nnz * nrhs + 16.0 * nc * nrhs;
+  const bool mixed = P.precision == MX_MIXED;
+  float2* rf = reinterpret_cast<float2*>(yc);  // c64 view of the workspace (mixed)
+  {
+    ProfScope ps(K_COARSE_RESTRICT, s, 1, rb, 4.0 * P.R0.nnz * nrhs);
+    if (mixed)
+      MX_LAUNCH(k_coarse_restrict<float2><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
+          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, rf));
+    else
+      MX_LAUNCH(k_coarse_restrict<double2><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
+          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, yc));
     MX_CHECK_LAUNCH();
-    sweep<float2>(P, P.A0f.p, r, nrhs);
-  } else {
-    k_coarse_restrict<double2><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(nc, P.fine.n_dof, nrhs, P.R0.rowptr.p,
-                                                                        P.R0.col.p, P.R0.val.p, v, vtype, yc);
-    MX_CHECK_LAUNCH();
-    sweep<double2>(P, P.A0.p, yc, nrhs);
   }
+  if (mixed) sweep<float2>(P, P.A0f.p, P.c_dinvf.p, rf, nrhs);
+  else sweep<double2>(P, P.A0.p, P.c_dinv.p, yc, nrhs);
 }
 
 }  // namespace mx

@@ -1,4 +1,7 @@
-// Error state, allocation hook and the deterministic device scan.
+// Error state, allocation hook, launch counter, profiler and the deterministic device scan.
+#include <atomic>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace mx {
@@ -36,6 +39,80 @@ void dev_free(void* p) {
   if (!p) return;
   if (g_free) g_free(p, g_ctx);
   else cudaFree(p);
+}
+
+// ---- launch counter and profiler ------------------------------------------------------
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(); }
+
+static const char* k_names[K_COUNT] = {
+    "mesh", "subdomains", "assemble", "coarse_r0", "load_vector", "extract_minors", "lu_diag", "lu_panel",
+    "lu_update", "coarse_lu", "local_solve", "coarse_restrict", "coarse_sweep", "scatter", "spmv",
+    "arnoldi_dots", "arnoldi_update", "arnoldi_small", "update_x", "residual", "layout"};
+const char* kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? k_names[id] : ""; }
+
+struct Pending {
+  int id, launches;
+  double bytes, flops;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<cudaEvent_t> g_pool;
+static size_t g_pool_used = 0;
+static std::vector<Pending> g_pending;
+static double g_ms[K_COUNT], g_bytes[K_COUNT], g_flops[K_COUNT];
+static int64_t g_cnt[K_COUNT];
+
+bool prof_enabled() { return g_prof_on; }
+
+cudaEvent_t prof_event() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_pool_used == g_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    g_pool.push_back(e);
+  }
+  return g_pool[g_pool_used++];
+}
+
+void prof_push(int id, cudaEvent_t a, cudaEvent_t b, int launches, double bytes, double flops) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_pending.push_back({id, launches, bytes, flops, a, b});
+}
+
+static void prof_resolve() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_pending.empty()) cudaEventSynchronize(g_pending.back().b);
+  for (auto& p : g_pending) {
+    cudaEventSynchronize(p.b);
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) g_ms[p.id] += ms;
+    g_cnt[p.id] += p.launches;
+    g_bytes[p.id] += p.bytes;
+    g_flops[p.id] += p.flops;
+  }
+  g_pending.clear();
+  g_pool_used = 0;
+}
+
+void prof_reset(bool on) {
+  prof_resolve();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on;
+  for (int i = 0; i < K_COUNT; ++i) g_ms[i] = g_bytes[i] = g_flops[i] = 0, g_cnt[i] = 0;
+}
+
+void prof_read(double* ms, int64_t* launches, double* bytes, double* flops) {
+  prof_resolve();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int i = 0; i < K_COUNT; ++i) {
+    if (ms) ms[i] = g_ms[i];
+    if (launches) launches[i] = g_cnt[i];
+    if (bytes) bytes[i] = g_bytes[i];
+    if (flops) flops[i] = g_flops[i];
+  }
 }
 
 int sm_count() {
@@ -118,11 +195,11 @@ template <typename T>
 static void scan_rec(const T* in, T* out, int64_t n, cudaStream_t s) {
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   DevBuf<T> sums(nb), pre(nb + 1);
-  k_scan_tiles<T><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, sums.p, n);
+  MX_LAUNCH(k_scan_tiles<T><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, sums.p, n));
   MX_CHECK_LAUNCH();
   if (nb > 1) {
     scan_rec<T>(sums.p, pre.p, nb, s);
-    k_scan_add<T><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(out, pre.p, n);
+    MX_LAUNCH(k_scan_add<T><<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(out, pre.p, n));
     MX_CHECK_LAUNCH();
   }
   MX_CUDA(cudaStreamSynchronize(s));  // keep temporaries alive until done
@@ -136,7 +213,7 @@ __global__ void k_last(const T* in, const T* out, T* dst, int64_t n) {
 template <typename T>
 static int64_t scan_impl(const T* in, T* out, int64_t n, cudaStream_t s) {
   if (n > 0) scan_rec<T>(in, out, n, s);
-  k_last<T><<<1, 1, 0, s>>>(in, out, out, n);
+  MX_LAUNCH(k_last<T><<<1, 1, 0, s>>>(in, out, out, n));
   MX_CHECK_LAUNCH();
   T total = 0;
   MX_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(T), cudaMemcpyDeviceToHost, s));

@@ -31,6 +31,49 @@ void set_last_error(const std::string& msg);
 
 #define MX_CHECK_LAUNCH() MX_CUDA(cudaGetLastError())
 
+// Every kernel launch of the library goes through MX_LAUNCH, which counts it.
+void note_launch();
+#define MX_LAUNCH(...)     \
+  do {                     \
+    __VA_ARGS__;           \
+    ::mx::note_launch();   \
+  } while (0)
+
+// ---- per-kernel device timing -------------------------------------------------------
+// When enabled, ProfScope brackets the launches of one step of the path with CUDA events
+// on the launching stream and books their device time, launch count and algorithmic
+// bytes / flops under a kernel id; mx_profile_read() resolves the events.
+enum KernelId {
+  K_MESH = 0, K_SUBDOMAINS, K_ASSEMBLE, K_COARSE_R0, K_LOAD, K_EXTRACT, K_LU_DIAG, K_LU_PANEL,
+  K_LU_UPDATE, K_COARSE_LU, K_LOCAL_SOLVE, K_COARSE_RESTRICT, K_COARSE_SWEEP, K_SCATTER, K_SPMV,
+  K_DOTS, K_ORTH_UPDATE, K_ARNOLDI_SMALL, K_UPDATE_X, K_RESIDUAL, K_LAYOUT, K_COUNT
+};
+const char* kernel_name(int id);
+bool prof_enabled();
+void prof_push(int id, cudaEvent_t a, cudaEvent_t b, int launches, double bytes, double flops);
+cudaEvent_t prof_event();
+
+struct ProfScope {
+  int id, launches;
+  double bytes, flops;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(int id_, cudaStream_t s_, int launches_ = 1, double bytes_ = 0, double flops_ = 0)
+      : id(id_), launches(launches_), bytes(bytes_), flops(flops_), s(s_) {
+    if (prof_enabled()) {
+      a = prof_event();
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event();
+      cudaEventRecord(b, s);
+      prof_push(id, a, b, launches, bytes, flops);
+    }
+  }
+};
+
 #define MX_REQUIRE(cond, code, msg)                          \
   do {                                                       \
     if (!(cond)) throw ::mx::Error((code), std::string(msg)); \

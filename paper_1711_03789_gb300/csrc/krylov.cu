@@ -45,12 +45,16 @@ __global__ void k_spmv(int64_t rows, int nrhs, const int32_t* __restrict__ rowpt
 void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int nrhs, cudaStream_t s) {
   const int64_t work = P.A.rows * nrhs;
   const double sr = P.k * P.k, si = xi;
+  // K, M values and column indices once, x once, y once (algorithmic minimum)
+  const double xb = xtype == 0 ? 16.0 : 8.0;
+  ProfScope ps(K_SPMV, s, 1, 20.0 * P.A.nnz + 4.0 * (P.A.rows + 1) + (xb + 16.0) * (double)P.A.rows * nrhs,
+               8.0 * (double)P.A.nnz * nrhs);
   if (xtype == 0)
-    k_spmv<double2><<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, P.A.K.p,
-                                                                    P.A.M.p, sr, si, (const double2*)x, y);
+    MX_LAUNCH(k_spmv<double2><<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, P.A.K.p,
+                                                                    P.A.M.p, sr, si, (const double2*)x, y));
   else
-    k_spmv<float2><<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, P.A.K.p,
-                                                                   P.A.M.p, sr, si, (const float2*)x, y);
+    MX_LAUNCH(k_spmv<float2><<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, P.A.K.p,
+                                                                   P.A.M.p, sr, si, (const float2*)x, y));
   MX_CHECK_LAUNCH();
 }
 
@@ -167,9 +171,15 @@ void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, i
   const int64_t work = P.fine.n_dof * nrhs;
   const int32_t* tp = coarse ? P.R0T.rowptr.p : nullptr;
   const unsigned grid = grid_for(work, 256, 152LL * 32);
+  const double lsz = mixed ? 8.0 : 16.0, zb = ztype == 0 ? 16.0 : 8.0;
+  ProfScope ps(K_SCATTER, s, 1,
+               (levels & 1 ? (lsz * nrhs + 4.0) * (double)P.sum_local : 0.0) + 4.0 * (P.fine.n_dof + 1) +
+                   (coarse ? 12.0 * P.R0T.nnz + 4.0 * P.fine.n_dof + lsz * (double)P.n_c * nrhs : 0.0) +
+                   zb * (double)work,
+               (levels & 1 ? 2.0 * (double)P.sum_local * nrhs : 0.0) + (coarse ? 4.0 * (double)P.R0T.nnz * nrhs : 0.0));
 #define MX_SCATTER(LT, CT, ZT)                                                                            \
-  k_scatter<LT, CT, ZT><<<grid, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p, (const LT*)W.loc.p, tp, \
-                                             P.R0T.col.p, P.R0T.val.p, (const CT*)W.yc.p, levels & 1, (ZT*)z)
+  MX_LAUNCH(k_scatter<LT, CT, ZT><<<grid, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p, (const LT*)W.loc.p, tp, \
+                                             P.R0T.col.p, P.R0T.val.p, (const CT*)W.yc.p, levels & 1, (ZT*)z))
   if (mixed) {
     if (ztype == 0) MX_SCATTER(float2, float2, double2);
     else MX_SCATTER(float2, float2, float2);
@@ -440,29 +450,36 @@ __global__ void k_copy_norm(int nrhs, const double* beta, double* bnorm) {
 
 template <int RP>
 static void launch_dots(Workspace& W, int64_t n, int nvec, int with_norm, const double2* V, cudaStream_t s) {
-  k_dots<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, with_norm, V, W.w.p, W.active.p, W.hpart.p);
+  MX_LAUNCH(k_dots<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, with_norm, V, W.w.p, W.active.p, W.hpart.p));
 }
 template <int RP>
 static void launch_update(Workspace& W, int64_t n, int nvec, cudaStream_t s) {
-  k_orth_update<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, W.V.p, W.h2.p, W.active.p, W.w.p, W.npart.p);
+  MX_LAUNCH(k_orth_update<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, W.V.p, W.h2.p, W.active.p, W.w.p, W.npart.p));
 }
 
 static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s) {
   const int nr = W.nrhs;
-  if (nr <= 1) launch_dots<1>(W, n, nvec, with_norm, W.V.p, s);
-  else if (nr <= 2) launch_dots<2>(W, n, nvec, with_norm, W.V.p, s);
-  else if (nr <= 4) launch_dots<4>(W, n, nvec, with_norm, W.V.p, s);
-  else if (nr <= 8) launch_dots<8>(W, n, nvec, with_norm, W.V.p, s);
-  else if (nr <= 16) launch_dots<16>(W, n, nvec, with_norm, W.V.p, s);
-  else launch_dots<32>(W, n, nvec, with_norm, W.V.p, s);
-  MX_CHECK_LAUNCH();
+  {
+    // V_0..V_{nvec-1} and w read once each
+    ProfScope ps(K_DOTS, s, 1, 16.0 * (nvec + 1) * (double)n * nr, 8.0 * (nvec + with_norm) * (double)n * nr);
+    if (nr <= 1) launch_dots<1>(W, n, nvec, with_norm, W.V.p, s);
+    else if (nr <= 2) launch_dots<2>(W, n, nvec, with_norm, W.V.p, s);
+    else if (nr <= 4) launch_dots<4>(W, n, nvec, with_norm, W.V.p, s);
+    else if (nr <= 8) launch_dots<8>(W, n, nvec, with_norm, W.V.p, s);
+    else if (nr <= 16) launch_dots<16>(W, n, nvec, with_norm, W.V.p, s);
+    else launch_dots<32>(W, n, nvec, with_norm, W.V.p, s);
+    MX_CHECK_LAUNCH();
+  }
   const int total = nvec + with_norm;
-  k_reduce_dots<<<grid_for((int64_t)total * nr, 128), 128, 0, s>>>(W.nblk, total, nr, W.hpart.p, W.h2.p);
+  ProfScope ps(K_ARNOLDI_SMALL, s);
+  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * nr, 128), 128, 0, s>>>(W.nblk, total, nr, W.hpart.p, W.h2.p));
   MX_CHECK_LAUNCH();
 }
 
 static void orth_update(Workspace& W, int64_t n, int nvec, cudaStream_t s) {
   const int nr = W.nrhs;
+  // V_0..V_{nvec-1} read once, w read and written once
+  ProfScope ps(K_ORTH_UPDATE, s, 1, 16.0 * (nvec + 2) * (double)n * nr, 8.0 * (nvec + 0.25) * (double)n * nr);
   if (nr <= 1) launch_update<1>(W, n, nvec, s);
   else if (nr <= 2) launch_update<2>(W, n, nvec, s);
   else if (nr <= 4) launch_update<4>(W, n, nvec, s);
@@ -474,7 +491,8 @@ static void orth_update(Workspace& W, int64_t n, int nvec, cudaStream_t s) {
 
 static void true_residual(Problem& P, Workspace& W, cudaStream_t s) {
   spmv(P, P.xi_prob, W.x.p, 0, W.r.p, W.nrhs, s);
-  k_residual<<<W.nblk, 256, 0, s>>>(W.n, W.nrhs, W.b.p, W.r.p, W.npart.p);
+  ProfScope ps(K_RESIDUAL, s, 1, 48.0 * (double)W.n * W.nrhs, 6.0 * (double)W.n * W.nrhs);
+  MX_LAUNCH(k_residual<<<W.nblk, 256, 0, s>>>(W.n, W.nrhs, W.b.p, W.r.p, W.npart.p));
   MX_CHECK_LAUNCH();
 }
 
@@ -500,10 +518,10 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
   MX_CUDA(cudaMemsetAsync(W.x.p, 0, nv * sizeof(double2), s));
   // ||b||: residual of x = 0
   MX_CUDA(cudaMemsetAsync(W.r.p, 0, nv * sizeof(double2), s));
-  k_residual<<<W.nblk, 256, 0, s>>>(n, nrhs, W.b.p, W.r.p, W.npart.p);
+  MX_LAUNCH(k_residual<<<W.nblk, 256, 0, s>>>(n, nrhs, W.b.p, W.r.p, W.npart.p));
   MX_CUDA(cudaMemsetAsync(W.active.p, 0, nrhs * 4, s));
-  k_restart<<<1, 32, 0, s>>>(W.nblk, nrhs, m, W.npart.p, W.bnorm.p, -1.0, W.active.p, beta.p, W.g.p);
-  k_copy_norm<<<1, 32, 0, s>>>(nrhs, beta.p, W.bnorm.p);
+  MX_LAUNCH(k_restart<<<1, 32, 0, s>>>(W.nblk, nrhs, m, W.npart.p, W.bnorm.p, -1.0, W.active.p, beta.p, W.g.p));
+  MX_LAUNCH(k_copy_norm<<<1, 32, 0, s>>>(nrhs, beta.p, W.bnorm.p));
   launches += 3;
   MX_CHECK_LAUNCH();
   MX_CUDA(cudaMemcpyAsync(bn.data(), W.bnorm.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
@@ -515,7 +533,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     if (!act[r]) { done[r] = 1; rel[r] = 0; estv[r] = 0; }
   }
   MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
-  k_scale_v0<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p);
+  MX_LAUNCH(k_scale_v0<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p));
   MX_CHECK_LAUNCH();
   ++launches;
 
@@ -539,14 +557,16 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
         }
         dots(W, n, j + 1, pass == 0 ? 1 : 0, s);
         orth_update(W, n, j + 1, s);
-        k_arnoldi_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, pass, W.h2.p, W.npart.p, W.H.p, W.wnorm0.p,
-                                          W.active.p, W.flags.p);
+        ProfScope ps(K_ARNOLDI_SMALL, s);
+        MX_LAUNCH(k_arnoldi_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, pass, W.h2.p, W.npart.p, W.H.p, W.wnorm0.p,
+                                          W.active.p, W.flags.p));
         MX_CHECK_LAUNCH();
         launches += 4;
       }
-      k_normalize<<<gv, 256, 0, s>>>(nv, nrhs, j, m, W.H.p, W.active.p, W.w.p, W.V.p + (int64_t)(j + 1) * nv);
-      k_givens<<<1, 32, 0, s>>>(nrhs, j, m, tol, W.bnorm.p, W.H.p, W.cs.p, W.sn.p, W.g.p, W.active.p, W.est.p,
-                                W.flags.p);
+      ProfScope ps(K_ARNOLDI_SMALL, s, 2, 32.0 * (double)nv, 2.0 * (double)nv);
+      MX_LAUNCH(k_normalize<<<gv, 256, 0, s>>>(nv, nrhs, j, m, W.H.p, W.active.p, W.w.p, W.V.p + (int64_t)(j + 1) * nv));
+      MX_LAUNCH(k_givens<<<1, 32, 0, s>>>(nrhs, j, m, tol, W.bnorm.p, W.H.p, W.cs.p, W.sn.p, W.g.p, W.active.p, W.est.p,
+                                W.flags.p));
       MX_CHECK_LAUNCH();
       launches += 2;
       MX_CUDA(cudaMemcpyAsync(W.h_small, W.est.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
@@ -567,14 +587,19 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     // x += Z y for the right-hand sides that ran in this cycle
     for (int r = 0; r < nrhs; ++r) if (!start_active[r]) kcols[r] = 0;
     MX_CUDA(cudaMemcpyAsync(dk.p, kcols.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
-    k_backsolve<<<1, 32, 0, s>>>(nrhs, m, dk.p, W.H.p, W.g.p, W.y.p);
-    if (mixed) k_update_x<float2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const float2*)W.Z.p, W.y.p, W.x.p);
-    else k_update_x<double2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const double2*)W.Z.p, W.y.p, W.x.p);
+    {
+      int kmax = 0;
+      for (int r = 0; r < nrhs; ++r) kmax = std::max(kmax, kcols[r]);
+      ProfScope ps(K_UPDATE_X, s, 2, ((double)zsz * kmax + 32.0) * (double)nv, 8.0 * kmax * (double)nv);
+    MX_LAUNCH(k_backsolve<<<1, 32, 0, s>>>(nrhs, m, dk.p, W.H.p, W.g.p, W.y.p));
+    if (mixed) MX_LAUNCH(k_update_x<float2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const float2*)W.Z.p, W.y.p, W.x.p));
+    else MX_LAUNCH(k_update_x<double2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const double2*)W.Z.p, W.y.p, W.x.p));
     MX_CHECK_LAUNCH();
+    }
     true_residual(P, W, s);
     launches += 4;
     // restart set-up for every right-hand side that is not finished
-    k_restart<<<1, 32, 0, s>>>(W.nblk, nrhs, m, W.npart.p, W.bnorm.p, tol, W.active.p, beta.p, W.g.p);
+    MX_LAUNCH(k_restart<<<1, 32, 0, s>>>(W.nblk, nrhs, m, W.npart.p, W.bnorm.p, tol, W.active.p, beta.p, W.g.p));
     MX_CHECK_LAUNCH();
     ++launches;
     MX_CUDA(cudaMemcpyAsync(W.h_small, beta.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
@@ -594,7 +619,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     if (!any) break;
     ++restarts;
     MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
-    k_scale_v0<<<gv, 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p);
+    MX_LAUNCH(k_scale_v0<<<gv, 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p));
     MX_CHECK_LAUNCH();
     ++launches;
   }

@@ -231,23 +231,46 @@ __global__ void __launch_bounds__(256) k_lu_update(BandBatch B, T2* A, int k0) {
 }
 
 template <typename T2>
-void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s) {
+void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s,
+             const int32_t* hn, const int32_t* hb, int kid_update) {
   const int chunks = (max_span + 255) / 256;
   const int tiles = (max_span + 63) / 64;
+  const double esz = sizeof(T2);
   for (int k0 = 0; k0 < max_n; k0 += NB) {
-    k_lu_diag<T2><<<B.count, 256, 0, s>>>(B, A, k0, status);
-    MX_CHECK_LAUNCH();
-    if (max_span > 0) {
-      k_lu_panel<T2><<<dim3(B.count, 2 * chunks), 256, 0, s>>>(B, A, k0);
+    // algorithmic work of this step over the batch (complex MAC = 8 flops)
+    double upd_flops = 0, upd_bytes = 0, pan_flops = 0, pan_bytes = 0;
+    if (hn && hb)
+      for (int m = 0; m < B.count; ++m) {
+        if (k0 >= hn[m]) continue;
+        const double kb = std::min(NB, hn[m] - k0);
+        const double span = std::max(0, std::min(hn[m], k0 + (int)kb + hb[m]) - (k0 + (int)kb));
+        upd_flops += 8.0 * span * span * kb;
+        upd_bytes += esz * (2.0 * span * span + 2.0 * span * kb);
+        pan_flops += 8.0 * span * kb * kb;
+        pan_bytes += esz * 4.0 * span * kb;
+      }
+    {
+      ProfScope ps(kid_update < 0 ? K_LU_DIAG : kid_update, s);
+      MX_LAUNCH(k_lu_diag<T2><<<B.count, 256, 0, s>>>(B, A, k0, status));
       MX_CHECK_LAUNCH();
-      k_lu_update<T2><<<dim3(B.count, tiles * tiles), 256, 0, s>>>(B, A, k0);
+    }
+    if (max_span > 0) {
+      {
+        ProfScope ps(kid_update < 0 ? K_LU_PANEL : kid_update, s, 1, pan_bytes, pan_flops);
+        MX_LAUNCH(k_lu_panel<T2><<<dim3(B.count, 2 * chunks), 256, 0, s>>>(B, A, k0));
+        MX_CHECK_LAUNCH();
+      }
+      ProfScope ps(kid_update < 0 ? K_LU_UPDATE : kid_update, s, 1, upd_bytes, upd_flops);
+      MX_LAUNCH(k_lu_update<T2><<<dim3(B.count, tiles * tiles), 256, 0, s>>>(B, A, k0));
       MX_CHECK_LAUNCH();
     }
   }
 }
 
-template void band_lu<double2>(const BandBatch&, double2*, int, int, int32_t*, cudaStream_t);
-template void band_lu<float2>(const BandBatch&, float2*, int, int, int32_t*, cudaStream_t);
+template void band_lu<double2>(const BandBatch&, double2*, int, int, int32_t*, cudaStream_t, const int32_t*,
+                               const int32_t*, int);
+template void band_lu<float2>(const BandBatch&, float2*, int, int, int32_t*, cudaStream_t, const int32_t*,
+                              const int32_t*, int);
 
 // ---- host: extraction and factorisation -------------------------------------------
 static int round4(int x) { return (x + 3) & ~3; }
@@ -271,15 +294,18 @@ void extract_minors(Problem& P) {
   DevBuf<int32_t> band(P.n_sub);
   MX_CUDA(cudaMemsetAsync(band.p, 0, band.bytes(), s));
   a.band = band.p;
-  k_extract<float2, false><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a);
+  MX_LAUNCH(k_extract<float2, false><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a));
   MX_CHECK_LAUNCH();
   P.h_band.assign(P.n_sub, 0);
   MX_CUDA(cudaMemcpyAsync(P.h_band.data(), band.p, band.bytes(), cudaMemcpyDeviceToHost, s));
   MX_CUDA(cudaStreamSynchronize(s));
   P.h_ld.assign(P.n_sub, 0);
   P.h_mat_off.assign(P.n_sub + 1, 0);
+  P.band_entries = 0;
   for (int l = 0; l < P.n_sub; ++l) {
     if (P.dense_local) P.h_band[l] = P.h_nl[l] - 1;
+    const int64_t nn = P.h_nl[l], bb = std::min<int64_t>(P.h_band[l], nn - 1);
+    P.band_entries += nn * (2 * bb + 1) - bb * (bb + 1);  // entries with |i - j| <= b
     P.h_ld[l] = round4(2 * P.h_band[l] + 1);
     P.h_mat_off[l + 1] = P.h_mat_off[l] + (int64_t)P.h_ld[l] * P.h_nl[l];
   }
@@ -297,24 +323,92 @@ void extract_minors(Problem& P) {
   a.moff = P.mat_off.p;
   a.out = P.factors.p;
   if (P.precision == MX_MIXED)
-    k_extract<float2, true><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a);
+    MX_LAUNCH(k_extract<float2, true><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a));
   else
-    k_extract<double2, true><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a);
+    MX_LAUNCH(k_extract<double2, true><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a));
   MX_CHECK_LAUNCH();
   MX_CUDA(cudaStreamSynchronize(s));
   P.minors_ready = true;
   P.factored = false;
 }
 
+// Inverses of the NB x NB diagonal blocks of L (unit lower) and U (upper) of every
+// factored band matrix: block q of matrix m goes to Dinv + doff[m] + q * 2 NB^2 as two
+// column-major NB x NB blocks [L_qq^{-1}, U_qq^{-1}] (zero outside the matrix). The sweeps
+// then apply each diagonal block as a small matrix-vector product instead of a
+// sequential substitution. One block per (matrix, diagonal block), thread j = column j.
+template <typename T2>
+__global__ void k_invert_diag(BandBatch B, const T2* A, const int64_t* doff, T2* Dinv) {
+  __shared__ T2 L[NB][NB + 1], U[NB][NB + 1];
+  const int m = blockIdx.x, q = blockIdx.y;
+  const int n = B.n[m], b = B.b[m], ld = B.ld[m];
+  const int64_t off = B.off[m];
+  const int c0 = q * NB;
+  if (c0 >= n) return;
+  const int kb = min(NB, n - c0);
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int i = t % NB, k = t / NB;
+    const bool in = i < kb && k < kb && abs(i - k) <= b;
+    const T2 v = in ? A[bidx(off, ld, b, c0 + i, c0 + k)] : czero<T2>();
+    L[i][k] = (i > k) ? v : czero<T2>();
+    U[i][k] = (i <= k) ? v : czero<T2>();
+  }
+  __syncthreads();
+  T2* out = Dinv + doff[m] + (int64_t)q * 2 * NB * NB;
+  const int j = threadIdx.x;
+  if (j < NB) {
+    T2 x[NB];
+    // L x = e_j (unit lower), forward
+    for (int i = 0; i < NB; ++i) {
+      T2 v = (i == j) ? mk(decltype(T2::x)(1), decltype(T2::x)(0)) : czero<T2>();
+      for (int k = 0; k < i; ++k) cfms(v, L[i][k], x[k]);
+      x[i] = (i < kb && j < kb) ? v : czero<T2>();
+    }
+    for (int i = 0; i < NB; ++i) out[(int64_t)j * NB + i] = x[i];
+    // U x = e_j, backward
+    for (int i = NB - 1; i >= 0; --i) {
+      T2 v = (i == j) ? mk(decltype(T2::x)(1), decltype(T2::x)(0)) : czero<T2>();
+      for (int k = i + 1; k < NB; ++k) cfms(v, U[i][k], x[k]);
+      x[i] = (i < kb && j < kb) ? cmul(v, crcp(U[i][i])) : czero<T2>();
+    }
+    for (int i = 0; i < NB; ++i) out[NB * NB + (int64_t)j * NB + i] = x[i];
+  }
+}
+
+template <typename T2>
+void invert_diag_blocks(const BandBatch& B, const T2* A, const int64_t* doff, T2* Dinv, int max_n, cudaStream_t s) {
+  const int nq = (max_n + NB - 1) / NB;
+  ProfScope ps(K_LU_DIAG, s);
+  MX_LAUNCH(k_invert_diag<T2><<<dim3(B.count, nq), 64, 0, s>>>(B, A, doff, Dinv));
+  MX_CHECK_LAUNCH();
+}
+template void invert_diag_blocks<float2>(const BandBatch&, const float2*, const int64_t*, float2*, int, cudaStream_t);
+template void invert_diag_blocks<double2>(const BandBatch&, const double2*, const int64_t*, double2*, int,
+                                          cudaStream_t);
+
 void factor_local(Problem& P) {
   if (!P.minors_ready) extract_minors(P);
   BandBatch B{P.n_sub, P.nl.p, P.band.p, P.ld.p, P.mat_off.p};
   int max_span = 0;
   for (int l = 0; l < P.n_sub; ++l) max_span = std::max(max_span, std::min(P.h_band[l], P.h_nl[l]));
-  if (P.precision == MX_MIXED)
-    band_lu<float2>(B, reinterpret_cast<float2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream);
-  else
-    band_lu<double2>(B, reinterpret_cast<double2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream);
+  // offsets of the inverted diagonal blocks
+  std::vector<int64_t> doff(P.n_sub + 1, 0);
+  for (int l = 0; l < P.n_sub; ++l) doff[l + 1] = doff[l] + (int64_t)((P.h_nl[l] + NB - 1) / NB) * 2 * NB * NB;
+  P.dinv_off.alloc(P.n_sub + 1);
+  MX_CUDA(cudaMemcpyAsync(P.dinv_off.p, doff.data(), doff.size() * 8, cudaMemcpyHostToDevice, P.stream));
+  const size_t esz = P.precision == MX_MIXED ? sizeof(float2) : sizeof(double2);
+  P.dinv.alloc((size_t)doff[P.n_sub] * esz);
+  if (P.precision == MX_MIXED) {
+    band_lu<float2>(B, reinterpret_cast<float2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream,
+                    P.h_nl.data(), P.h_band.data(), -1);
+    invert_diag_blocks<float2>(B, reinterpret_cast<float2*>(P.factors.p), P.dinv_off.p,
+                               reinterpret_cast<float2*>(P.dinv.p), P.max_local, P.stream);
+  } else {
+    band_lu<double2>(B, reinterpret_cast<double2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream,
+                     P.h_nl.data(), P.h_band.data(), -1);
+    invert_diag_blocks<double2>(B, reinterpret_cast<double2*>(P.factors.p), P.dinv_off.p,
+                                reinterpret_cast<double2*>(P.dinv.p), P.max_local, P.stream);
+  }
   MX_CUDA(cudaStreamSynchronize(P.stream));
   P.minors_ready = false;
   P.factored = true;
@@ -335,10 +429,13 @@ struct SolveArgs {
   const int32_t* ld;
   const int64_t* moff;
   const void* factors;
+  const void* dinv;       // inverted diagonal blocks
+  const int64_t* doff;    // [n_sub] their offsets
   const void* v;  // [n][nrhs] c128 or c64 (right-hand side index fastest)
   int vtype;
   void* out;      // [sum_local][nrhs] of T2
   int win;        // window rows
+  double alg_bytes, alg_flops;  // algorithmic traffic / work of one launch (profiling)
 };
 
 template <typename T2>
@@ -348,56 +445,103 @@ __device__ inline T2 load_v(const void* v, int vtype, int64_t idx) {
   return conv<T2>(make_double2(f.x, f.y));
 }
 
+// x_blk = D r_blk for the kb x kb diagonal block (D = L_qq^{-1}, unit lower, or
+// D = U_qq^{-1}, upper; column-major NB x NB in global memory) on the window rows
+// c0..c0+kb-1, all G right-hand sides. Every thread of the block takes part (256 threads).
+template <typename T2, int G, bool UPPER>
+__device__ inline void diag_apply(const T2* __restrict__ D, int c0, int kb, T2* W, int win, T2 (*Ds)[NB + 1]) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t < NB * NB; t += 256) Ds[t % NB][t / NB] = D[t];
+  __syncthreads();
+  constexpr int PER = (NB * G + 255) / 256;
+  const int s0 = c0 % win;
+  T2 out[PER];
+#pragma unroll
+  for (int c = 0; c < PER; ++c) {
+    const int t = tid + 256 * c;
+    out[c] = czero<T2>();
+    if (t < kb * G) {
+      const int i = t / G, g = t % G;
+      // D is zero outside its triangle and beyond kb; window slots always hold finite values
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        int sk = s0 + k;
+        if (sk >= win) sk -= win;
+        cfma(out[c], Ds[i][k], W[sk * G + g]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < PER; ++c) {
+    const int t = tid + 256 * c;
+    if (t < kb * G) W[((c0 + t / G) % win) * G + t % G] = out[c];
+  }
+  __syncthreads();
+}
+
+// W[i] -= sum_k F(i, k) W[k] over the block columns k in [c0, c0 + kb) ∩ [klo, khi) for one
+// window row i and all G right-hand sides. Fixed 32-column trip count, factor entries
+// loaded 16 at a time ahead of their use (out-of-range entries load as zero; window
+// slots always hold finite values, so the extra products add exact zeros).
 template <typename T2, int G>
-__global__ void __launch_bounds__(256) k_local_solve(SolveArgs a) {
+__device__ __forceinline__ void row_update(const T2* __restrict__ F, int64_t off, int ld, int b, int i, int c0, int kb,
+                                           int klo, int khi, T2* W, int win) {
+  const int si = i % win, s0 = c0 % win;
+  T2 acc[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) acc[g] = W[si * G + g];
+#pragma unroll
+  for (int kk = 0; kk < NB; kk += 16) {
+    T2 l[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = c0 + kk + u;
+      l[u] = (kk + u < kb && k >= klo && k < khi) ? F[bidx(off, ld, b, i, k)] : czero<T2>();
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      int sk = s0 + kk + u;
+      if (sk >= win) sk -= win;
+#pragma unroll
+      for (int g = 0; g < G; ++g) cfms(acc[g], l[u], W[sk * G + g]);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) W[si * G + g] = acc[g];
+}
+
+template <typename T2, int G>
+__global__ void __launch_bounds__(256, 2) k_local_solve(SolveArgs a) {
   extern __shared__ unsigned char smem_raw[];
   T2* W = reinterpret_cast<T2*>(smem_raw);  // [win][G]
+  __shared__ T2 Ds[NB][NB + 1];             // diagonal block of the current step
   const int groups = (a.nrhs + G - 1) / G;
   const int l = blockIdx.x / groups;
   const int g0 = (blockIdx.x % groups) * G;
   const int gn = min(G, a.nrhs - g0);
   const int n = a.nl[l], b = a.band[l], ld = a.ld[l];
   const int64_t off = a.moff[l], pos0 = a.offsets[l];
-  const T2* F = reinterpret_cast<const T2*>(a.factors);
+  const T2* __restrict__ F = reinterpret_cast<const T2*>(a.factors);
+  const T2* Dinv = reinterpret_cast<const T2*>(a.dinv);
+  const int64_t doff = a.doff[l];
   T2* out = reinterpret_cast<T2*>(a.out);
   const int win = a.win;
   const int tid = threadIdx.x, nt = blockDim.x;
 
   // ---- forward sweep: L y = R^l v
-  for (int t = tid; t < min(n, win) * G; t += nt) {
+  for (int t = tid; t < win * G; t += nt) {
     const int i = t / G, g = t % G;
-    W[(i % win) * G + g] = (g < gn) ? load_v<T2>(a.v, a.vtype, (int64_t)a.lists[pos0 + i] * a.nrhs + g0 + g) : czero<T2>();
+    W[t] = (i < n && g < gn) ? load_v<T2>(a.v, a.vtype, (int64_t)a.lists[pos0 + i] * a.nrhs + g0 + g) : czero<T2>();
   }
   __syncthreads();
   for (int c0 = 0; c0 < n; c0 += NB) {
     const int c1 = min(c0 + NB, n);
-    // diagonal block (unit lower), column by column
-    for (int k = c0; k < c1 - 1; ++k) {
-      for (int t = tid; t < (c1 - k - 1) * G; t += nt) {
-        const int i = k + 1 + t / G, g = t % G;
-        if (i - k <= b) {
-          T2 v = W[(i % win) * G + g];
-          cfms(v, F[bidx(off, ld, b, i, k)], W[(k % win) * G + g]);
-          W[(i % win) * G + g] = v;
-        }
-      }
-      __syncthreads();
-    }
+    // diagonal block: x_blk = L_qq^{-1} r_blk with the precomputed inverse
+    diag_apply<T2, G, false>(Dinv + doff + (int64_t)(c0 / NB) * 2 * NB * NB, c0, c1 - c0, W, win, Ds);
     // rows below the block within the band
     const int r1 = min(n, c1 + b);
-    for (int i = c1 + tid; i < r1; i += nt) {
-      T2 acc[G];
-#pragma unroll
-      for (int g = 0; g < G; ++g) acc[g] = W[(i % win) * G + g];
-      const int kstart = max(c0, i - b);
-      for (int k = kstart; k < c1; ++k) {
-        const T2 lik = F[bidx(off, ld, b, i, k)];
-#pragma unroll
-        for (int g = 0; g < G; ++g) cfms(acc[g], lik, W[(k % win) * G + g]);
-      }
-#pragma unroll
-      for (int g = 0; g < G; ++g) W[(i % win) * G + g] = acc[g];
-    }
+    for (int i = c1 + tid; i < r1; i += nt) row_update<T2, G>(F, off, ld, b, i, c0, c1 - c0, max(c0, i - b), c1, W, win);
     __syncthreads();
     // retire rows c0..c1-1 (y), load rows entering the window
     for (int t = tid; t < (c1 - c0) * G; t += nt) {
@@ -421,38 +565,11 @@ __global__ void __launch_bounds__(256) k_local_solve(SolveArgs a) {
   __syncthreads();
   for (int blk = nblk - 1; blk >= 0; --blk) {
     const int c0 = blk * NB, c1 = min(c0 + NB, n);
-    for (int k = c1 - 1; k >= c0; --k) {
-      // x_k = r_k / U_kk, then r_i -= U_ik x_k for c0 <= i < k
-      if (tid < G) {
-        const T2 d = F[bidx(off, ld, b, k, k)];
-        W[(k % win) * G + tid] = cmul(W[(k % win) * G + tid], crcp(d));
-      }
-      __syncthreads();
-      for (int t = tid; t < (k - c0) * G; t += nt) {
-        const int i = c0 + t / G, g = t % G;
-        if (k - i <= b) {
-          T2 v = W[(i % win) * G + g];
-          cfms(v, F[bidx(off, ld, b, i, k)], W[(k % win) * G + g]);
-          W[(i % win) * G + g] = v;
-        }
-      }
-      __syncthreads();
-    }
+    // diagonal block: x_blk = U_qq^{-1} r_blk with the precomputed inverse
+    diag_apply<T2, G, true>(Dinv + doff + (int64_t)(c0 / NB) * 2 * NB * NB + NB * NB, c0, c1 - c0, W, win, Ds);
     // rows above the block within the band
     const int r0 = max(0, c0 - b);
-    for (int i = r0 + tid; i < c0; i += nt) {
-      T2 acc[G];
-#pragma unroll
-      for (int g = 0; g < G; ++g) acc[g] = W[(i % win) * G + g];
-      const int kend = min(c1, i + b + 1);
-      for (int k = c0; k < kend; ++k) {
-        const T2 uik = F[bidx(off, ld, b, i, k)];
-#pragma unroll
-        for (int g = 0; g < G; ++g) cfms(acc[g], uik, W[(k % win) * G + g]);
-      }
-#pragma unroll
-      for (int g = 0; g < G; ++g) W[(i % win) * G + g] = acc[g];
-    }
+    for (int i = r0 + tid; i < c0; i += nt) row_update<T2, G>(F, off, ld, b, i, c0, c1 - c0, c0, min(c1, i + b + 1), W, win);
     __syncthreads();
     for (int t = tid; t < (c1 - c0) * G; t += nt) {
       const int i = c0 + t / G, g = t % G;
@@ -468,14 +585,16 @@ __global__ void __launch_bounds__(256) k_local_solve(SolveArgs a) {
 template <typename T2, int G>
 static void launch_local_solve(const SolveArgs& a, int win, cudaStream_t s) {
   const size_t smem = (size_t)win * G * sizeof(T2);
-  static bool configured = false;
-  if (!configured) {
-    MX_CUDA(cudaFuncSetAttribute(k_local_solve<T2, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    configured = true;
+  // dynamic window + the static diagonal-block tile must fit the 227 KB per-block limit
+  MX_REQUIRE(smem + sizeof(T2) * NB * (NB + 1) <= 227 * 1024, MX_EINVAL, "local solve window exceeds shared memory");
+  static size_t configured = 0;
+  if (smem > configured) {
+    MX_CUDA(cudaFuncSetAttribute(k_local_solve<T2, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
   }
-  MX_REQUIRE(smem <= 227 * 1024, MX_EINVAL, "local solve window exceeds shared memory");
   const int groups = (a.nrhs + G - 1) / G;
-  k_local_solve<T2, G><<<a.n_sub * groups, 256, smem, s>>>(a);
+  ProfScope ps(K_LOCAL_SOLVE, s, 1, a.alg_bytes, a.alg_flops);
+  MX_LAUNCH(k_local_solve<T2, G><<<a.n_sub * groups, 256, smem, s>>>(a));
   MX_CHECK_LAUNCH();
 }
 
@@ -492,12 +611,23 @@ void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs) {
   a.ld = P.ld.p;
   a.moff = P.mat_off.p;
   a.factors = P.factors.p;
+  a.dinv = P.dinv.p;
+  a.doff = P.dinv_off.p;
   a.v = v;
   a.vtype = vtype;
   a.out = loc;
   int bmax = 0;
   for (int l = 0; l < P.n_sub; ++l) bmax = std::max(bmax, std::min(P.h_band[l], P.h_nl[l]));
-  a.win = std::min(P.max_local, bmax + NB);
+  // window rows: at least one block of NB (the slot arithmetic in row_update / diag_apply
+  // wraps once, so it needs win >= NB), at most the largest subdomain or band + block
+  a.win = std::max(NB, std::min(P.max_local, bmax + NB));
+  MX_REQUIRE(a.win >= NB, MX_EINVAL, "local solve window smaller than one block");
+  {
+    const double esz = P.precision == MX_MIXED ? 8.0 : 16.0;
+    // factors read once, right-hand sides gathered once (c128), solutions written once
+    a.alg_bytes = esz * (double)P.band_entries + (16.0 + esz) * (double)P.sum_local * nrhs;
+    a.alg_flops = 8.0 * (double)P.band_entries * nrhs;
+  }
   const bool mixed = P.precision == MX_MIXED;
   // right-hand sides per block: the window must fit in shared memory
   const size_t esz = mixed ? 8 : 16;

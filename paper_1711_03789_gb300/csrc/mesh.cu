@@ -75,16 +75,16 @@ void build_mesh(MeshDev& m, int n, cudaStream_t s) {
   const int64_t total = (int64_t)(n + 1) * (n + 1) * (n + 1) * 7;
   MX_REQUIRE(total < (1LL << 31), MX_EINVAL, "mesh too large for 32-bit edge keys");
   DevBuf<int32_t> flag(total), pre(total + 1);
-  k_edge_flags<<<grid_for(total, 256), 256, 0, s>>>(n, flag.p);
+  MX_LAUNCH(k_edge_flags<<<grid_for(total, 256), 256, 0, s>>>(n, flag.p));
   MX_CHECK_LAUNCH();
   m.n_dof = exclusive_scan_i32(flag.p, pre.p, total, s);
   m.edge_dof.alloc(total);
   m.dof_key.alloc(std::max<int64_t>(m.n_dof, 1));
-  k_edge_numbers<<<grid_for(total, 256), 256, 0, s>>>(total, flag.p, pre.p, m.edge_dof.p, m.dof_key.p);
+  MX_LAUNCH(k_edge_numbers<<<grid_for(total, 256), 256, 0, s>>>(total, flag.p, pre.p, m.edge_dof.p, m.dof_key.p));
   MX_CHECK_LAUNCH();
   const int64_t ntet = 6LL * n * n * n;
   m.tet2dof.alloc(ntet * 6);
-  k_tet2dof<<<grid_for(ntet, 256), 256, 0, s>>>(n, m.edge_dof.p, m.tet2dof.p);
+  MX_LAUNCH(k_tet2dof<<<grid_for(ntet, 256), 256, 0, s>>>(n, m.edge_dof.p, m.tet2dof.p));
   MX_CHECK_LAUNCH();
   MX_CUDA(cudaStreamSynchronize(s));
 }
@@ -253,7 +253,7 @@ void build_subdomains(Problem& P) {
   MX_CUDA(cudaMemcpyAsync(P.offsets.p, P.h_offsets.data(), (P.n_sub + 1) * 8, cudaMemcpyHostToDevice, s));
   MX_CUDA(cudaMemcpyAsync(P.nl.p, P.h_nl.data(), P.n_sub * 4, cudaMemcpyHostToDevice, s));
   BoxArgs ba{n, dbox.p, P.offsets.p, P.fine.edge_dof.p, P.lists.p};
-  k_box_lists<<<P.n_sub, 256, 0, s>>>(ba);
+  MX_LAUNCH(k_box_lists<<<P.n_sub, 256, 0, s>>>(ba));
   MX_CHECK_LAUNCH();
 
   const int64_t nd = P.fine.n_dof;
@@ -261,14 +261,14 @@ void build_subdomains(Problem& P) {
   P.inv_ptr.alloc(nd + 1);
   InvArgs ia{n, P.core, P.overlap, N, nd, P.fine.dof_key.p, dbox.p, P.offsets.p, P.nl.p,
              P.lists.p, cnt.p, nullptr, nullptr};
-  k_inverse_map<false><<<grid_for(nd, 256), 256, 0, s>>>(ia);
+  MX_LAUNCH(k_inverse_map<false><<<grid_for(nd, 256), 256, 0, s>>>(ia));
   MX_CHECK_LAUNCH();
   const int64_t total = exclusive_scan_i32(cnt.p, P.inv_ptr.p, nd, s);
   MX_REQUIRE(total == P.sum_local, MX_EINVAL, "subdomain cover mismatch");
   P.inv_pos.alloc(P.sum_local);
   ia.ptr = P.inv_ptr.p;
   ia.pos = P.inv_pos.p;
-  k_inverse_map<true><<<grid_for(nd, 256), 256, 0, s>>>(ia);
+  MX_LAUNCH(k_inverse_map<true><<<grid_for(nd, 256), 256, 0, s>>>(ia));
   MX_CHECK_LAUNCH();
   MX_CUDA(cudaStreamSynchronize(s));
 }

@@ -79,12 +79,15 @@ struct Problem {
   // element type float2 (mixed) or double2 (plain), matrix l at mat_off[l] elements.
   bool dense_local = false;        // force b_l = n_l - 1 (full dense storage)
   std::vector<int32_t> h_band;     // [n_sub] half-bandwidths
+  int64_t band_entries = 0;        // sum over subdomains of entries with |i - j| <= b_l
   DevBuf<int32_t> band;
   std::vector<int64_t> h_mat_off;  // [n_sub + 1]
   std::vector<int32_t> h_ld;
   DevBuf<int64_t> mat_off;
   DevBuf<int32_t> ld;
   DevBuf<unsigned char> factors;
+  DevBuf<int64_t> dinv_off;        // [n_sub + 1] offsets of the inverted diagonal blocks
+  DevBuf<unsigned char> dinv;      // inverted NB x NB diagonal blocks of L and U
   bool factored = false;
   bool minors_ready = false;
 
@@ -98,6 +101,8 @@ struct Problem {
   DevBuf<float2> A0f;     // c64 copy of the factors (mixed)
   DevBuf<int32_t> c_meta; // n, b, ld of the coarse band matrix (device)
   DevBuf<int64_t> c_off;
+  DevBuf<double2> c_dinv; // inverted diagonal blocks of the coarse factors (FP64)
+  DevBuf<float2> c_dinvf; // c64 copy (mixed)
   DevBuf<int32_t> status; // [4] device error words: 0 local pivot, 1 coarse pivot, 2 timeout
 
   Workspace* ws = nullptr;
@@ -120,7 +125,10 @@ void build_coarse_restriction(Problem& P);
 void extract_minors(Problem& P);
 void factor_local(Problem& P);
 template <typename T2>
-void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s);
+void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s,
+             const int32_t* hn, const int32_t* hb, int kid_update);
+template <typename T2>
+void invert_diag_blocks(const BandBatch& B, const T2* A, const int64_t* doff, T2* Dinv, int max_n, cudaStream_t s);
 // z_l = (A^l)^{-1} R^l v for every l, written at the subdomain positions of `loc`
 // (element type of the factors), v [nrhs][n] c128 or c64 (vtype 0: c128, 1: c64).
 void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs);
