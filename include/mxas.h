@@ -194,6 +194,17 @@ MX_API int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels)
  * column-major n_l x n_l, c128 (host). Unit lower L below the diagonal, U on and above. */
 MX_API int mx_get_local(mx_handle h, int l, double* out);
 
+/* Batched inner products of the Gram-Schmidt step of the Arnoldi process (Sec. 5.2 recalls
+ * GMRES; the right-preconditioned GMRES of Sec. 6.1 orthogonalises each new vector
+ * against the basis): h[i][r] = sum_x conj(V_i[x][r]) w[x][r] for i < nvec, r < nrhs.
+ * V: nvec blocks [nvec][n][nrhs] c128 and w: [n][nrhs] c128, both device memory
+ * (right-hand side index fastest); h: [nvec][nrhs] c128, host or device. FP64 products
+ * and fixed-order reductions (deterministic). stream: a cudaStream_t (NULL = legacy default);
+ * the call synchronises it. Scratch for the block partial sums is allocated per call
+ * through the library's allocator. MX_EINVAL for nrhs outside 1..32, nvec < 1, n < 1 or
+ * host V / w. */
+MX_API int mx_dots(const void* V, const void* w, int64_t n, int nrhs, int nvec, void* h, void* stream);
+
 /* ---- Instrumentation ----------------------------------------------------------------- */
 
 /* Number of kernel launches made by the library since it was loaded (all handles). */

@@ -79,6 +79,7 @@ _sig = {
     "mx_spmv": (C.c_int, [H, P, P, C.c_int]),
     "mx_precond": (C.c_int, [H, P, P, C.c_int, C.c_int]),
     "mx_get_local": (C.c_int, [H, C.c_int, P]),
+    "mx_dots": (C.c_int, [P, P, C.c_int64, C.c_int, C.c_int, P, C.c_void_p]),
     "mx_launch_count": (C.c_int64, []),
     "mx_profile": (C.c_int, [C.c_int]),
     "mx_profile_read": (C.c_int, [P, P, P, P]),
@@ -264,6 +265,17 @@ def mx_get_local(h, l, n_l):
     out = np.empty((n_l, n_l), dtype=np.complex128)  # column-major content
     _check(lib.mx_get_local(h, int(l), _ptr(out)))
     return out.T.copy()  # row-major [i, j]
+
+
+def mx_dots(V, w, h=None, stream=0):
+    """h[i, r] = sum_x conj(V[i, x, r]) w[x, r]; V [nvec, n, nrhs], w [n, nrhs] complex128 CUDA
+    tensors; h [nvec, nrhs] (numpy or torch, host or CUDA; numpy by default)."""
+    nvec, n, nrhs = V.shape
+    assert tuple(w.shape) == (n, nrhs)
+    if h is None:
+        h = np.empty((nvec, nrhs), dtype=np.complex128)
+    _check(lib.mx_dots(_ptr(V), _ptr(w), n, nrhs, nvec, _ptr(h), C.c_void_p(int(stream))))
+    return h
 
 
 def mx_launch_count():

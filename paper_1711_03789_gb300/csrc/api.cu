@@ -385,6 +385,21 @@ int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels) {
   });
 }
 
+int mx_dots(const void* V, const void* w, int64_t n, int nrhs, int nvec, void* h, void* stream) {
+  return guard([&] {
+    MX_REQUIRE(V && w && h && n >= 1 && nrhs >= 1 && nrhs <= 32 && nvec >= 1, MX_EINVAL, "bad mx_dots arguments");
+    MX_REQUIRE(is_device_ptr(V) && is_device_ptr(w), MX_EINVAL, "mx_dots: V and w must be device memory");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int nblk = 2 * sm_count();
+    DevBuf<double2> partials((size_t)nblk * nvec * nrhs), res((size_t)nvec * nrhs);
+    DevBuf<int32_t> ones(nrhs);
+    fill_i32(ones.p, nrhs, 1, s);
+    batched_dots((const double2*)V, (const double2*)w, n, nrhs, nvec, res.p, partials.p, nblk, ones.p, s);
+    MX_CUDA(cudaMemcpyAsync(h, res.p, res.bytes(), cudaMemcpyDefault, s));
+    MX_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
 int mx_profile(int enable) {
   return guard([&] { prof_reset(enable != 0); });
 }

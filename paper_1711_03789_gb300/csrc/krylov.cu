@@ -496,6 +496,31 @@ static void true_residual(Problem& P, Workspace& W, cudaStream_t s) {
   MX_CHECK_LAUNCH();
 }
 
+__global__ void k_fill_i32(int n, int32_t v, int32_t* p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+void fill_i32(int32_t* p, int n, int32_t v, cudaStream_t s) {
+  MX_LAUNCH(k_fill_i32<<<1, 256, 0, s>>>(n, v, p));
+  MX_CHECK_LAUNCH();
+}
+
+void batched_dots(const double2* V, const double2* w, int64_t n, int nrhs, int nvec, double2* h, double2* partials,
+                  int nblk, const int32_t* ones, cudaStream_t s) {
+  MX_REQUIRE(nrhs >= 1 && nrhs <= 32 && nvec >= 1 && n >= 1 && nblk >= 1, MX_EINVAL, "bad batched_dots sizes");
+#define MX_DOTS(RP) MX_LAUNCH(k_dots<RP><<<nblk, 256, 0, s>>>(n, nrhs, nvec, 0, V, w, ones, partials))
+  if (nrhs <= 1) MX_DOTS(1);
+  else if (nrhs <= 2) MX_DOTS(2);
+  else if (nrhs <= 4) MX_DOTS(4);
+  else if (nrhs <= 8) MX_DOTS(8);
+  else if (nrhs <= 16) MX_DOTS(16);
+  else MX_DOTS(32);
+#undef MX_DOTS
+  MX_CHECK_LAUNCH();
+  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)nvec * nrhs, 128), 128, 0, s>>>(nblk, nvec, nrhs, partials, h));
+  MX_CHECK_LAUNCH();
+}
+
 int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, int restart, int max_it,
                 mx_rhs_stats* stats) {
   MX_REQUIRE(P.factored, MX_ENOTFACTORED, "mx_solve before mx_factor");

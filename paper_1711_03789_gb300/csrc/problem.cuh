@@ -147,5 +147,10 @@ void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, i
 int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, int restart,
                 int max_it, mx_rhs_stats* stats);
 void free_workspace(Problem& P);
+// h[i][r] = sum_x conj(V_i[x][r]) w[x][r], i < nvec; V [nvec][n][nrhs], w [n][nrhs] (device);
+// partials: nblk * nvec * nrhs entries of scratch; ones: nrhs flags equal to 1
+void batched_dots(const double2* V, const double2* w, int64_t n, int nrhs, int nvec, double2* h, double2* partials,
+                  int nblk, const int32_t* ones, cudaStream_t s);
+void fill_i32(int32_t* p, int n, int32_t v, cudaStream_t s);
 
 }  // namespace mx

@@ -225,3 +225,16 @@ def test_single_dof_mesh():
         x, st, rc = P.solve(np.array([[1.0 + 1.0j]]), tol=1e-12)
         A = fem.a_xi(*fem.assemble_KM(KuhnMesh(1)), 2.0, 1.0).toarray()
         assert abs(x[0, 0] - (1 + 1j) / A[0, 0]) < 1e-14
+
+
+@pytest.mark.parametrize("nvec,n,nrhs", [(1, 7, 1), (5, 40001, 3), (12, 100000, 16)])
+def test_batched_dots(nvec, n, nrhs):
+    """mx_dots against the definition h[i, r] = sum_x conj(V[i, x, r]) w[x, r] in FP64."""
+    V = inputs.random_complex(21, (nvec, n, nrhs))
+    w = inputs.random_complex(22, (n, nrhs))
+    he = np.einsum("ixr,xr->ir", V.conj(), w)
+    h = mx.mx_dots(torch.from_numpy(V).cuda(), torch.from_numpy(w).cuda())
+    assert np.abs(h - he).max() <= 1e-13 * np.sqrt(n) * np.abs(V).max() * np.abs(w).max()
+    hd = torch.zeros((nvec, nrhs), dtype=torch.complex128, device="cuda")
+    mx.mx_dots(torch.from_numpy(V).cuda(), torch.from_numpy(w).cuda(), hd)
+    assert np.array_equal(hd.cpu().numpy(), h)
