@@ -205,6 +205,19 @@ MX_API int mx_get_local(mx_handle h, int l, double* out);
  * host V / w. */
 MX_API int mx_dots(const void* V, const void* w, int64_t n, int nrhs, int nvec, void* h, void* stream);
 
+/* mx_dots for callers that cannot allocate device memory: a host framework that owns all
+ * device memory through its own pool, or code recording CUDA graphs that must not allocate
+ * between recordings. The paper has no counterpart; it is a deployment variant.
+ * Same arguments, layouts and results as mx_dots, but the block partial sums live in a
+ * fixed 4 MiB array inside the library's device image (held on every GPU that loads the
+ * library until the process exits), so the call allocates nothing. Limit: nvec * nrhs <=
+ * 16384, else MX_EINVAL with a message. The first call on a device looks the array's
+ * device address up (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. All calls on one device share the array: calls that overlap
+ * on the GPU (unordered streams or threads) race on it. Every word a call reads from the
+ * array is written earlier in the same call, so no clearing is needed between calls. */
+MX_API int mx_dots_noalloc(const void* V, const void* w, int64_t n, int nrhs, int nvec, void* h, void* stream);
+
 /* ---- Instrumentation ----------------------------------------------------------------- */
 
 /* Number of kernel launches made by the library since it was loaded (all handles). */

@@ -17,6 +17,6 @@ from ._lib import (  # noqa: F401
     mx_factor, mx_load_vector, mx_solve, mx_num_dofs, mx_info, mx_timings, mx_destroy,
     mx_get_mesh, mx_get_subdomains, mx_get_csr, mx_get_coarse_restriction, mx_spmv, mx_precond,
     mx_get_local, mx_set_allocator, use_torch_allocator,
-    mx_launch_count, mx_profile, mx_profile_read, mx_profile_name, mx_dots,
+    mx_launch_count, mx_profile, mx_profile_read, mx_profile_name, mx_dots, mx_dots_noalloc,
 )
 from .problem import Problem  # noqa: F401

@@ -80,6 +80,7 @@ _sig = {
     "mx_precond": (C.c_int, [H, P, P, C.c_int, C.c_int]),
     "mx_get_local": (C.c_int, [H, C.c_int, P]),
     "mx_dots": (C.c_int, [P, P, C.c_int64, C.c_int, C.c_int, P, C.c_void_p]),
+    "mx_dots_noalloc": (C.c_int, [P, P, C.c_int64, C.c_int, C.c_int, P, C.c_void_p]),
     "mx_launch_count": (C.c_int64, []),
     "mx_profile": (C.c_int, [C.c_int]),
     "mx_profile_read": (C.c_int, [P, P, P, P]),
@@ -275,6 +276,17 @@ def mx_dots(V, w, h=None, stream=0):
     if h is None:
         h = np.empty((nvec, nrhs), dtype=np.complex128)
     _check(lib.mx_dots(_ptr(V), _ptr(w), n, nrhs, nvec, _ptr(h), C.c_void_p(int(stream))))
+    return h
+
+
+def mx_dots_noalloc(V, w, h=None, stream=0):
+    """mx_dots without any device allocation (block partials in the library's fixed 4 MiB
+    device array); for callers that cannot allocate. Requires nvec * nrhs <= 16384."""
+    nvec, n, nrhs = V.shape
+    assert tuple(w.shape) == (n, nrhs)
+    if h is None:
+        h = np.empty((nvec, nrhs), dtype=np.complex128)
+    _check(lib.mx_dots_noalloc(_ptr(V), _ptr(w), n, nrhs, nvec, _ptr(h), C.c_void_p(int(stream))))
     return h
 
 
