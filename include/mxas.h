@@ -103,6 +103,16 @@ MX_API int mx_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*rele
  * effect at the next mx_factor. For comparison runs. */
 MX_API int mx_set_dense_local(mx_handle h, int dense);
 
+/* Tuning knobs (used by the autotuner); value 0 restores the default.
+ *   MX_TUNE_LOCAL_RHS_GROUP: most right-hand sides one local-solve block handles
+ *   (power of two, 1..16; default 16). Smaller groups run more blocks per subdomain. */
+#define MX_TUNE_LOCAL_RHS_GROUP 1
+/*   MX_TUNE_LU_TENSOR: trailing update of the MX_MIXED local LU; 3 = tcgen05 tensor cores
+ *   with three TF32 products per term (hi*hi + hi*lo + lo*hi, close to FP32), 1 = one TF32
+ *   product, 0 (default) = FP32 CUDA cores. MX_PLAIN_FP64 always uses FP64 CUDA cores. */
+#define MX_TUNE_LU_TENSOR 2
+MX_API int mx_set_tuning(mx_handle h, int key, int value);
+
 /* Message of the last error on the calling thread ("" if none). */
 MX_API const char* mx_last_error(void);
 

@@ -61,6 +61,7 @@ _sig = {
     "mx_last_error": (C.c_char_p, []),
     "mx_set_allocator": (C.c_int, [_ALLOC, _FREE, C.c_void_p]),
     "mx_set_dense_local": (C.c_int, [H, C.c_int]),
+    "mx_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
     "mx_build_problem": (C.c_int, [C.POINTER(MeshDesc), C.c_double, C.c_double, C.c_double, C.POINTER(DdDesc),
                                    C.POINTER(CoarseDesc), C.c_int, C.POINTER(H)]),
     "mx_set_xi_prob": (C.c_int, [H, C.c_double]),
@@ -148,6 +149,14 @@ def mx_set_stream(h, stream):
 
 def mx_set_dense_local(h, dense):
     _check(lib.mx_set_dense_local(h, int(bool(dense))))
+
+
+MX_TUNE_LOCAL_RHS_GROUP = 1
+MX_TUNE_LU_TENSOR = 2
+
+
+def mx_set_tuning(h, key, value):
+    _check(lib.mx_set_tuning(h, int(key), int(value)))
 
 
 def mx_factor(h):

@@ -108,6 +108,7 @@ static void check_status(Problem& P) {
   MX_CUDA(cudaStreamSynchronize(P.stream));
   MX_REQUIRE(st[0] == 0, MX_ESINGULAR, std::to_string(st[0]) + " zero or non-finite local pivots");
   MX_REQUIRE(st[1] == 0, MX_ESINGULAR, std::to_string(st[1]) + " zero or non-finite coarse pivots");
+  MX_REQUIRE(st[2] == 0, MX_ETIMEOUT, std::to_string(st[2]) + " tensor-core waits ran out in the factorisation");
 }
 
 }  // namespace mx
@@ -193,6 +194,23 @@ int mx_set_dense_local(mx_handle h, int dense) {
     P.dense_local = dense != 0;
     P.minors_ready = false;
     P.factored = false;
+  });
+}
+
+int mx_set_tuning(mx_handle h, int key, int value) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    if (key == MX_TUNE_LOCAL_RHS_GROUP) {
+      MX_REQUIRE(value == 0 || (value >= 1 && value <= 16 && (value & (value - 1)) == 0), MX_EINVAL,
+                 "local rhs group must be 0 or a power of two in 1..16");
+      P.tune_local_group = value;
+    } else if (key == MX_TUNE_LU_TENSOR) {
+      MX_REQUIRE(value == 0 || value == 1 || value == 3, MX_EINVAL, "LU tensor mode must be 0, 1 or 3");
+      P.tune_lu_tc = value;
+    } else {
+      throw Error(MX_EINVAL, "unknown tuning key " + std::to_string(key));
+    }
   });
 }
 

@@ -65,7 +65,7 @@ void factor_coarse(Problem& P) {
   MX_CUDA(cudaMemcpyAsync(P.c_meta.p, meta, 12, cudaMemcpyHostToDevice, s));
   MX_CUDA(cudaMemcpyAsync(P.c_off.p, &zero, 8, cudaMemcpyHostToDevice, s));
   BandBatch B{1, P.c_meta.p, P.c_meta.p + 1, P.c_meta.p + 2, P.c_off.p};
-  band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU);
+  band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU, 0);
   const int64_t nq = (nc + CB - 1) / CB;
   P.c_dinv.alloc(nq * 2 * CB * CB);
   invert_diag_blocks<double2>(B, P.A0.p, P.c_off.p, P.c_dinv.p, (int)nc, s);

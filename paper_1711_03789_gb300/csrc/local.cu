@@ -14,6 +14,8 @@
 // kernels per step for the whole batch (diagonal block, panels, trailing update).
 // Local solves: forward/backward substitution on the band with a sliding window of the
 // right-hand side block in shared memory; the gather R^l v is fused into the window load.
+#include <type_traits>
+
 #include "problem.cuh"
 
 namespace mx {
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(256) k_lu_update(BandBatch B, T2* A, int k0) {
 
 template <typename T2>
 void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s,
-             const int32_t* hn, const int32_t* hb, int kid_update) {
+             const int32_t* hn, const int32_t* hb, int kid_update, int tc_split) {
   const int chunks = (max_span + 255) / 256;
   const int tiles = (max_span + 63) / 64;
   const double esz = sizeof(T2);
@@ -261,6 +263,12 @@ void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status
         MX_CHECK_LAUNCH();
       }
       ProfScope ps(kid_update < 0 ? K_LU_UPDATE : kid_update, s, 1, upd_bytes, upd_flops);
+      if constexpr (std::is_same<T2, float2>::value) {
+        if (tc_split > 0) {  // tcgen05 tensor-core update (TF32 or 3 x TF32)
+          lu_update_tc(B, A, k0, max_span, tc_split, status + 2, s);
+          continue;
+        }
+      }
       MX_LAUNCH(k_lu_update<T2><<<dim3(B.count, tiles * tiles), 256, 0, s>>>(B, A, k0));
       MX_CHECK_LAUNCH();
     }
@@ -268,9 +276,9 @@ void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status
 }
 
 template void band_lu<double2>(const BandBatch&, double2*, int, int, int32_t*, cudaStream_t, const int32_t*,
-                               const int32_t*, int);
+                               const int32_t*, int, int);
 template void band_lu<float2>(const BandBatch&, float2*, int, int, int32_t*, cudaStream_t, const int32_t*,
-                              const int32_t*, int);
+                              const int32_t*, int, int);
 
 // ---- host: extraction and factorisation -------------------------------------------
 static int round4(int x) { return (x + 3) & ~3; }
@@ -400,12 +408,12 @@ void factor_local(Problem& P) {
   P.dinv.alloc((size_t)doff[P.n_sub] * esz);
   if (P.precision == MX_MIXED) {
     band_lu<float2>(B, reinterpret_cast<float2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream,
-                    P.h_nl.data(), P.h_band.data(), -1);
+                    P.h_nl.data(), P.h_band.data(), -1, P.tune_lu_tc);
     invert_diag_blocks<float2>(B, reinterpret_cast<float2*>(P.factors.p), P.dinv_off.p,
                                reinterpret_cast<float2*>(P.dinv.p), P.max_local, P.stream);
   } else {
     band_lu<double2>(B, reinterpret_cast<double2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream,
-                     P.h_nl.data(), P.h_band.data(), -1);
+                     P.h_nl.data(), P.h_band.data(), -1, 0);
     invert_diag_blocks<double2>(B, reinterpret_cast<double2*>(P.factors.p), P.dinv_off.p,
                                 reinterpret_cast<double2*>(P.dinv.p), P.max_local, P.stream);
   }
@@ -632,7 +640,8 @@ void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs) {
   // right-hand sides per block: the window must fit in shared memory
   const size_t esz = mixed ? 8 : 16;
   int G = 1;
-  while (G < nrhs && G < 16) G *= 2;
+  const int gmax = P.tune_local_group > 0 ? std::min(16, P.tune_local_group) : 16;
+  while (G < nrhs && G < gmax) G *= 2;
   while (G > 1 && (size_t)a.win * G * esz > 100 * 1024) G /= 2;
   MX_REQUIRE((size_t)a.win * esz <= 200 * 1024, MX_EINVAL, "subdomain bandwidth too large for the local solve window");
   if (mixed) {

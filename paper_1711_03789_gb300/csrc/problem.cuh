@@ -75,9 +75,11 @@ struct Problem {
   DevBuf<int32_t> inv_ptr;         // [n_dof + 1]
   DevBuf<int32_t> inv_pos;         // [sum_local]
 
-  // local factors: dense column-major n_l x n_l with leading dimension ld_l,
-  // element type float2 (mixed) or double2 (plain), matrix l at mat_off[l] elements.
+  // local factors: band storage (see local.cu), element type float2 (mixed) or double2
+  // (plain), matrix l at mat_off[l] elements.
   bool dense_local = false;        // force b_l = n_l - 1 (full dense storage)
+  int tune_local_group = 0;        // cap on right-hand sides per local-solve block (0 = 16)
+  int tune_lu_tc = 0;              // FP32 LU trailing update: 0 CUDA cores, 1 TF32, 3 split 3 x TF32
   std::vector<int32_t> h_band;     // [n_sub] half-bandwidths
   int64_t band_entries = 0;        // sum over subdomains of entries with |i - j| <= b_l
   DevBuf<int32_t> band;
@@ -126,7 +128,9 @@ void extract_minors(Problem& P);
 void factor_local(Problem& P);
 template <typename T2>
 void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s,
-             const int32_t* hn, const int32_t* hb, int kid_update);
+             const int32_t* hn, const int32_t* hb, int kid_update, int tc_split);
+// one tcgen05 trailing-update step of the FP32 band LU (lu_tc.cu); split 1 or 3 TF32 products
+void lu_update_tc(const BandBatch& B, float2* A, int k0, int max_span, int split, int32_t* status, cudaStream_t s);
 template <typename T2>
 void invert_diag_blocks(const BandBatch& B, const T2* A, const int64_t* doff, T2* Dinv, int max_n, cudaStream_t s);
 // z_l = (A^l)^{-1} R^l v for every l, written at the subdomain positions of `loc`

@@ -238,3 +238,22 @@ def test_batched_dots(nvec, n, nrhs):
     hd = torch.zeros((nvec, nrhs), dtype=torch.complex128, device="cuda")
     mx.mx_dots(torch.from_numpy(V).cuda(), torch.from_numpy(w).cuda(), hd)
     assert np.array_equal(hd.cpu().numpy(), h)
+
+
+@pytest.mark.parametrize("mode,tol", [(0, 2e-5), (3, 2e-5), (1, 5e-3)])
+def test_local_factor_tensor_core_modes(mode, tol):
+    """FP32 local LU with the trailing update on CUDA cores (0), tcgen05 3 x TF32 (3) and
+    tcgen05 TF32 (1): L U reproduces the minor to the precision of each mode."""
+    n, k, xi = 10, 4.0, 16.0
+    m = KuhnMesh(n)
+    Ko, Mo = fem.assemble_KM(m)
+    A = fem.a_xi(Ko, Mo, k, xi)
+    S = dd.Schwarz(m, A, 5, 1)
+    with _handle(n, k, 0.0, xi, 5, 1, prec=mx.MX_MIXED) as P:
+        mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_TENSOR, mode)
+        P.factor()
+        for l in (0, 5):
+            F = mx.mx_get_local(P.h, l, len(S.idx[l]))
+            L = np.tril(F, -1) + np.eye(F.shape[0])
+            Al = S.minor(l).toarray()
+            assert np.abs(L @ np.triu(F) - Al).max() <= tol * np.abs(Al).max()
