@@ -271,6 +271,67 @@ def cpu_baseline(W, iterations, budget_s=20.0):
             "per_iteration_s": per_it}
 
 
+def run_serving(args):
+    """Serving mix: requests with k in {10, 15, 20, 25} (2k cells per side, 5^3-cell
+    subdomains + 1-cell overlap, one level), xi_prec = k, xi_prob in {0, k, k^2/10},
+    1..32 seeded Gaussian-bump right-hand sides each, through mx_server_*. A closed-loop
+    run (everything submitted at once) measures capacity; a Poisson run at 0.8 x that
+    capacity measures latency under load. Reports p50 / p99 latency and solves per second."""
+    import torch
+    import inputs
+    import paper_1711_03789_gb300 as mx
+
+    torch.cuda.set_device(0)
+    mx.use_torch_allocator(0)
+    free, _ = torch.cuda.mem_get_info()
+    rng = np.random.default_rng(4)
+    nreq = args.requests
+
+    def draw(i):
+        k = float(rng.choice([10, 15, 20, 25]))
+        xp = float(rng.choice([0.0, k, k * k / 10]))
+        nrhs = int(rng.integers(1, 33))
+        c, p = inputs.bump_batch(10_000 + i, nrhs)
+        return dict(n=int(2 * k), k=k, xp=xp, nrhs=nrhs, c=c, p=p)
+
+    def run(reqs, rate):
+        s = mx.mx_server_create(int(0.8 * free), workers=args.workers)
+        tickets = []
+        t0 = time.perf_counter()
+        tnext = t0
+        for r in reqs:
+            if rate:
+                tnext += rng.exponential(1.0 / rate)
+                while time.perf_counter() < tnext:
+                    time.sleep(0.0005)
+            tickets.append(mx.mx_server_submit(s, r["n"], r["k"], r["xp"], r["k"], r["c"], r["p"], width=0.1,
+                                               tol=1e-6, restart=100, max_it=args.serve_max_it))
+        lat, conv, rhs = [], 0, 0
+        for r, t in zip(reqs, tickets):
+            n = 3 * r["n"] * (r["n"] - 1) ** 2 + 3 * r["n"] ** 2 * (r["n"] - 1) + r["n"] ** 3
+            x, st, tm, rc = mx.mx_server_poll(s, t, n, r["nrhs"])
+            lat.append(tm["latency_ms"])
+            conv += sum(v["converged"] for v in st)
+            rhs += r["nrhs"]
+        wall = time.perf_counter() - t0
+        info = mx.mx_server_stats(s)
+        mx.mx_server_destroy(s)
+        return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)), wall_s=wall,
+                    requests_per_s=len(reqs) / wall, rhs_per_s=rhs / wall, converged_rhs=conv, rhs=rhs,
+                    batches=info["batches"], factorisations=info["factorisations"], evictions=info["evictions"])
+
+    reqs = [draw(i) for i in range(nreq)]
+    closed = run(reqs, 0.0)
+    poisson = run(reqs, 0.8 * closed["requests_per_s"])
+    line = {"metric": METRIC, "value": poisson["p99_ms"] / 1e3, "unit": "s (p99 latency)", "n_gpus": 1,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c64 factors / f64 Krylov",
+            "data": "synthetic (seeded request mix and Gaussian-bump right-hand sides)",
+            "config": {"workload": "serving_mix", "requests": nreq, "workers": args.workers,
+                       "max_it": args.serve_max_it, "restart": 100, "tol": 1e-6},
+            "closed_loop": closed, "poisson_0.8x": poisson}
+    print(json.dumps(line))
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -301,7 +362,14 @@ def main():
     ap.add_argument("--max-it", type=int, default=None)
     ap.add_argument("--nrhs", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the solve benchmark")
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--workers", type=int, default=3)
+    ap.add_argument("--serve-max-it", type=int, default=200)
     args = ap.parse_args()
+    if args.serving:
+        run_serving(args)
+        return
     W = dict(WORKLOADS[args.workload])
     if args.xi_prec:
         W["xi_prec"] = args.xi_prec if args.xi_prec in ("k", "k1.5", "k2") else float(args.xi_prec)

@@ -228,6 +228,59 @@ MX_API int mx_dots(const void* V, const void* w, int64_t n, int nrhs, int nvec, 
  * array is written earlier in the same call, so no clearing is needed between calls. */
 MX_API int mx_dots_noalloc(const void* V, const void* w, int64_t n, int nrhs, int nvec, void* h, void* stream);
 
+/* ---- Serving --------------------------------------------------------------------------
+ * A request loop for many solves with different operators and right-hand-side counts on
+ * one GPU. Worker threads (each with its own CUDA stream) take the oldest pending request
+ * together with every pending request of the same operator and solver settings (continuous
+ * batching, at most 32 right-hand sides per batch); batches of different operators run
+ * concurrently. Factorisations stay resident in HBM, cached by the preconditioner key
+ * (n_cells, k, xi_prec, subdomains, coarse mesh, precision; xi_prob does not enter it, since
+ * B^{-1} is built from A_{xi_prec} only, Sec. 6.2). A new factorisation is admitted when its
+ * planned factor bytes plus the batch's Krylov workspace fit the budget after evicting idle
+ * cached factorisations (least recently used first) and fit the device's free memory;
+ * otherwise the request waits. */
+typedef struct mx_server_s* mx_server;
+
+typedef struct {
+  int n_cells;             /* mesh (mx_mesh_desc) */
+  double k, xi_prob, xi_prec;
+  int core_cells, overlap_cells, coarse_cells, precision;
+  int nrhs, nbumps;        /* right-hand sides as in mx_load_vector: 1..32 of them */
+  const double* centres;   /* [nrhs][nbumps][3], copied at submit */
+  const double* pol;       /* [nrhs][nbumps][3] complex, copied at submit */
+  double width;
+  double tol;              /* GMRES settings as in mx_solve */
+  int restart, max_it;
+} mx_request;
+
+typedef struct {
+  double latency_ms;       /* submit -> result available, host clock */
+  double queue_ms;         /* submit -> start of the batch that solved it */
+  int64_t n_dof;
+} mx_request_timing;
+
+typedef struct {
+  int64_t batches, factorisations, evictions, completed, cached_bytes;
+  int32_t cached_operators, pending;
+} mx_server_info;
+
+#define MX_PENDING 1       /* mx_server_poll without wait: result not ready yet */
+
+/* Start a server with a device memory budget for cached factorisations and workspaces,
+ * and `workers` worker threads / streams (1..16). */
+MX_API int mx_server_create(int64_t budget_bytes, int workers, mx_server* out);
+/* Queue a request; returns a ticket. Arrays are copied before the call returns. */
+MX_API int mx_server_submit(mx_server s, const mx_request* req, int64_t* ticket);
+/* Result of a ticket: with wait = 0 returns MX_PENDING if not finished; otherwise blocks.
+ * x: [nrhs][n_dof] c128 host (or NULL), stats: nrhs entries (or NULL), timing (or NULL).
+ * Returns the request's MX_OK / MX_ENOCONV / error code and forgets the ticket. */
+MX_API int mx_server_poll(mx_server s, int64_t ticket, int wait, void* x, mx_rhs_stats* stats,
+                          mx_request_timing* timing);
+MX_API int mx_server_stats(mx_server s, mx_server_info* out);
+/* Finish running batches, stop the workers and free every cached factorisation. Pending
+ * requests that were not started are dropped. */
+MX_API void mx_server_destroy(mx_server s);
+
 /* ---- Instrumentation ----------------------------------------------------------------- */
 
 /* Number of kernel launches made by the library since it was loaded (all handles). */

@@ -350,3 +350,77 @@ def use_torch_allocator(device=0):
         torch.cuda.caching_allocator_delete(p)
 
     mx_set_allocator(alloc, release)
+
+
+# ---- serving ---------------------------------------------------------------------------
+class MxRequest(C.Structure):
+    _fields_ = [("n_cells", C.c_int), ("k", C.c_double), ("xi_prob", C.c_double), ("xi_prec", C.c_double),
+                ("core_cells", C.c_int), ("overlap_cells", C.c_int), ("coarse_cells", C.c_int),
+                ("precision", C.c_int), ("nrhs", C.c_int), ("nbumps", C.c_int), ("centres", C.c_void_p),
+                ("pol", C.c_void_p), ("width", C.c_double), ("tol", C.c_double), ("restart", C.c_int),
+                ("max_it", C.c_int)]
+
+
+class RequestTiming(C.Structure):
+    _fields_ = [("latency_ms", C.c_double), ("queue_ms", C.c_double), ("n_dof", C.c_int64)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("batches", C.c_int64), ("factorisations", C.c_int64), ("evictions", C.c_int64),
+                ("completed", C.c_int64), ("cached_bytes", C.c_int64), ("cached_operators", C.c_int32),
+                ("pending", C.c_int32)]
+
+
+MX_PENDING = 1
+for _n, (_r, _a) in {
+    "mx_server_create": (C.c_int, [C.c_int64, C.c_int, C.POINTER(C.c_void_p)]),
+    "mx_server_submit": (C.c_int, [C.c_void_p, C.POINTER(MxRequest), C.POINTER(C.c_int64)]),
+    "mx_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, P, C.POINTER(RhsStats), C.POINTER(RequestTiming)]),
+    "mx_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerInfo)]),
+    "mx_server_destroy": (None, [C.c_void_p]),
+}.items():
+    _f = getattr(lib, _n)
+    _f.restype = _r
+    _f.argtypes = _a
+
+
+def mx_server_create(budget_bytes, workers=2):
+    s = C.c_void_p()
+    _check(lib.mx_server_create(int(budget_bytes), int(workers), C.byref(s)))
+    return s
+
+
+def mx_server_submit(s, n_cells, k, xi_prob, xi_prec, centres, pol, width=0.1, core_cells=5, overlap_cells=1,
+                     coarse_cells=0, precision=MX_MIXED, tol=1e-6, restart=0, max_it=200):
+    """Queue one request (centres [nrhs, nbumps, 3], pol [nrhs, nbumps, 3] complex); returns its ticket."""
+    centres = np.ascontiguousarray(centres, dtype=np.float64)
+    pol = np.ascontiguousarray(pol, dtype=np.complex128)
+    q = MxRequest(n_cells, k, xi_prob, xi_prec, core_cells, overlap_cells, coarse_cells, precision,
+                  centres.shape[0], centres.shape[1], centres.ctypes.data, pol.ctypes.data, width, tol, restart,
+                  max_it)
+    t = C.c_int64()
+    _check(lib.mx_server_submit(s, C.byref(q), C.byref(t)))
+    return t.value
+
+
+def mx_server_poll(s, ticket, n_dof, nrhs, wait=True):
+    """Returns None while pending (wait=False), else (x [nrhs, n_dof], stats, timing dict, rc)."""
+    x = np.empty((nrhs, n_dof), dtype=np.complex128)
+    st = (RhsStats * nrhs)()
+    tm = RequestTiming()
+    rc = lib.mx_server_poll(s, int(ticket), int(bool(wait)), _ptr(x), st, C.byref(tm))
+    if rc == MX_PENDING and not wait:
+        return None
+    _check(rc, allow=(MX_ENOCONV,))
+    stats = [dict(iterations=v.iterations, converged=bool(v.converged), rel_residual=v.rel_residual) for v in st]
+    return x, stats, dict(latency_ms=tm.latency_ms, queue_ms=tm.queue_ms), rc
+
+
+def mx_server_stats(s):
+    i = ServerInfo()
+    _check(lib.mx_server_stats(s, C.byref(i)))
+    return {f: getattr(i, f) for f, _ in ServerInfo._fields_}
+
+
+def mx_server_destroy(s):
+    lib.mx_server_destroy(s)

@@ -111,6 +111,69 @@ static void check_status(Problem& P) {
   MX_REQUIRE(st[2] == 0, MX_ETIMEOUT, std::to_string(st[2]) + " tensor-core waits ran out in the factorisation");
 }
 
+void transpose_to_internal(const double2* user, double2* in, int64_t n, int nrhs, cudaStream_t s) {
+  MX_LAUNCH(k_to_internal<<<grid_for(n * nrhs, 256), 256, 0, s>>>(n, nrhs, 0, nrhs, user, in));
+  MX_CHECK_LAUNCH();
+}
+
+void transpose_to_user(const double2* in, double2* user, int64_t n, int nrhs, cudaStream_t s) {
+  MX_LAUNCH(k_to_user<<<grid_for(n * nrhs, 256), 256, 0, s>>>(n, nrhs, 0, nrhs, in, user));
+  MX_CHECK_LAUNCH();
+}
+
+Problem* create_problem(int n, double k, double xi_prob, double xi_prec, int core, int overlap, int cm, int precision,
+                        cudaStream_t stream) {
+  MX_REQUIRE(n >= 1 && n <= 256, MX_EINVAL, "n_cells must be in 1..256");
+  MX_REQUIRE(core >= 1, MX_EINVAL, "core_cells must be >= 1");
+  MX_REQUIRE(overlap >= 0 && overlap <= 6 * core, MX_EINVAL, "overlap_cells must be in 0..6*core_cells");
+  MX_REQUIRE(k > 0 && std::isfinite(k), MX_EINVAL, "k must be > 0");
+  MX_REQUIRE(xi_prec != 0 && std::isfinite(xi_prec) && std::isfinite(xi_prob), MX_EINVAL,
+             "xi_prec must be nonzero and finite");
+  MX_REQUIRE(precision == MX_MIXED || precision == MX_PLAIN_FP64, MX_EINVAL, "unknown precision");
+  MX_REQUIRE(cm >= 0 && (cm == 0 || n % cm == 0), MX_EINVAL, "coarse n_cells must divide the fine n_cells");
+  auto P = new Problem();
+  try {
+    P->n = n;
+    P->k = k;
+    P->xi_prob = xi_prob;
+    P->xi_prec = xi_prec;
+    P->core = core;
+    P->overlap = overlap;
+    P->coarse_m = cm;
+    P->precision = precision;
+    P->stream = stream;
+    P->status.alloc(4);
+    MX_CUDA(cudaMemsetAsync(P->status.p, 0, 16, P->stream));
+    EventTimer t(P->stream);
+    build_mesh(P->fine, P->n, P->stream);
+    MX_REQUIRE(P->fine.n_dof > 0, MX_EINVAL, "mesh has no interior edge");
+    assemble_KM(P->fine, P->A, P->stream);
+    build_subdomains(*P);
+    if (cm) {
+      build_mesh(P->coarse, cm, P->stream);
+      MX_REQUIRE(P->coarse.n_dof > 0, MX_EINVAL, "coarse mesh has no interior edge (use n_cells >= 2)");
+      assemble_KM(P->coarse, P->Ac, P->stream);
+      build_coarse_restriction(*P);
+      P->n_c = P->coarse.n_dof;
+    }
+    P->timing.build_ms = t.stop();
+  } catch (...) {
+    delete P;
+    throw;
+  }
+  return P;
+}
+
+void factor_problem(Problem& P) {
+  MX_CUDA(cudaMemsetAsync(P.status.p, 0, 16, P.stream));
+  EventTimer t(P.stream);
+  extract_minors(P);
+  factor_local(P);
+  factor_coarse(P);
+  P.timing.factor_ms = t.stop();
+  check_status(P);
+}
+
 }  // namespace mx
 
 using namespace mx;
@@ -129,46 +192,8 @@ int mx_build_problem(const mx_mesh_desc* mesh, double k, double xi_prob, double 
                      const mx_coarse_desc* coarse, int precision, mx_handle* out) {
   return guard([&] {
     MX_REQUIRE(mesh && dd && out, MX_EINVAL, "null descriptor");
-    MX_REQUIRE(mesh->n_cells >= 1 && mesh->n_cells <= 256, MX_EINVAL, "n_cells must be in 1..256");
-    MX_REQUIRE(dd->core_cells >= 1, MX_EINVAL, "core_cells must be >= 1");
-    MX_REQUIRE(dd->overlap_cells >= 0 && dd->overlap_cells <= 6 * dd->core_cells, MX_EINVAL,
-               "overlap_cells must be in 0..6*core_cells");
-    MX_REQUIRE(k > 0 && std::isfinite(k), MX_EINVAL, "k must be > 0");
-    MX_REQUIRE(xi_prec != 0 && std::isfinite(xi_prec) && std::isfinite(xi_prob), MX_EINVAL,
-               "xi_prec must be nonzero and finite");
-    MX_REQUIRE(precision == MX_MIXED || precision == MX_PLAIN_FP64, MX_EINVAL, "unknown precision");
-    const int cm = coarse ? coarse->n_cells : 0;
-    MX_REQUIRE(cm >= 0 && (cm == 0 || mesh->n_cells % cm == 0), MX_EINVAL,
-               "coarse n_cells must divide the fine n_cells");
-    auto P = new Problem();
-    try {
-      P->n = mesh->n_cells;
-      P->k = k;
-      P->xi_prob = xi_prob;
-      P->xi_prec = xi_prec;
-      P->core = dd->core_cells;
-      P->overlap = dd->overlap_cells;
-      P->coarse_m = cm;
-      P->precision = precision;
-      P->status.alloc(4);
-      MX_CUDA(cudaMemsetAsync(P->status.p, 0, 16, P->stream));
-      EventTimer t(P->stream);
-      build_mesh(P->fine, P->n, P->stream);
-      MX_REQUIRE(P->fine.n_dof > 0, MX_EINVAL, "mesh has no interior edge");
-      assemble_KM(P->fine, P->A, P->stream);
-      build_subdomains(*P);
-      if (cm) {
-        build_mesh(P->coarse, cm, P->stream);
-        MX_REQUIRE(P->coarse.n_dof > 0, MX_EINVAL, "coarse mesh has no interior edge (use n_cells >= 2)");
-        assemble_KM(P->coarse, P->Ac, P->stream);
-        build_coarse_restriction(*P);
-        P->n_c = P->coarse.n_dof;
-      }
-      P->timing.build_ms = t.stop();
-    } catch (...) {
-      delete P;
-      throw;
-    }
+    Problem* P = create_problem(mesh->n_cells, k, xi_prob, xi_prec, dd->core_cells, dd->overlap_cells,
+                                coarse ? coarse->n_cells : 0, precision, nullptr);
     *out = reinterpret_cast<mx_handle>(P);
   });
 }
@@ -217,14 +242,7 @@ int mx_set_tuning(mx_handle h, int key, int value) {
 int mx_factor(mx_handle h) {
   return guard([&] {
     MX_REQUIRE(h, MX_EINVAL, "null handle");
-    auto& P = *reinterpret_cast<Problem*>(h);
-    MX_CUDA(cudaMemsetAsync(P.status.p, 0, 16, P.stream));
-    EventTimer t(P.stream);
-    extract_minors(P);
-    factor_local(P);
-    factor_coarse(P);
-    P.timing.factor_ms = t.stop();
-    check_status(P);
+    factor_problem(*reinterpret_cast<Problem*>(h));
   });
 }
 

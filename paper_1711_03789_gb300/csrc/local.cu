@@ -283,9 +283,7 @@ template void band_lu<float2>(const BandBatch&, float2*, int, int, int32_t*, cud
 // ---- host: extraction and factorisation -------------------------------------------
 static int round4(int x) { return (x + 3) & ~3; }
 
-void extract_minors(Problem& P) {
-  cudaStream_t s = P.stream;
-  const size_t esz = P.precision == MX_MIXED ? sizeof(float2) : sizeof(double2);
+static ExtractArgs extract_args(const Problem& P) {
   ExtractArgs a{};
   a.n_sub = P.n_sub;
   a.sum_local = P.sum_local;
@@ -299,6 +297,14 @@ void extract_minors(Problem& P) {
   a.M = P.A.M.p;
   a.sr = P.k * P.k;
   a.si = P.xi_prec;
+  return a;
+}
+
+// Half-bandwidth of every minor (one pass over the CSR rows of all subdomains) and the
+// band storage plan: h_band, h_ld, h_mat_off, band_entries.
+void plan_local_storage(Problem& P) {
+  cudaStream_t s = P.stream;
+  ExtractArgs a = extract_args(P);
   DevBuf<int32_t> band(P.n_sub);
   MX_CUDA(cudaMemsetAsync(band.p, 0, band.bytes(), s));
   a.band = band.p;
@@ -317,6 +323,33 @@ void extract_minors(Problem& P) {
     P.h_ld[l] = round4(2 * P.h_band[l] + 1);
     P.h_mat_off[l + 1] = P.h_mat_off[l] + (int64_t)P.h_ld[l] * P.h_nl[l];
   }
+}
+
+// Device bytes the local factors (band + inverted diagonal blocks) will hold.
+int64_t local_factor_bytes(Problem& P) {
+  plan_local_storage(P);
+  const int64_t esz = P.precision == MX_MIXED ? 8 : 16;
+  int64_t blocks = 0;
+  for (int l = 0; l < P.n_sub; ++l) blocks += (P.h_nl[l] + NB - 1) / NB;
+  return esz * (P.h_mat_off[P.n_sub] + blocks * 2 * NB * NB);
+}
+
+void extract_minors(Problem& P) {
+  cudaStream_t s = P.stream;
+  const size_t esz = P.precision == MX_MIXED ? sizeof(float2) : sizeof(double2);
+  plan_local_storage(P);
+  ExtractArgs a{};
+  a.n_sub = P.n_sub;
+  a.sum_local = P.sum_local;
+  a.offsets = P.offsets.p;
+  a.lists = P.lists.p;
+  a.inv_ptr = P.inv_ptr.p;
+  a.inv_pos = P.inv_pos.p;
+  a.rowptr = P.A.rowptr.p;
+  a.col = P.A.col.p;
+  a.K = P.A.K.p;
+  a.M = P.A.M.p;
+  a = extract_args(P);
   P.band.alloc(P.n_sub);
   P.ld.alloc(P.n_sub);
   P.mat_off.alloc(P.n_sub + 1);

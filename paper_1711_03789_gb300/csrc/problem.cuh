@@ -113,6 +113,18 @@ struct Problem {
   ~Problem();
 };
 
+// ---- api.cu -------------------------------------------------------------------------
+// validate, build mesh / assembly / subdomains / coarse space on `stream` (throws Error)
+Problem* create_problem(int n, double k, double xi_prob, double xi_prec, int core, int overlap, int coarse_m,
+                        int precision, cudaStream_t stream);
+// extract minors, batched local LU, coarse LU; checks pivots and waits (throws Error)
+void factor_problem(Problem& P);
+// device bytes of the local factors a factorisation will allocate (runs the band pass)
+int64_t local_factor_bytes(Problem& P);
+// [nrhs][n] (caller layout) <-> [n][nrhs] (solver layout), device to device
+void transpose_to_internal(const double2* user, double2* in, int64_t n, int nrhs, cudaStream_t s);
+void transpose_to_user(const double2* in, double2* user, int64_t n, int nrhs, cudaStream_t s);
+
 // ---- mesh.cu ------------------------------------------------------------------------
 void build_mesh(MeshDev& m, int n, cudaStream_t s);
 void build_subdomains(Problem& P);

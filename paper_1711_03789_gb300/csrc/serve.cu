@@ -1,0 +1,383 @@
+// Serving loop: many solve requests with different operators and right-hand-side counts on
+// one GPU, with factorisations cached in HBM and continuous batching.
+//
+// - Requests are queued on submit. A pool of worker threads, each with its own CUDA stream,
+//   takes work: the oldest pending request and every other pending request with the same
+//   operator (mesh, k, xi_prob, xi_prec, subdomains, coarse mesh, precision) and the same
+//   solver settings are solved together as one batch of right-hand sides (at most 32).
+//   Requests that arrive while batches run join the next batch of their operator, and
+//   batches of different operators run concurrently on the workers' streams.
+// - Factorisations are cached by the preconditioner key (everything but xi_prob: the
+//   preconditioner is built from A_{xi_prec} only, Sec. 6.2), so requests that differ in
+//   xi_prob share factors; the operator A_{xi_prob} is set per batch.
+// - Admission: a new factorisation is admitted only if its local factors (band storage,
+//   planned before allocation) plus the Krylov workspace of the batch fit in the memory
+//   budget after evicting unused cached factorisations (least recently used first) and in
+//   the device's free memory; otherwise the request waits for memory to free up.
+// - Latency is measured per request from submit to completion on the host clock.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+
+#include "problem.cuh"
+
+namespace mx {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Key {
+  int n, core, overlap, coarse, precision;
+  double k, xi_prec;
+  bool operator<(const Key& o) const {
+    return std::tie(n, core, overlap, coarse, precision, k, xi_prec) <
+           std::tie(o.n, o.core, o.overlap, o.coarse, o.precision, o.k, o.xi_prec);
+  }
+  bool operator==(const Key& o) const { return !(*this < o) && !(o < *this); }
+};
+
+struct Req {
+  int64_t id = 0;
+  Key key{};
+  double xi_prob = 0, tol = 1e-6, width = 0.1;
+  int restart = 0, max_it = 200, nrhs = 1, nbumps = 1;
+  std::vector<double> centres, pol;
+  std::vector<double2> x;
+  std::vector<mx_rhs_stats> stats;
+  int rc = MX_OK;
+  std::string err;
+  bool done = false, taken = false;
+  Clock::time_point t_submit, t_start, t_done;
+};
+
+struct Entry {
+  std::unique_ptr<Problem> P;
+  int64_t bytes = 0;
+  bool busy = false;
+  uint64_t last_used = 0;
+};
+
+}  // namespace
+
+struct Server {
+  int64_t budget = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<int64_t> pending;
+  std::map<int64_t, std::unique_ptr<Req>> reqs;
+  std::map<Key, Entry> cache;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;
+  bool stop = false;
+  int64_t next_id = 1;
+  uint64_t clock = 0;
+  int64_t cached_bytes = 0;
+  int device = 0;
+  // statistics
+  int64_t batches = 0, factorisations = 0, evictions = 0, completed = 0;
+
+  static bool same_batch(const Req& a, const Req& b) {
+    return a.key == b.key && a.xi_prob == b.xi_prob && a.tol == b.tol && a.restart == b.restart &&
+           a.max_it == b.max_it;
+  }
+
+  static int64_t workspace_bytes(const Key& k, int64_t n_dof, int nrhs, int m) {
+    const int64_t esz = k.precision == MX_MIXED ? 8 : 16;
+    return n_dof * nrhs * ((int64_t)(m + 1) * 16 + (int64_t)m * esz + 6 * 16) + (64LL << 20);
+  }
+
+  // Evict unused entries (least recently used first) until `need` more bytes fit the budget.
+  bool make_room(int64_t need) {
+    while (cached_bytes + need > budget) {
+      auto victim = cache.end();
+      for (auto it = cache.begin(); it != cache.end(); ++it)
+        if (!it->second.busy && (victim == cache.end() || it->second.last_used < victim->second.last_used))
+          victim = it;
+      if (victim == cache.end()) return false;
+      cached_bytes -= victim->second.bytes;
+      cache.erase(victim);
+      ++evictions;
+    }
+    return true;
+  }
+
+  void work(int wid) {
+    cudaSetDevice(device);
+    cudaStream_t s = streams[wid];
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+      // find a batch whose operator is not busy
+      std::vector<Req*> batch;
+      Entry* entry = nullptr;
+      bool create = false;
+      while (!stop) {
+        batch.clear();
+        for (int64_t id : pending) {
+          Req* r = reqs[id].get();
+          if (r->taken) continue;
+          auto it = cache.find(r->key);
+          if (it != cache.end() && it->second.busy) continue;
+          // gather every pending request of the same operator and settings, up to 32 rhs
+          int nr = 0;
+          for (int64_t id2 : pending) {
+            Req* q = reqs[id2].get();
+            if (q->taken || !same_batch(*q, *r) || nr + q->nrhs > 32) continue;
+            batch.push_back(q);
+            nr += q->nrhs;
+          }
+          entry = it != cache.end() ? &it->second : nullptr;
+          create = entry == nullptr;
+          break;
+        }
+        if (!batch.empty()) break;
+        cv_work.wait(lk);
+      }
+      if (stop) return;
+      for (Req* r : batch) r->taken = true;
+      pending.erase(std::remove_if(pending.begin(), pending.end(),
+                                   [&](int64_t id) { return reqs[id]->taken; }),
+                    pending.end());
+      const Key key = batch[0]->key;
+      if (create) {
+        entry = &cache[key];
+        entry->busy = true;
+      } else {
+        entry->busy = true;
+      }
+      lk.unlock();
+
+      int rc = MX_OK;
+      std::string err;
+      int64_t charged = 0;  // bytes admitted into the budget for a new factorisation
+      int nrhs = 0;
+      for (Req* r : batch) nrhs += r->nrhs;
+      const auto t_start = Clock::now();
+      try {
+        if (create) {
+          std::unique_ptr<Problem> P(create_problem(key.n, key.k, batch[0]->xi_prob, key.xi_prec, key.core,
+                                                    key.overlap, key.coarse, key.precision, s));
+          const int m = batch[0]->restart > 0 ? std::min(batch[0]->restart, batch[0]->max_it) : batch[0]->max_it;
+          const int64_t need = local_factor_bytes(*P) + workspace_bytes(key, P->fine.n_dof, nrhs, m);
+          // admission: memory budget (after evictions) and the device's free memory
+          MX_REQUIRE(need <= budget, MX_ENOMEM,
+                     "request needs " + std::to_string(need) + " bytes, more than the whole budget");
+          bool admitted = false;
+          for (int attempt = 0; attempt < 600 && !admitted; ++attempt) {
+            {
+              std::lock_guard<std::mutex> g(mu);
+              admitted = make_room(need);
+              if (admitted) cached_bytes += need;
+            }
+            size_t fr = 0, tot = 0;
+            if (admitted && cudaMemGetInfo(&fr, &tot) == cudaSuccess && (int64_t)fr < need) {
+              std::lock_guard<std::mutex> g(mu);
+              cached_bytes -= need;
+              admitted = false;
+            }
+            if (!admitted) std::this_thread::sleep_for(std::chrono::milliseconds(50));
+          }
+          MX_REQUIRE(admitted, MX_ENOMEM, "request does not fit the memory budget");
+          charged = need;
+          factor_problem(*P);
+          {
+            std::lock_guard<std::mutex> g(mu);
+            entry->P = std::move(P);
+            entry->bytes = need;
+            ++factorisations;
+          }
+        }
+        Problem& P = *entry->P;
+        P.stream = s;
+        P.xi_prob = batch[0]->xi_prob;
+        const int64_t n = P.fine.n_dof;
+        DevBuf<double2> f((size_t)n * nrhs), bi((size_t)n * nrhs), xi((size_t)n * nrhs);
+        // load vectors of every request, stacked as one block of right-hand sides
+        int r0 = 0;
+        for (Req* r : batch) {
+          load_vector(P, r->nrhs, r->nbumps, r->centres.data(), r->pol.data(), r->width, f.p + (int64_t)r0 * n);
+          r0 += r->nrhs;
+        }
+        transpose_to_internal(f.p, bi.p, n, nrhs, s);
+        std::vector<mx_rhs_stats> st(nrhs);
+        const int c = gmres_solve(P, bi.p, xi.p, nrhs, batch[0]->tol, batch[0]->restart, batch[0]->max_it, st.data());
+        transpose_to_user(xi.p, f.p, n, nrhs, s);
+        r0 = 0;
+        for (Req* r : batch) {
+          r->x.resize((size_t)n * r->nrhs);
+          MX_CUDA(cudaMemcpyAsync(r->x.data(), f.p + (int64_t)r0 * n, sizeof(double2) * n * r->nrhs,
+                                  cudaMemcpyDeviceToHost, s));
+          r->stats.assign(st.begin() + r0, st.begin() + r0 + r->nrhs);
+          r0 += r->nrhs;
+        }
+        MX_CUDA(cudaStreamSynchronize(s));
+        if (c != MX_OK) rc = c;
+      } catch (const Error& e) {
+        rc = e.code;
+        err = e.what();
+      } catch (const std::exception& e) {
+        rc = MX_ECUDA;
+        err = e.what();
+      }
+      lk.lock();
+      if (create && !entry->P) {  // failed before caching
+        cached_bytes -= charged;
+        cache.erase(key);
+      } else {
+        entry->busy = false;
+        entry->last_used = ++clock;
+      }
+      const auto t_done = Clock::now();
+      for (Req* r : batch) {
+        r->rc = (rc == MX_ENOCONV) ? (std::all_of(r->stats.begin(), r->stats.end(),
+                                                  [](const mx_rhs_stats& x) { return x.converged != 0; })
+                                          ? MX_OK
+                                          : MX_ENOCONV)
+                                   : rc;
+        r->err = err;
+        r->t_start = t_start;
+        r->t_done = t_done;
+        r->done = true;
+        ++completed;
+      }
+      ++batches;
+      cv_done.notify_all();
+      cv_work.notify_all();
+    }
+  }
+};
+
+}  // namespace mx
+
+using namespace mx;
+
+extern "C" {
+
+MX_API int mx_server_create(int64_t budget_bytes, int workers, mx_server* out) {
+  try {
+    MX_REQUIRE(out && budget_bytes > 0 && workers >= 1 && workers <= 16, MX_EINVAL, "bad server arguments");
+    auto S = new Server();
+    S->budget = budget_bytes;
+    cudaGetDevice(&S->device);
+    for (int w = 0; w < workers; ++w) {
+      cudaStream_t st;
+      MX_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      S->streams.push_back(st);
+    }
+    for (int w = 0; w < workers; ++w) S->workers.emplace_back([S, w] { S->work(w); });
+    *out = reinterpret_cast<mx_server>(S);
+    set_last_error("");
+    return MX_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
+MX_API int mx_server_submit(mx_server sv, const mx_request* q, int64_t* ticket) {
+  try {
+    MX_REQUIRE(sv && q && ticket, MX_EINVAL, "null argument");
+    MX_REQUIRE(q->nrhs >= 1 && q->nrhs <= 32 && q->nbumps >= 1 && q->centres && q->pol && q->width > 0 && q->tol > 0 &&
+                   q->max_it >= 1 && q->restart >= 0,
+               MX_EINVAL, "bad request");
+    MX_REQUIRE(q->n_cells >= 1 && q->core_cells >= 1 && q->k > 0 && q->xi_prec != 0 &&
+                   (q->coarse_cells == 0 || q->n_cells % q->coarse_cells == 0),
+               MX_EINVAL, "bad operator in request");
+    auto S = reinterpret_cast<Server*>(sv);
+    auto r = std::make_unique<Req>();
+    r->key = Key{q->n_cells, q->core_cells, q->overlap_cells, q->coarse_cells, q->precision, q->k, q->xi_prec};
+    r->xi_prob = q->xi_prob;
+    r->tol = q->tol;
+    r->restart = q->restart;
+    r->max_it = q->max_it;
+    r->nrhs = q->nrhs;
+    r->nbumps = q->nbumps;
+    r->width = q->width;
+    r->centres.assign(q->centres, q->centres + (size_t)q->nrhs * q->nbumps * 3);
+    r->pol.assign(q->pol, q->pol + (size_t)q->nrhs * q->nbumps * 6);
+    r->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->id = S->next_id++;
+    *ticket = r->id;
+    S->pending.push_back(r->id);
+    S->reqs[r->id] = std::move(r);
+    S->cv_work.notify_one();
+    set_last_error("");
+    return MX_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
+MX_API int mx_server_poll(mx_server sv, int64_t ticket, int wait, void* x, mx_rhs_stats* stats,
+                          mx_request_timing* timing) {
+  try {
+    MX_REQUIRE(sv, MX_EINVAL, "null server");
+    auto S = reinterpret_cast<Server*>(sv);
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    MX_REQUIRE(it != S->reqs.end(), MX_EINVAL, "unknown ticket");
+    Req* r = it->second.get();
+    if (!r->done) {
+      if (!wait) return 1;  // still running
+      S->cv_done.wait(lk, [&] { return r->done; });
+    }
+    if (x) std::memcpy(x, r->x.data(), r->x.size() * sizeof(double2));
+    if (stats) std::copy(r->stats.begin(), r->stats.end(), stats);
+    if (timing) {
+      timing->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+      timing->queue_ms = std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count();
+      timing->n_dof = (int64_t)(r->x.size() / std::max(1, r->nrhs));
+    }
+    const int rc = r->rc;
+    const std::string err = r->err;
+    S->reqs.erase(it);
+    lk.unlock();
+    set_last_error(err);
+    return rc;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+}
+
+MX_API int mx_server_stats(mx_server sv, mx_server_info* out) {
+  if (!sv || !out) return MX_EINVAL;
+  auto S = reinterpret_cast<Server*>(sv);
+  std::lock_guard<std::mutex> lk(S->mu);
+  out->batches = S->batches;
+  out->factorisations = S->factorisations;
+  out->evictions = S->evictions;
+  out->completed = S->completed;
+  out->cached_bytes = S->cached_bytes;
+  out->cached_operators = (int32_t)S->cache.size();
+  out->pending = (int32_t)S->pending.size();
+  return MX_OK;
+}
+
+MX_API void mx_server_destroy(mx_server sv) {
+  if (!sv) return;
+  auto S = reinterpret_cast<Server*>(sv);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (auto st : S->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  delete S;
+}
+
+}  // extern "C"
