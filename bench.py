@@ -130,6 +130,8 @@ def run_ours(args, W, rank, world):
 
     def step(host):
         P = mx.Problem(W["n"], k, xp, xq, W["core"], W["overlap"], W["coarse"], prec, stream=stream.cuda_stream)
+        if args.local_tensor is not None:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, args.local_tensor)
         P.factor()
         n = P.n_dof
         if host:
@@ -361,6 +363,8 @@ def main():
     ap.add_argument("--restart", type=int, default=None)
     ap.add_argument("--max-it", type=int, default=None)
     ap.add_argument("--nrhs", type=int, default=None)
+    ap.add_argument("--local-tensor", type=int, default=None, choices=[0, 1],
+                    help="local solves on the tensor cores (1) or CUDA cores (0); default: library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the solve benchmark")
     ap.add_argument("--requests", type=int, default=48)

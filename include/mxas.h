@@ -111,6 +111,16 @@ MX_API int mx_set_dense_local(mx_handle h, int dense);
  *   with three TF32 products per term (hi*hi + hi*lo + lo*hi, close to FP32), 1 = one TF32
  *   product, 0 (default) = FP32 CUDA cores. MX_PLAIN_FP64 always uses FP64 CUDA cores. */
 #define MX_TUNE_LU_TENSOR 2
+/*   MX_TUNE_COARSE_BLOCKS: thread blocks of the cooperative coarse sweep (0 = sized by the
+ *   band work, at most one per SM); fewer blocks make its grid-wide barriers cheaper. */
+#define MX_TUNE_COARSE_BLOCKS 3
+/*   MX_TUNE_LOCAL_TENSOR: local solves of the MX_MIXED form; 1 = tcgen05 tensor cores
+ *   (the off-diagonal band updates as TF32 GEMMs against panel images of the factors that
+ *   mx_factor stores beside the band, about as many bytes again; the right-hand-side block
+ *   enters as a TF32 hi + lo pair; default), 0 = FP32 CUDA-core substitution. Half-bandwidths
+ *   above 448 fall back to the CUDA cores. Changing it after mx_factor builds the panel
+ *   images at the next solve. */
+#define MX_TUNE_LOCAL_TENSOR 4
 MX_API int mx_set_tuning(mx_handle h, int key, int value);
 
 /* Message of the last error on the calling thread ("" if none). */

@@ -153,6 +153,8 @@ def mx_set_dense_local(h, dense):
 
 MX_TUNE_LOCAL_RHS_GROUP = 1
 MX_TUNE_LU_TENSOR = 2
+MX_TUNE_COARSE_BLOCKS = 3
+MX_TUNE_LOCAL_TENSOR = 4
 
 
 def mx_set_tuning(h, key, value):

@@ -230,9 +230,15 @@ int mx_set_tuning(mx_handle h, int key, int value) {
       MX_REQUIRE(value == 0 || (value >= 1 && value <= 16 && (value & (value - 1)) == 0), MX_EINVAL,
                  "local rhs group must be 0 or a power of two in 1..16");
       P.tune_local_group = value;
+    } else if (key == MX_TUNE_COARSE_BLOCKS) {
+      MX_REQUIRE(value >= 0 && value <= 4096, MX_EINVAL, "coarse blocks must be in 0..4096");
+      P.tune_coarse_blocks = value;
     } else if (key == MX_TUNE_LU_TENSOR) {
       MX_REQUIRE(value == 0 || value == 1 || value == 3, MX_EINVAL, "LU tensor mode must be 0, 1 or 3");
       P.tune_lu_tc = value;
+    } else if (key == MX_TUNE_LOCAL_TENSOR) {
+      MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "local tensor mode must be 0 or 1");
+      P.tune_local_tc = value;
     } else {
       throw Error(MX_EINVAL, "unknown tuning key " + std::to_string(key));
     }

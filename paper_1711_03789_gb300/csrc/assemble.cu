@@ -216,8 +216,31 @@ struct LoadArgs {
   QuadRule rule;
   const double* centres;  // [nrhs][nbumps][3]
   const double2* pol;     // [nrhs][nbumps][3]
+  const double* etab;     // [nrhs][nbumps][3][n][81] per-axis Gaussian factors
   double2* contrib;       // [ntet][6][nrhs]
 };
+
+// The Gaussian bump is a product of one-dimensional factors, and inside cube i (per axis)
+// the quadrature points' coordinates are (i + S[u]) h, u = 3q + t, with S[3q] = xi1+xi2+xi3,
+// S[3q+1] = xi2+xi3, S[3q+2] = xi3 of rule point q (the path vertices add e_s0, e_s1, e_s2).
+// etab[r][b][a][i][u] = exp(-((i + S[u]) h - c_{r,b,a})^2 / w^2): n * 243 exponentials per
+// bump instead of one per point.
+__global__ void k_load_table(LoadArgs a, double* etab) {
+  const int64_t total = (int64_t)a.nrhs * a.nbumps * 3 * a.n * 81;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int u = (int)(t % 81);
+    int64_t rest = t / 81;
+    const int i = (int)(rest % a.n);
+    rest /= a.n;
+    const int ax = (int)(rest % 3);
+    rest /= 3;  // = r * nbumps + b
+    const int q = u / 3, tt = u % 3;
+    const double s = tt == 0 ? a.rule.xi[q][0] + a.rule.xi[q][1] + a.rule.xi[q][2]
+                             : (tt == 1 ? a.rule.xi[q][1] + a.rule.xi[q][2] : a.rule.xi[q][2]);
+    const double d = (i + s) * a.h - a.centres[rest * 3 + ax];
+    etab[t] = exp(-d * d * a.inv_w2);
+  }
+}
 
 // contrib[T][a][r] = int_T F_r . w_a with the rule above (6 |T| = h^3).
 __global__ void k_load_tets(LoadArgs a) {
@@ -242,18 +265,22 @@ __global__ void k_load_tets(LoadArgs a) {
     kuhn_grads(p, g);
     double2 acc[6];
     for (int e = 0; e < 6; ++e) acc[e] = make_double2(0.0, 0.0);
-    const double* C = a.centres + (int64_t)r * a.nbumps * 3;
     const double2* PL = a.pol + (int64_t)r * a.nbumps * 3;
+    // Gaussian factors from the per-axis table: the point's coordinate along axis s_t
+    // (t = 0, 1, 2) is (c + S[3q + t]) h with S the partial sums xi1+xi2+xi3, xi2+xi3, xi3
+    int cs[3];
+    for (int t = 0; t < 3; ++t) cs[t] = (int)(P[0][a_perms[p][t]] / a.h + 0.5);
+    const double* E = a.etab + (int64_t)r * a.nbumps * 3 * a.n * 81;
     for (int q = 0; q < 27; ++q) {
       const double x1 = a.rule.xi[q][0], x2 = a.rule.xi[q][1], x3 = a.rule.xi[q][2];
       const double lam[4] = {1.0 - x1 - x2 - x3, x1, x2, x3};
-      double x[3];
-      for (int ax = 0; ax < 3; ++ax)
-        x[ax] = P[0][ax] + x1 * (P[1][ax] - P[0][ax]) + x2 * (P[2][ax] - P[0][ax]) + x3 * (P[3][ax] - P[0][ax]);
       double2 F[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
       for (int b = 0; b < a.nbumps; ++b) {
-        const double dx = x[0] - C[3 * b], dy = x[1] - C[3 * b + 1], dz = x[2] - C[3 * b + 2];
-        const double e = exp(-(dx * dx + dy * dy + dz * dz) * a.inv_w2);
+        // exp(-|x - c_b|^2 / w^2) = product over axes of exp(-(x_a - c_{b,a})^2 / w^2)
+        const double* Eb = E + (int64_t)b * 3 * a.n * 81;
+        double e = 1.0;
+        for (int t = 0; t < 3; ++t)
+          e *= Eb[((int64_t)a_perms[p][t] * a.n + cs[t]) * 81 + 3 * q + t];
         for (int ax = 0; ax < 3; ++ax) {
           F[ax].x += e * PL[3 * b + ax].x;
           F[ax].y += e * PL[3 * b + ax].y;
@@ -310,6 +337,7 @@ void load_vector(const Problem& P, int nrhs, int nbumps, const double* h_centres
   MX_CUDA(cudaMemcpyAsync(dc.p, h_centres, dc.bytes(), cudaMemcpyHostToDevice, s));
   MX_CUDA(cudaMemcpyAsync(dp.p, h_pol, dp.bytes(), cudaMemcpyHostToDevice, s));
   DevBuf<double2> contrib(ntet * 6 * chunk);
+  DevBuf<double> etab((size_t)chunk * nbumps * 3 * n * 81);
   for (int r0 = 0; r0 < nrhs; r0 += chunk) {
     const int nr = std::min(chunk, nrhs - r0);
     LoadArgs a;
@@ -320,6 +348,9 @@ void load_vector(const Problem& P, int nrhs, int nbumps, const double* h_centres
     a.centres = dc.p + (int64_t)r0 * nbumps * 3;
     a.pol = dp.p + (int64_t)r0 * nbumps * 3;
     a.contrib = contrib.p;
+    a.etab = etab.p;
+    MX_LAUNCH(k_load_table<<<grid_for((int64_t)nr * nbumps * 3 * n * 81, 256), 256, 0, s>>>(a, etab.p));
+    MX_CHECK_LAUNCH();
     MX_LAUNCH(k_load_tets<<<grid_for(ntet * nr, 128), 128, 0, s>>>(a));
     MX_CHECK_LAUNCH();
     MX_LAUNCH(k_load_gather<<<grid_for(P.fine.n_dof * nr, 256), 256, 0, s>>>(

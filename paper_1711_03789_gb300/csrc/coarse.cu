@@ -180,6 +180,8 @@ static void sweep(Problem& P, T2* F, const T2* Dinv, T2* r, int nrhs) {
   const int64_t work = (int64_t)std::min(b, n) * nrhs;
   int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, std::max<int64_t>(1, (work + 255) / 256));
   grid = std::max(1, std::min(grid, sm_count()));
+  // fewer blocks make the grid-wide barrier between column blocks cheaper (tunable)
+  if (P.tune_coarse_blocks > 0) grid = std::min(P.tune_coarse_blocks, sm_count() * per_sm);
   void* args[] = {(void*)&n, (void*)&b, (void*)&ld, (void*)&F, (void*)&Dinv, (void*)&r, (void*)&nrhs};
   const double entries = (double)n * (2.0 * b + 1.0) - (double)b * (b + 1.0);
   ProfScope ps(K_COARSE_SWEEP, P.stream, 1, sizeof(T2) * (entries + 2.0 * n * nrhs), 8.0 * entries * nrhs);

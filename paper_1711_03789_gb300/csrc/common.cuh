@@ -117,6 +117,19 @@ template <typename C> __host__ __device__ inline C crcp(C a) {
 }
 template <typename C> __host__ __device__ inline auto cabs2(C a) { return a.x * a.x + a.y * a.y; }
 
+// Complex accumulation on the paired FP32 pipe (sm_100 family FFMA2): for a sum of
+// products a * b keep p = sum a.x * b and q = sum a.y * b (two paired FMAs per term, no
+// lane swaps); the complex sum is (p.x - q.y, p.y + q.x).
+struct CAcc2 {
+  float2 p, q;
+};
+__device__ __forceinline__ void cacc_zero(CAcc2& s) { s.p = make_float2(0.f, 0.f); s.q = s.p; }
+__device__ __forceinline__ void cacc(CAcc2& s, float2 a, float2 b) {
+  s.p = __ffma2_rn(make_float2(a.x, a.x), b, s.p);
+  s.q = __ffma2_rn(make_float2(a.y, a.y), b, s.q);
+}
+__device__ __forceinline__ float2 cacc_value(const CAcc2& s) { return make_float2(s.p.x - s.q.y, s.p.y + s.q.x); }
+
 __host__ __device__ inline float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
 __host__ __device__ inline float2 to_c64(float2 a) { return a; }
 __host__ __device__ inline double2 to_c128(float2 a) { return make_double2(a.x, a.y); }

@@ -60,10 +60,13 @@ void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int
 
 // ---- preconditioner: scatter-add of local solutions (+ coarse prolongation) ---------
 // z[i][r] = sum_{q in inv(i)} loc[q][r] + sum_{p} (R^0)^T_{ip} y0[p][r]   (Eq. 3.4)
+// zc (optional): the stored z promoted to c128, so that the operator reads exactly the
+// stored vector without converting it once per nonzero.
 template <typename LT, typename CT, typename ZT>
 __global__ void k_scatter(int64_t n, int nrhs, const int32_t* __restrict__ inv_ptr, const int32_t* __restrict__ inv_pos,
                           const LT* __restrict__ loc, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tcol,
-                          const double* __restrict__ tval, const CT* __restrict__ y0, int use_local, ZT* __restrict__ z) {
+                          const double* __restrict__ tval, const CT* __restrict__ y0, int use_local, ZT* __restrict__ z,
+                          double2* __restrict__ zc) {
   const int64_t work = n * nrhs;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t % nrhs);
@@ -83,7 +86,9 @@ __global__ void k_scatter(int64_t n, int nrhs, const int32_t* __restrict__ inv_p
         acc.x = fma(tval[e], v.x, acc.x);
         acc.y = fma(tval[e], v.y, acc.y);
       }
-    z[t] = conv<ZT>(acc);
+    const ZT zv = conv<ZT>(acc);
+    z[t] = zv;
+    if (zc) zc[t] = to_c128(zv);
   }
 }
 
@@ -94,6 +99,7 @@ struct Workspace {
   DevBuf<double2> V;              // (m+1) [n][nrhs]
   DevBuf<unsigned char> Z;        // m [n][nrhs] of c64 / c128
   DevBuf<double2> w, b, x, r;     // [n][nrhs]
+  DevBuf<double2> zc;             // [n][nrhs] current z_j promoted to c128 (mixed)
   DevBuf<unsigned char> loc;      // [sum_local][nrhs] local solutions
   DevBuf<double2> yc;             // [n_c][nrhs]
   DevBuf<double2> H;              // [m][m+1][nrhs]   column j, row i
@@ -140,6 +146,7 @@ static Workspace& workspace(Problem& P, int nrhs, int m) {
   W->b.alloc(nv);
   W->x.alloc(nv);
   W->r.alloc(nv);
+  if (P.precision == MX_MIXED) W->zc.alloc(nv);
   W->loc.alloc((size_t)P.sum_local * nrhs * zsz);
   if (P.coarse_m) W->yc.alloc((size_t)P.n_c * nrhs);
   W->H.alloc((size_t)m * (m + 1) * nrhs);
@@ -161,7 +168,7 @@ static Workspace& workspace(Problem& P, int nrhs, int m) {
   return *W;
 }
 
-void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, int levels) {
+void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, int levels, double2* zc) {
   Workspace& W = workspace(P, nrhs, P.ws ? std::max(P.ws->m, 1) : 1);
   cudaStream_t s = P.stream;
   const bool mixed = P.precision == MX_MIXED;
@@ -179,7 +186,7 @@ void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, i
                (levels & 1 ? 2.0 * (double)P.sum_local * nrhs : 0.0) + (coarse ? 4.0 * (double)P.R0T.nnz * nrhs : 0.0));
 #define MX_SCATTER(LT, CT, ZT)                                                                            \
   MX_LAUNCH(k_scatter<LT, CT, ZT><<<grid, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p, (const LT*)W.loc.p, tp, \
-                                             P.R0T.col.p, P.R0T.val.p, (const CT*)W.yc.p, levels & 1, (ZT*)z))
+                                             P.R0T.col.p, P.R0T.val.p, (const CT*)W.yc.p, levels & 1, (ZT*)z, zc))
   if (mixed) {
     if (ztype == 0) MX_SCATTER(float2, float2, double2);
     else MX_SCATTER(float2, float2, float2);
@@ -569,9 +576,11 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     for (int j = 0; j < m; ++j) {
       unsigned char* zj = W.Z.p + (size_t)j * nv * zsz;
       // z_j = B^{-1} v_j ; w = A z_j
-      precond_apply(P, W.V.p + (int64_t)j * nv, zj, ztype, nrhs, 3);
+      // mixed: the scatter also writes the stored c64 z_j promoted to c128 for the operator
+      precond_apply(P, W.V.p + (int64_t)j * nv, zj, ztype, nrhs, 3, mixed ? W.zc.p : nullptr);
       launches += 1 + (P.coarse_m ? 2 : 0) + 1;
-      spmv(P, P.xi_prob, zj, ztype, W.w.p, nrhs, s);
+      if (mixed) spmv(P, P.xi_prob, W.zc.p, 0, W.w.p, nrhs, s);
+      else spmv(P, P.xi_prob, zj, ztype, W.w.p, nrhs, s);
       ++launches;
       // Arnoldi: classical Gram-Schmidt, second pass when needed
       for (int pass = 0; pass < 2; ++pass) {

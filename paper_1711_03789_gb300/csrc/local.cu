@@ -331,7 +331,8 @@ int64_t local_factor_bytes(Problem& P) {
   const int64_t esz = P.precision == MX_MIXED ? 8 : 16;
   int64_t blocks = 0;
   for (int l = 0; l < P.n_sub; ++l) blocks += (P.h_nl[l] + NB - 1) / NB;
-  return esz * (P.h_mat_off[P.n_sub] + blocks * 2 * NB * NB);
+  const int64_t panels = P.tune_local_tc ? panel_bytes_planned(P) : 0;
+  return esz * (P.h_mat_off[P.n_sub] + blocks * 2 * NB * NB) + panels;
 }
 
 void extract_minors(Problem& P) {
@@ -453,6 +454,9 @@ void factor_local(Problem& P) {
   MX_CUDA(cudaStreamSynchronize(P.stream));
   P.minors_ready = false;
   P.factored = true;
+  P.panels.reset();
+  P.panels_ok = false;
+  if (P.precision == MX_MIXED && P.tune_local_tc) build_panels(P);
 }
 
 // ---- local solves -------------------------------------------------------------------
@@ -504,11 +508,23 @@ __device__ inline void diag_apply(const T2* __restrict__ D, int c0, int kb, T2* 
     if (t < kb * G) {
       const int i = t / G, g = t % G;
       // D is zero outside its triangle and beyond kb; window slots always hold finite values
+      if constexpr (std::is_same<T2, float2>::value) {
+        CAcc2 s;
+        cacc_zero(s);
 #pragma unroll
-      for (int k = 0; k < NB; ++k) {
-        int sk = s0 + k;
-        if (sk >= win) sk -= win;
-        cfma(out[c], Ds[i][k], W[sk * G + g]);
+        for (int k = 0; k < NB; ++k) {
+          int sk = s0 + k;
+          if (sk >= win) sk -= win;
+          cacc(s, Ds[i][k], W[sk * G + g]);
+        }
+        out[c] = cacc_value(s);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          int sk = s0 + k;
+          if (sk >= win) sk -= win;
+          cfma(out[c], Ds[i][k], W[sk * G + g]);
+        }
       }
     }
   }
@@ -529,19 +545,46 @@ template <typename T2, int G>
 __device__ __forceinline__ void row_update(const T2* __restrict__ F, int64_t off, int ld, int b, int i, int c0, int kb,
                                            int klo, int khi, T2* W, int win) {
   const int si = i % win, s0 = c0 % win;
+  // chunk of factor entries in flight per thread: smaller for wide right-hand-side groups
+  constexpr int CH = G >= 8 ? 8 : 16;
+  if constexpr (std::is_same<T2, float2>::value) {
+    // FP32: paired-FMA accumulation, two FFMA2 per complex product
+    CAcc2 s[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) cacc_zero(s[g]);
+#pragma unroll
+    for (int kk = 0; kk < NB; kk += CH) {
+      float2 l[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int k = c0 + kk + u;
+        l[u] = (kk + u < kb && k >= klo && k < khi) ? F[bidx(off, ld, b, i, k)] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        int sk = s0 + kk + u;
+        if (sk >= win) sk -= win;
+#pragma unroll
+        for (int g = 0; g < G; ++g) cacc(s[g], l[u], W[sk * G + g]);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) W[si * G + g] = csub(W[si * G + g], cacc_value(s[g]));
+    return;
+  }
   T2 acc[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) acc[g] = W[si * G + g];
 #pragma unroll
-  for (int kk = 0; kk < NB; kk += 16) {
-    T2 l[16];
+  for (int kk = 0; kk < NB; kk += CH) {
+    T2 l[CH];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
+    for (int u = 0; u < CH; ++u) {
       const int k = c0 + kk + u;
       l[u] = (kk + u < kb && k >= klo && k < khi) ? F[bidx(off, ld, b, i, k)] : czero<T2>();
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
+    for (int u = 0; u < CH; ++u) {
       int sk = s0 + kk + u;
       if (sk >= win) sk -= win;
 #pragma unroll
@@ -553,7 +596,7 @@ __device__ __forceinline__ void row_update(const T2* __restrict__ F, int64_t off
 }
 
 template <typename T2, int G>
-__global__ void __launch_bounds__(256, 2) k_local_solve(SolveArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T2) == 8 && G < 16 ? 3 : 2)) k_local_solve(SolveArgs a) {
   extern __shared__ unsigned char smem_raw[];
   T2* W = reinterpret_cast<T2*>(smem_raw);  // [win][G]
   __shared__ T2 Ds[NB][NB + 1];             // diagonal block of the current step
@@ -670,6 +713,13 @@ void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs) {
     a.alg_flops = 8.0 * (double)P.band_entries * nrhs;
   }
   const bool mixed = P.precision == MX_MIXED;
+  if (mixed && P.tune_local_tc) {
+    if (!P.panels_ok) build_panels(P);
+    if (P.panels_ok) {
+      local_solves_tc(P, v, vtype, loc, nrhs, a.alg_bytes, a.alg_flops);
+      return;
+    }
+  }
   // right-hand sides per block: the window must fit in shared memory
   const size_t esz = mixed ? 8 : 16;
   int G = 1;

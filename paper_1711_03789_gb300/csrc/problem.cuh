@@ -80,6 +80,7 @@ struct Problem {
   bool dense_local = false;        // force b_l = n_l - 1 (full dense storage)
   int tune_local_group = 0;        // cap on right-hand sides per local-solve block (0 = 16)
   int tune_lu_tc = 0;              // FP32 LU trailing update: 0 CUDA cores, 1 TF32, 3 split 3 x TF32
+  int tune_coarse_blocks = 0;      // blocks of the cooperative coarse sweep (0 = by work)
   std::vector<int32_t> h_band;     // [n_sub] half-bandwidths
   int64_t band_entries = 0;        // sum over subdomains of entries with |i - j| <= b_l
   DevBuf<int32_t> band;
@@ -90,6 +91,14 @@ struct Problem {
   DevBuf<unsigned char> factors;
   DevBuf<int64_t> dinv_off;        // [n_sub + 1] offsets of the inverted diagonal blocks
   DevBuf<unsigned char> dinv;      // inverted NB x NB diagonal blocks of L and U
+  // tensor-core local solves (mixed form): TF32-rounded panel images of the factors in the
+  // K-major shared-memory layout, one per block column and sweep (local_tc.cu)
+  int tune_local_tc = 1;           // 0 CUDA-core substitution, 1 tensor-core panels (mixed form)
+  bool panels_ok = false;
+  int64_t panel_bytes = 0;
+  DevBuf<unsigned char> panels;
+  DevBuf<int64_t> pan_start;       // [n_sub + 1] first panel of each subdomain
+  DevBuf<int64_t> pan_tab;         // byte offset of every panel image
   bool factored = false;
   bool minors_ready = false;
 
@@ -149,6 +158,14 @@ void invert_diag_blocks(const BandBatch& B, const T2* A, const int64_t* doff, T2
 // (element type of the factors), v [nrhs][n] c128 or c64 (vtype 0: c128, 1: c64).
 void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs);
 
+// ---- local_tc.cu --------------------------------------------------------------------
+// panel images of the c64 factors for the tensor-core solves (after factor_local)
+void build_panels(Problem& P);
+// bytes build_panels will allocate (0 when a half-bandwidth is too large for them)
+int64_t panel_bytes_planned(const Problem& P);
+// the local solves of local_solves() on the tensor cores (requires P.panels_ok)
+void local_solves_tc(Problem& P, const void* v, int vtype, void* loc, int nrhs, double alg_bytes, double alg_flops);
+
 // ---- coarse.cu ----------------------------------------------------------------------
 void factor_coarse(Problem& P);
 // y = (A^0)^{-1} R^0 v: coarse_rhs [nrhs][n_c] c128 workspace
@@ -159,7 +176,7 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs);
 void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int nrhs,
           cudaStream_t s);
 // z = B^{-1} v into z [nrhs][n] c128 (ztype 0) or c64 (ztype 1)
-void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, int levels);
+void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, int levels, double2* zc = nullptr);
 int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, int restart,
                 int max_it, mx_rhs_stats* stats);
 void free_workspace(Problem& P);

@@ -140,6 +140,7 @@ def test_preconditioner_apply(prec, levels, nrhs):
     lv = tuple(x for x, bit in ((1, 1), (0, 2)) if levels & bit)
     ze = O.dd.apply(v.T, levels=lv).T
     with _handle(n, k, 0.0, xi, 5, 1, cm=5, prec=prec) as P:
+        mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, 0)  # FP32 CUDA-core local solves
         P.factor()
         z = P.precond(v, levels=levels)
     tol = 1e-11 if prec == mx.MX_PLAIN_FP64 else 1e-4
@@ -257,3 +258,58 @@ def test_local_factor_tensor_core_modes(mode, tol):
             L = np.tril(F, -1) + np.eye(F.shape[0])
             Al = S.minor(l).toarray()
             assert np.abs(L @ np.triu(F) - Al).max() <= tol * np.abs(Al).max()
+
+
+@pytest.mark.parametrize("n,nrhs,after", [(10, 1, False), (10, 16, True), (20, 16, False), (20, 20, False),
+                                          (20, 32, True)])
+def test_local_solves_tensor_cores(n, nrhs, after):
+    """Local solves on tcgen05 (TF32 panels of the c64 factors, right-hand-side block as a
+    TF32 hi + lo pair) against the oracle's pivoted dense local solves. At n = 20 the local
+    matrices have about 2000 rows, so the 512-slot accumulator ring wraps several times;
+    nrhs = 20 leaves a ragged group of 32. `after` switches the mode after factor (panel
+    images built at the first solve). Bound: the factors enter rounded to TF32 (unit
+    roundoff u = 2^-12 relative), so the solves carry a perturbation of a few u; the test
+    allows 8 u per right-hand side."""
+    k, xi = 10.0, 100.0
+    O = OracleProblem(n, k, 0.0, xi, 5, 1)
+    O.factor()
+    v = inputs.random_complex(11, (nrhs, O.n_dof))
+    ze = O.dd.apply(v.T, levels=(1,)).T
+    with _handle(n, k, 0.0, xi, 5, 1, prec=mx.MX_MIXED) as P:
+        if not after:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, 1)
+        P.factor()
+        if after:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, 1)
+        z = P.precond(v, levels=1)
+        mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, 0)
+        zc = P.precond(v, levels=1)
+    err = np.linalg.norm(z - ze) / np.linalg.norm(ze)
+    err_c = np.linalg.norm(zc - ze) / np.linalg.norm(ze)
+    print("tensor", err, "cuda cores", err_c)
+    per_rhs = np.linalg.norm(z - ze, axis=1) / np.linalg.norm(ze, axis=1)
+    assert np.isfinite(z).all()
+    assert per_rhs.max() <= 8 * 2.0**-12, (per_rhs.max(), err_c)
+
+
+def test_gmres_tensor_core_local_solves():
+    """FGMRES with the tensor-core local solves reaches the same solution as the oracle.
+    The TF32 panels perturb the preconditioner by a few 2^-12 relative, which FGMRES
+    absorbs with a few more iterations at a 1e-10 tolerance (bound: 25 % more)."""
+    n, k, nrhs = 10, 6.0, 3
+    c, p = inputs.bump_batch(1, nrhs)
+    O = OracleProblem(n, k, k, k, 5, 1, coarse_m=5)
+    O.factor()
+    fo = O.load_vector(c, p, 0.1)
+    xo, ost = O.solve(fo, tol=1e-10, restart=0, max_it=300)
+    with _handle(n, k, k, k, 5, 1, cm=5, prec=mx.MX_MIXED) as P:
+        mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, 1)
+        P.factor()
+        f = P.load_vector(c, p, 0.1)
+        x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
+    assert rc == mx.MX_OK
+    for r in range(nrhs):
+        assert st[r]["converged"]
+        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
+        assert err <= 1e-8, (r, err)
+        assert st[r]["iterations"] <= 1.25 * ost[r][0], (st[r], ost[r])
