@@ -18,10 +18,13 @@
 // A row leaves the ring when its block is solved: the block's 32 columns are read back
 // (hi + lo lanes), subtracted from the right-hand side and zeroed for reuse.
 //
-// Warp roles: warps 0-7 run the substitution steps (the elected thread 0 issues the
-// MMAs); warp 8 streams the panel chunks (up to 128 rows, 32 KB) through a ring of
-// NBUF shared-memory buffers with mbarrier hand-off. Every wait is bounded; a timeout
-// sets status[2], stops the block at the next step and drains the copies in flight.
+// Warp roles: warps 0-7 run the substitution steps; warp 9 issues the MMAs of a step as
+// soon as its A operand is staged (the 32 rows the next block needs first, so the rest of
+// the update runs on the tensor cores while the next block is solved); warp 8 streams the
+// panel chunks (up to 128 rows, 32 KB) through a ring of shared-memory buffers and the
+// inverted diagonal blocks through a second ring, with mbarrier hand-off. Every wait is
+// bounded; a timeout sets status[2], stops the block at the next step and drains the
+// copies in flight.
 #include "problem.cuh"
 #include "tc.cuh"
 
@@ -36,13 +39,12 @@ constexpr uint32_t SBO = (KR / 4) * 128;       // 8-row groups: 2048 bytes
 constexpr int ROW_BYTES = KR * 4;              // one panel row: 256 bytes
 constexpr int CHUNK_ROWS = 128;
 constexpr int CHUNK_BYTES = CHUNK_ROWS * ROW_BYTES;  // 32 KB
-constexpr int NBUF = 5;
 constexpr int RING = 512;                      // TMEM columns (accumulator ring)
 constexpr int A_BYTES = 128 * ROW_BYTES;       // A operand: 32 KB
 constexpr int D_BYTES = SB * SB * 8;           // one inverted diagonal block (c64)
 constexpr int MAX_BP = 448;                    // rows alive (<= bp + 2 NB) must fit the ring
 constexpr int WAIT_LIMIT = 1 << 22;
-constexpr int THREADS = 288;                   // 8 compute warps + 1 copy warp
+constexpr int THREADS = 320;                   // 8 compute warps, 1 copy warp, 1 MMA warp
 
 __host__ __device__ inline int pad32(int x) { return (x + 31) & ~31; }
 __host__ __device__ inline int imin(int a, int b) { return a < b ? a : b; }
@@ -61,12 +63,6 @@ __host__ __device__ inline void panel_rows(int dir, int s, int n, int bp, int& r
     rb = imax(0, c0 - bp);
     cnt = c0 - rb;
   }
-}
-
-size_t solve_smem_bytes(int G) {
-  const int lo = 2 * G > 32 ? 2 * G : 32;
-  const int nld = (lo + 2 * G + 31) / 32;
-  return (size_t)NBUF * CHUNK_BYTES + A_BYTES + D_BYTES + (size_t)nld * 32 * 32 * 4;
 }
 
 }  // namespace
@@ -190,21 +186,56 @@ __device__ __forceinline__ float2 load_rhs(const void* v, int vtype, int64_t idx
 }
 
 template <int G>
+struct TcCfg {
+  static constexpr int LO = 2 * G > 32 ? 2 * G : 32;       // first lane / A row of the low parts
+  static constexpr int NLD = (LO + 2 * G + 31) / 32;       // warps reading accumulator lanes
+  static constexpr int UNITS = 16 * G;                     // (row pair, rhs) units per block step
+  static constexpr int UPT = UNITS >= 256 ? UNITS / 256 : 1;
+  static constexpr int NBUF = G >= 32 ? 3 : 4;             // panel chunk buffers
+  static constexpr size_t OFF_A = (size_t)NBUF * CHUNK_BYTES;
+  static constexpr size_t OFF_D = OFF_A + 2 * A_BYTES;
+  static constexpr size_t OFF_ACC = OFF_D + 2 * D_BYTES;
+  static constexpr size_t OFF_VS = OFF_ACC + (size_t)NLD * 32 * 32 * 4;
+  static constexpr size_t SMEM = OFF_VS + (size_t)SB * G * 8;
+};
+
+// A operand row (TMEM lane) of real component ri of right-hand side g, part 0 = TF32 hi,
+// part 1 = remainder: eight consecutive right-hand sides share a core matrix, so the
+// 16-byte stores of eight threads hit eight different bank groups.
+template <int G>
+__device__ __forceinline__ int arow(int g, int ri, int part) {
+  return part * TcCfg<G>::LO + 16 * (g >> 3) + 8 * ri + (g & 7);
+}
+
+// MMAs for `len` panel rows starting at row `off` of the chunk in shared memory at b0,
+// matrix row `row0` first; split where the accumulator ring wraps.
+__device__ __forceinline__ void mma_rows(uint32_t tmem, uint64_t da, uint32_t b0, int off, int len, int row0) {
+  while (len > 0) {
+    const int col = row0 & (RING - 1);
+    const int nn = imin(len, RING - col);
+    const uint32_t idesc = tc::idesc_tf32(128, nn);
+    const uint64_t db = tc::sdesc(b0 + (uint32_t)(off >> 3) * SBO, LBO, SBO);
+#pragma unroll
+    for (int kk = 0; kk < KR / 8; ++kk) tc::mma_tf32(tmem + (uint32_t)col, da + 16 * kk, db + 16 * kk, idesc, 1);
+    off += nn;
+    row0 += nn;
+    len -= nn;
+  }
+}
+
+template <int G>
 __global__ void __launch_bounds__(THREADS, 1) k_local_solve_tc(TcArgs a) {
-  constexpr int LO = 2 * G > 32 ? 2 * G : 32;     // first lane / A row of the low parts
-  constexpr int NLD = (LO + 2 * G + 31) / 32;     // warps reading accumulator lanes
-  constexpr int PAIRS = SB * G / 256;             // (row, rhs) pairs per compute thread
-  static_assert(SB * G % 256 == 0 && LO + 2 * G <= 128, "unsupported group size");
+  using C = TcCfg<G>;
+  constexpr int LO = C::LO, NLD = C::NLD, UNITS = C::UNITS, UPT = C::UPT, NBUF = C::NBUF;
+  static_assert(G % 8 == 0 && LO + 2 * G <= 128, "unsupported group size");
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* bufs = smem;
-  unsigned char* Aop = smem + NBUF * CHUNK_BYTES;
-  float2* Dsm = reinterpret_cast<float2*>(Aop + A_BYTES);
-  float* accs = reinterpret_cast<float*>(Aop + A_BYTES + D_BYTES);  // [NLD][32 rows][32 lanes]
-  float2* vs = reinterpret_cast<float2*>(accs);                     // [32][G], reuses accs
-  __shared__ __align__(8) uint64_t full[NBUF], empty[NBUF], mma_bar;
+  float* accs = reinterpret_cast<float*>(smem + C::OFF_ACC);  // [32 rows][NLD * 32 lanes]
+  float2* vs = reinterpret_cast<float2*>(smem + C::OFF_VS);   // [32 rows][G]
+  __shared__ __align__(8) uint64_t full[NBUF], empty[NBUF], dfull[2], dempty[2], mma_bar, aready;
   __shared__ uint32_t tmem_base;
-  __shared__ volatile int cerr;  // set by compute threads only, read after barrier B
+  __shared__ volatile int cerr;   // set by compute threads only, read after barrier B
+  __shared__ volatile int merr;   // set by the MMA warp, folded into cerr by thread 0
 
   const int groups = (a.nrhs + G - 1) / G;
   const int l = blockIdx.x / groups, g0 = (blockIdx.x % groups) * G;
@@ -215,21 +246,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_local_solve_tc(TcArgs a) {
   const int64_t pbase = a.pstart[l];
   const float2* Dl = a.dinv + a.doff[l];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bufs_a = tc::smem_u32(bufs), A_a = tc::smem_u32(Aop);
+  const uint32_t bufs_a = tc::smem_u32(smem), A_a = bufs_a + (uint32_t)C::OFF_A;
+  const uint32_t D_a = bufs_a + (uint32_t)C::OFF_D;
   const uint32_t full_a = tc::smem_u32(&full[0]), empty_a = tc::smem_u32(&empty[0]);
-  const uint32_t mma_a = tc::smem_u32(&mma_bar);
+  const uint32_t dfull_a = tc::smem_u32(&dfull[0]), dempty_a = tc::smem_u32(&dempty[0]);
+  const uint32_t mma_a = tc::smem_u32(&mma_bar), aready_a = tc::smem_u32(&aready);
 
   if (tid == 0) {
     for (int i = 0; i < NBUF; ++i) {
       tc::mbar_init(full_a + 8 * i, 1);
       tc::mbar_init(empty_a + 8 * i, 1);
     }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(dfull_a + 8 * i, 1);
+      tc::mbar_init(dempty_a + 8 * i, 1);
+    }
     tc::mbar_init(mma_a, 1);
+    tc::mbar_init(aready_a, 1);
     tc::mbar_fence_init();
     cerr = 0;
+    merr = 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_base), RING);
-  for (int t = tid; t < A_BYTES / 16; t += THREADS) reinterpret_cast<float4*>(Aop)[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  {
+    float4* A4 = reinterpret_cast<float4*>(smem + C::OFF_A);
+    for (int t = tid; t < 2 * A_BYTES / 16; t += THREADS) A4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -243,8 +285,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_local_solve_tc(TcArgs a) {
   tc::fence_after();
 
   if (warp == 8) {
-    // ---- copy warp: every panel chunk of both sweeps, in consumption order
     if (lane == 0) {
+      // ---- panel chunks of both sweeps in consumption order (backward panels bottom-up)
       int it = 0;
       bool stop = false;
       for (int dir = 0; dir < 2 && !stop; ++dir)
@@ -253,10 +295,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_local_solve_tc(TcArgs a) {
           int rb, cnt;
           panel_rows(dir, s, n, bp, rb, cnt);
           const unsigned char* src = a.img + a.ptab[pbase + (dir ? nblk + s : s)];
-          for (int r0 = 0; r0 < cnt; r0 += CHUNK_ROWS) {
-            const int nr = imin(CHUNK_ROWS, cnt - r0);
+          const int nch = (cnt + CHUNK_ROWS - 1) / CHUNK_ROWS;
+          for (int k = 0; k < nch; ++k) {
+            const int ch = dir == 0 ? k : nch - 1 - k;
+            const int r0 = ch * CHUNK_ROWS, nr = imin(CHUNK_ROWS, cnt - r0);
             const int buf = it % NBUF, use = it / NBUF;
-            if (cerr) { stop = true; break; }
+            if (cerr || merr) { stop = true; break; }
             if (use > 0 && !tc::mbar_wait(empty_a + 8 * buf, (use - 1) & 1, WAIT_LIMIT)) {
               atomicAdd(a.status + 2, 1);
               stop = true;
@@ -268,137 +312,201 @@ __global__ void __launch_bounds__(THREADS, 1) k_local_solve_tc(TcArgs a) {
             ++it;
           }
         }
-      // no copy may still be in flight when the block exits
       for (int j = imax(0, it - NBUF); j < it; ++j) tc::mbar_wait(full_a + 8 * (j % NBUF), (j / NBUF) & 1, WAIT_LIMIT);
+    } else if (lane == 1) {
+      // ---- inverted diagonal blocks, one step ahead
+      int ss = 0;
+      for (int dir = 0; dir < 2; ++dir)
+        for (int q = 0; q < nblk; ++q, ++ss) {
+          const int s = dir == 0 ? q : nblk - 1 - q;
+          const int st = ss & 1, use = ss >> 1;
+          if (cerr || merr) break;
+          if (use > 0 && !tc::mbar_wait(dempty_a + 8 * st, (use - 1) & 1, WAIT_LIMIT)) {
+            atomicAdd(a.status + 2, 1);
+            break;
+          }
+          tc::mbar_expect_tx(dfull_a + 8 * st, (uint32_t)D_BYTES);
+          tc::bulk_g2s(D_a + st * D_BYTES, Dl + (int64_t)s * 2 * SB * SB + dir * SB * SB, (uint32_t)D_BYTES,
+                       dfull_a + 8 * st);
+        }
+      for (int j = imax(0, ss - 2); j < ss; ++j) tc::mbar_wait(dfull_a + 8 * (j & 1), (j >> 1) & 1, WAIT_LIMIT);
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      // ---- MMA issue: per step, once the compute warps have staged the A operand, the
+      // 32 rows the next block needs first (then the mma_bar commit), then the rest
+      int it = 0, ss = 0;
+      bool failed = false;
+      for (int dir = 0; dir < 2; ++dir) {
+        bool stop = false;
+        for (int q = 0; q < nblk; ++q, ++ss) {
+          const int s = dir == 0 ? q : nblk - 1 - q;
+          int rb, cnt;
+          panel_rows(dir, s, n, bp, rb, cnt);
+          if (!tc::mbar_wait_flag(aready_a, ss & 1, WAIT_LIMIT, &cerr)) { stop = true; break; }
+          tc::fence_after();
+          if (cnt == 0 || failed) {
+            tc::mma_commit(mma_a);
+            continue;
+          }
+          const uint64_t da = tc::sdesc(A_a + (uint32_t)((ss & 1) * A_BYTES), LBO, SBO);
+          const int nch = (cnt + CHUNK_ROWS - 1) / CHUNK_ROWS;
+          for (int k = 0; k < nch; ++k) {
+            const int ch = dir == 0 ? k : nch - 1 - k;
+            const int r0 = ch * CHUNK_ROWS, nr = imin(CHUNK_ROWS, cnt - r0);
+            const int buf = it % NBUF, use = it / NBUF;
+            const uint32_t b0 = bufs_a + buf * CHUNK_BYTES;
+            const bool ok = !failed && tc::mbar_wait(full_a + 8 * buf, use & 1, WAIT_LIMIT);
+            if (!ok && !failed) {
+              failed = true;
+              merr = 1;
+              atomicAdd(a.status + 2, 1);
+            }
+            if (k == 0) {
+              const int fr = dir == 0 ? 0 : cnt - 32 - r0;
+              if (ok) mma_rows(tmem, da, b0, fr, 32, rb + r0 + fr);
+              tc::mma_commit(mma_a);
+              if (ok && fr > 0) mma_rows(tmem, da, b0, 0, fr, rb + r0);
+              if (ok && nr - fr - 32 > 0) mma_rows(tmem, da, b0, fr + 32, nr - fr - 32, rb + r0 + fr + 32);
+            } else if (ok) {
+              mma_rows(tmem, da, b0, 0, nr, rb + r0);
+            }
+            if (ok) tc::mma_commit(empty_a + 8 * buf);
+            ++it;
+          }
+        }
+        if (stop) break;
+      }
     }
   } else {
     // ---- compute warps
-    float2 rpre[PAIRS];
-    float4 dpre[2];
-    auto prefetch = [&](int dir, int s) {
+    float2 rcur[UPT][2], rnext[UPT][2];
+    auto load_r = [&](float2 (&r)[UPT][2], int dir, int s) {
       const int c0 = SB * s;
 #pragma unroll
-      for (int c = 0; c < PAIRS; ++c) {
-        const int t = tid + 256 * c, j = t / G, g = t % G, i = c0 + j;
-        float2 r = make_float2(0.f, 0.f);
-        if (i < n && g < gn) {
-          r = dir == 0 ? load_rhs(a.v, a.vtype, (int64_t)a.lists[pos0 + i] * a.nrhs + g0 + g)
-                       : a.out[(pos0 + i) * a.nrhs + g0 + g];
+      for (int u = 0; u < UPT; ++u) {
+        const int t = tid + 256 * u, p = t / G, g = t % G;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int i = c0 + 2 * p + e;
+          float2 v = make_float2(0.f, 0.f);
+          if (t < UNITS && i < n && g < gn)
+            v = dir == 0 ? load_rhs(a.v, a.vtype, (int64_t)a.lists[pos0 + i] * a.nrhs + g0 + g)
+                         : a.out[(pos0 + i) * a.nrhs + g0 + g];
+          r[u][e] = v;
         }
-        rpre[c] = r;
       }
-      const float4* D4 = reinterpret_cast<const float4*>(Dl + (int64_t)s * 2 * SB * SB + dir * SB * SB);
-      dpre[0] = D4[tid];
-      dpre[1] = D4[tid + 256];
     };
-    if (nblk > 0) prefetch(0, 0);
+    if (nblk > 0) load_r(rcur, 0, 0);
     bool pending = false, stop = false;
     uint32_t mma_par = 0;
-    int it = 0;  // chunk counter (thread 0)
+    int ss = 0;
     for (int dir = 0; dir < 2 && !stop; ++dir) {
-      for (int q = 0; q < nblk; ++q) {
+      for (int q = 0; q < nblk; ++q, ++ss) {
         const int s = dir == 0 ? q : nblk - 1 - q;
         const int c0 = SB * s, kb = imin(SB, n - c0);
-        tc::bar_sync(1, 256);  // A
-        if (pending) {
-          if (!tc::mbar_wait(mma_a, mma_par, WAIT_LIMIT)) {
-            cerr = 1;
-            if (tid == 0) atomicAdd(a.status + 2, 1);
-          }
-          mma_par ^= 1;
-          pending = false;
-          tc::fence_after();
+        const bool transition = dir == 0 && q == nblk - 1;
+        // right-hand side of the next block, a full step ahead (at the turn of the sweeps
+        // it is this block's y, taken from the registers below)
+        if (!transition) {
+          if (dir == 0) load_r(rnext, 0, s + 1);
+          else if (q + 1 < nblk) load_r(rnext, 1, s - 1);
         }
-        // retire the block rows from the ring
+        // retire the block rows from the ring (the warps that own their lanes)
         if (warp < NLD) {
+          if (pending && !tc::mbar_wait(mma_a, mma_par, WAIT_LIMIT)) {
+            cerr = 1;
+            if (lane == 0) atomicAdd(a.status + 2, 1);
+          }
+          if (tid == 0 && merr) cerr = 1;
+          tc::fence_after();
           uint32_t r[32];
           const uint32_t ad = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(c0 & (RING - 1));
           tc::tmem_ld32(ad, r);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) accs[(warp * 32 + j) * 32 + lane] = __uint_as_float(r[j]);
+          for (int j = 0; j < 32; ++j) accs[j * (32 * NLD) + warp * 32 + lane] = __uint_as_float(r[j]);
           tc::tmem_zero32(ad);
         }
-        reinterpret_cast<float4*>(Dsm)[tid] = dpre[0];
-        reinterpret_cast<float4*>(Dsm)[tid + 256] = dpre[1];
+        if (pending) {
+          mma_par ^= 1;
+          pending = false;
+        }
         tc::bar_sync(1, 256);  // B
         if (cerr) { stop = true; break; }
         // v = r - (acc_hi + acc_lo)
-        float2 vv[PAIRS];
 #pragma unroll
-        for (int c = 0; c < PAIRS; ++c) {
-          const int t = tid + 256 * c, j = t / G, g = t % G;
-          auto acc = [&](int L) { return accs[((L >> 5) * 32 + j) * 32 + (L & 31)]; };
-          const float re = acc(2 * g) + acc(LO + 2 * g), im = acc(2 * g + 1) + acc(LO + 2 * g + 1);
-          vv[c] = make_float2(rpre[c].x - re, rpre[c].y - im);
-        }
-        tc::bar_sync(1, 256);
+        for (int u = 0; u < UPT; ++u) {
+          const int t = tid + 256 * u, p = t / G, g = t % G;
+          if (t < UNITS) {
+            const int mr = arow<G>(g, 0, 0), mi = arow<G>(g, 1, 0), lr = arow<G>(g, 0, 1), li = arow<G>(g, 1, 1);
 #pragma unroll
-        for (int c = 0; c < PAIRS; ++c) {
-          const int t = tid + 256 * c;
-          vs[(t / G) * G + t % G] = vv[c];
+            for (int e = 0; e < 2; ++e) {
+              const int j = 2 * p + e;
+              const float* row = accs + j * (32 * NLD);
+              vs[j * G + g] = make_float2(rcur[u][e].x - (row[mr] + row[lr]), rcur[u][e].y - (row[mi] + row[li]));
+            }
+          }
         }
-        tc::bar_sync(1, 256);
+        tc::bar_sync(1, 256);  // C
         // x_blk = D v (D zero outside the kb x kb block), written out and staged as A
+        const int st = ss & 1;
+        if (!tc::mbar_wait(dfull_a + 8 * st, (ss >> 1) & 1, WAIT_LIMIT)) {
+          cerr = 1;
+          if (tid == 0) atomicAdd(a.status + 2, 1);
+        }
+        const float4* D4 = reinterpret_cast<const float4*>(smem + C::OFF_D + st * D_BYTES);
+        unsigned char* Ab = smem + C::OFF_A + (ss & 1) * A_BYTES;
 #pragma unroll
-        for (int c = 0; c < PAIRS; ++c) {
-          const int t = tid + 256 * c, i = t / G, g = t % G;
-          CAcc2 sacc;
-          cacc_zero(sacc);
+        for (int u = 0; u < UPT; ++u) {
+          const int t = tid + 256 * u, p = t / G, g = t % G;
+          if (t < UNITS) {
+            CAcc2 s0, s1;
+            cacc_zero(s0);
+            cacc_zero(s1);
 #pragma unroll 8
-          for (int jj = 0; jj < SB; ++jj) cacc(sacc, Dsm[i + SB * jj], vs[jj * G + g]);
-          const float2 x = cacc_value(sacc);
-          if (i < kb && g < gn) a.out[(pos0 + c0 + i) * a.nrhs + g0 + g] = x;
-          const float2 h = make_float2(tc::tf32_hi(x.x), tc::tf32_hi(x.y));
-          const float2 e = make_float2(x.x - h.x, x.y - h.y);
-          *reinterpret_cast<float2*>(Aop + tc::kmaj(2 * g, 2 * i, LBO, SBO)) = make_float2(h.x, -h.y);
-          *reinterpret_cast<float2*>(Aop + tc::kmaj(2 * g + 1, 2 * i, LBO, SBO)) = make_float2(h.y, h.x);
-          *reinterpret_cast<float2*>(Aop + tc::kmaj(LO + 2 * g, 2 * i, LBO, SBO)) = make_float2(e.x, -e.y);
-          *reinterpret_cast<float2*>(Aop + tc::kmaj(LO + 2 * g + 1, 2 * i, LBO, SBO)) = make_float2(e.y, e.x);
+            for (int jj = 0; jj < SB; ++jj) {
+              const float4 d = D4[p + (SB / 2) * jj];  // D(2p, jj), D(2p + 1, jj)
+              const float2 w = vs[jj * G + g];
+              cacc(s0, make_float2(d.x, d.y), w);
+              cacc(s1, make_float2(d.z, d.w), w);
+            }
+            const float2 x0 = cacc_value(s0), x1 = cacc_value(s1);
+            if (g < gn) {
+              if (2 * p < kb) a.out[(pos0 + c0 + 2 * p) * a.nrhs + g0 + g] = x0;
+              if (2 * p + 1 < kb) a.out[(pos0 + c0 + 2 * p + 1) * a.nrhs + g0 + g] = x1;
+            }
+            if (transition) {
+              rnext[u][0] = x0;
+              rnext[u][1] = x1;
+            }
+            const float2 h0 = make_float2(tc::tf32_hi(x0.x), tc::tf32_hi(x0.y));
+            const float2 h1 = make_float2(tc::tf32_hi(x1.x), tc::tf32_hi(x1.y));
+            const float2 e0 = make_float2(x0.x - h0.x, x0.y - h0.y);
+            const float2 e1 = make_float2(x1.x - h1.x, x1.y - h1.y);
+            const int k4 = 4 * p;
+            *reinterpret_cast<float4*>(Ab + tc::kmaj(arow<G>(g, 0, 0), k4, LBO, SBO)) = make_float4(h0.x, -h0.y, h1.x, -h1.y);
+            *reinterpret_cast<float4*>(Ab + tc::kmaj(arow<G>(g, 1, 0), k4, LBO, SBO)) = make_float4(h0.y, h0.x, h1.y, h1.x);
+            *reinterpret_cast<float4*>(Ab + tc::kmaj(arow<G>(g, 0, 1), k4, LBO, SBO)) = make_float4(e0.x, -e0.y, e1.x, -e1.y);
+            *reinterpret_cast<float4*>(Ab + tc::kmaj(arow<G>(g, 1, 1), k4, LBO, SBO)) = make_float4(e0.y, e0.x, e1.y, e1.x);
+          }
         }
         tc::fence_proxy_async();
         tc::fence_before();
         tc::bar_sync(1, 256);  // D
-        // next block's right-hand side and diagonal block (y of this block is visible now)
-        if (dir == 0) {
-          if (q + 1 < nblk) prefetch(0, s + 1);
-          else prefetch(1, nblk - 1);
-        } else if (q + 1 < nblk) {
-          prefetch(1, s - 1);
+        if (tid == 0) {
+          tc::mbar_arrive(dempty_a + 8 * st);  // diagonal block consumed
+          tc::mbar_arrive(aready_a);            // A operand of this step staged
         }
-        int rb, cnt;
-        panel_rows(dir, s, n, bp, rb, cnt);
-        if (cnt > 0) {
-          if (tid == 0) {
-            tc::fence_after();
-            for (int r0 = 0; r0 < cnt; r0 += CHUNK_ROWS) {
-              const int nr = imin(CHUNK_ROWS, cnt - r0);
-              const int buf = it % NBUF, use = it / NBUF;
-              if (tc::mbar_wait(full_a + 8 * buf, use & 1, WAIT_LIMIT)) {
-                const uint32_t b0 = bufs_a + buf * CHUNK_BYTES;
-                int done = 0;
-                while (done < nr) {
-                  const int col = (rb + r0 + done) & (RING - 1);
-                  const int nn = imin(nr - done, RING - col);
-                  const uint32_t idesc = tc::idesc_tf32(128, nn);
+        pending = true;
 #pragma unroll
-                  for (int kk = 0; kk < KR / 8; ++kk)
-                    tc::mma_tf32(tmem + (uint32_t)col, tc::sdesc(A_a + kk * 256, LBO, SBO),
-                                 tc::sdesc(b0 + (done >> 3) * SBO + kk * 256, LBO, SBO), idesc, 1);
-                  done += nn;
-                }
-              } else {
-                cerr = 1;
-                atomicAdd(a.status + 2, 1);
-              }
-              tc::mma_commit(empty_a + 8 * buf);
-              ++it;
-            }
-            tc::mma_commit(mma_a);
-          }
-          pending = true;
+        for (int u = 0; u < UPT; ++u) {
+          rcur[u][0] = rnext[u][0];
+          rcur[u][1] = rnext[u][1];
         }
       }
     }
+    // the last step's commit covers every MMA: all have completed before the tensor
+    // memory is released
     if (pending && !tc::mbar_wait(mma_a, mma_par, WAIT_LIMIT) && tid == 0) atomicAdd(a.status + 2, 1);
   }
   tc::fence_before();
@@ -411,7 +519,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_local_solve_tc(TcArgs a) {
 
 template <int G>
 static void launch_tc(const TcArgs& a, int n_sub, cudaStream_t s, double alg_bytes, double alg_flops) {
-  const size_t smem = solve_smem_bytes(G);
+  const size_t smem = TcCfg<G>::SMEM;
   static bool configured = false;
   if (!configured) {
     MX_CUDA(cudaFuncSetAttribute(k_local_solve_tc<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

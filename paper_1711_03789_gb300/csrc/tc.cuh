@@ -115,6 +115,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int lim
   return done != 0;
 }
 
+// bounded wait that also gives up as soon as *flag becomes nonzero
+__device__ __forceinline__ bool mbar_wait_flag(uint32_t bar, uint32_t parity, int limit, const volatile int* flag) {
+  uint32_t done = 0;
+  for (int it = 0; it < limit && !done; ++it) {
+    if (*flag) return false;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing
 // `bytes` transactions on the mbarrier
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
