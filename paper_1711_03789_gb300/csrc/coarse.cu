@@ -1,14 +1,14 @@
 // Coarse level of the two-level preconditioner (Sec. 3.2-3.3, Eq. 3.4 with l = 0):
-// the Galerkin matrix A^0_{xi_prec} assembled on the coarse Kuhn mesh, its FP64 LU
-// (band-limited, no pivoting: A^0 is invertible for xi != 0 by coercivity, Sec. 3.3),
-// and the coarse solve y = (A^0)^{-1} R^0 v.
+// the Galerkin matrix A^0_{xi_prec} assembled on the coarse Kuhn mesh, its LU (band-limited,
+// no pivoting: A^0 is invertible for xi != 0 by coercivity, Sec. 3.3; FP64 in
+// MX_PLAIN_FP64, c64 in MX_MIXED) and the coarse solve y = (A^0)^{-1} R^0 v.
 //
 // The coarse solve runs as one cooperative kernel: the band triangular sweeps proceed in
 // blocks of CB columns; every block of the grid solves the small diagonal triangle
 // redundantly, then updates its share of the rows inside the band, and a grid-wide
-// barrier separates the steps. In MX_MIXED the sweep uses a c64 copy of the FP64
-// factors (the preconditioner only needs to be a fixed linear map; the outer FGMRES
-// recurrence stays in FP64); in MX_PLAIN_FP64 it uses the FP64 factors.
+// barrier separates the steps. In MX_MIXED the factors and the sweep are c64 (the
+// preconditioner only needs to be a fixed linear map; the outer FGMRES recurrence stays in
+// FP64); in MX_PLAIN_FP64 both are FP64.
 #include <cooperative_groups.h>
 
 #include "problem.cuh"
@@ -65,17 +65,24 @@ void factor_coarse(Problem& P) {
   MX_CUDA(cudaMemcpyAsync(P.c_meta.p, meta, 12, cudaMemcpyHostToDevice, s));
   MX_CUDA(cudaMemcpyAsync(P.c_off.p, &zero, 8, cudaMemcpyHostToDevice, s));
   BandBatch B{1, P.c_meta.p, P.c_meta.p + 1, P.c_meta.p + 2, P.c_off.p};
-  band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU, 0);
   const int64_t nq = (nc + CB - 1) / CB;
-  P.c_dinv.alloc(nq * 2 * CB * CB);
-  invert_diag_blocks<double2>(B, P.A0.p, P.c_off.p, P.c_dinv.p, (int)nc, s);
   if (P.precision == MX_MIXED) {
+    // the mixed sweep applies c64 factors: factor the c64 matrix directly (FP32 units,
+    // 1/64 of the FP64 work time on this part) and drop the FP64 copy
     P.A0f.alloc(P.A0.n);
     MX_LAUNCH(k_to_c64<<<grid_for(P.A0.n, 256), 256, 0, s>>>(P.A0.n, P.A0.p, P.A0f.p));
     MX_CHECK_LAUNCH();
-    P.c_dinvf.alloc(P.c_dinv.n);
-    MX_LAUNCH(k_to_c64<<<grid_for(P.c_dinv.n, 256), 256, 0, s>>>(P.c_dinv.n, P.c_dinv.p, P.c_dinvf.p));
-    MX_CHECK_LAUNCH();
+    MX_CUDA(cudaStreamSynchronize(s));  // the conversion has read A0 before it is released
+    P.A0.reset();
+    band_lu<float2>(B, P.A0f.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU,
+                    0);
+    P.c_dinvf.alloc(nq * 2 * CB * CB);
+    invert_diag_blocks<float2>(B, P.A0f.p, P.c_off.p, P.c_dinvf.p, (int)nc, s);
+  } else {
+    band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU,
+                     0);
+    P.c_dinv.alloc(nq * 2 * CB * CB);
+    invert_diag_blocks<double2>(B, P.A0.p, P.c_off.p, P.c_dinv.p, (int)nc, s);
   }
   MX_CUDA(cudaStreamSynchronize(s));
 }
