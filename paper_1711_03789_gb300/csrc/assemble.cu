@@ -190,9 +190,10 @@ void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s) {
 struct QuadRule {
   double xi[27][3];
   double w[27];
+  double cw[27][4];  // w_q h^2 lambda_k(xi_q): weight, Jacobian 6|T| = h^3 and the 1/h of the gradients
 };
 
-static QuadRule make_rule() {
+static QuadRule make_rule(double h) {
   QuadRule r;
   const double s = std::sqrt(0.6);
   const double t[3] = {0.5 * (1.0 - s), 0.5, 0.5 * (1.0 + s)};
@@ -206,6 +207,8 @@ static QuadRule make_rule() {
         r.xi[q][1] = (1.0 - u) * v;
         r.xi[q][2] = (1.0 - u) * (1.0 - v) * w;
         r.w[q] = wt[a] * wt[b] * wt[c] * (1.0 - u) * (1.0 - u) * (1.0 - v);
+        const double lam[4] = {1.0 - r.xi[q][0] - r.xi[q][1] - r.xi[q][2], r.xi[q][0], r.xi[q][1], r.xi[q][2]};
+        for (int k = 0; k < 4; ++k) r.cw[q][k] = r.w[q] * h * h * lam[k];
       }
   return r;
 }
@@ -242,7 +245,11 @@ __global__ void k_load_table(LoadArgs a, double* etab) {
   }
 }
 
-// contrib[T][a][r] = int_T F_r . w_a with the rule above (6 |T| = h^3).
+// contrib[T][a][r] = int_T F_r . w_a with the rule above (6 |T| = h^3). With w_a =
+// lam_P grad lam_Q - lam_Q grad lam_P and F = sum_b p_b G_b (G_b the real Gaussian of
+// bump b), the integral is sum_b (L_bP (p_b . g_Q) - L_bQ (p_b . g_P)) with the four
+// weighted moments L_bk = sum_q w_q h^2 lam_k(xi_q) G_b(x_q) and g the integer gradients
+// (grad lam = g / h): four FP64 FMAs per point and bump instead of a basis evaluation.
 __global__ void k_load_tets(LoadArgs a) {
   const int64_t ntet = 6LL * a.n * a.n * a.n;
   const int64_t work = ntet * a.nrhs;
@@ -252,53 +259,41 @@ __global__ void k_load_tets(LoadArgs a) {
     const int64_t tet = t / a.nrhs;
     const int64_t cube = tet / 6;
     const int p = (int)(tet % 6);
-    double P[4][3];
-    int c[3] = {(int)(cube % a.n), (int)((cube / a.n) % a.n), (int)(cube / ((int64_t)a.n * a.n))};
-    for (int ax = 0; ax < 3; ++ax) P[0][ax] = c[ax] * a.h;
-    for (int k = 0; k < 3; ++k) {
-      for (int ax = 0; ax < 3; ++ax) P[k + 1][ax] = P[k][ax];
-      const int ax = a_perms[p][k];
-      c[ax] += 1;
-      P[k + 1][ax] = c[ax] * a.h;
-    }
-    int g[4][3];
-    kuhn_grads(p, g);
-    double2 acc[6];
-    for (int e = 0; e < 6; ++e) acc[e] = make_double2(0.0, 0.0);
-    const double2* PL = a.pol + (int64_t)r * a.nbumps * 3;
+    const int cx = (int)(cube % a.n), cy = (int)((cube / a.n) % a.n), cz = (int)(cube / ((int64_t)a.n * a.n));
+    const int s0 = a_perms[p][0], s1 = a_perms[p][1], s2 = a_perms[p][2];
+    auto corner = [&](int ax) { return ax == 0 ? cx : (ax == 1 ? cy : cz); };
     // Gaussian factors from the per-axis table: the point's coordinate along axis s_t
-    // (t = 0, 1, 2) is (c + S[3q + t]) h with S the partial sums xi1+xi2+xi3, xi2+xi3, xi3
-    int cs[3];
-    for (int t = 0; t < 3; ++t) cs[t] = (int)(P[0][a_perms[p][t]] / a.h + 0.5);
+    // (t = 0, 1, 2) is (c_{s_t} + S[3q + t]) h with S the partial sums xi1+xi2+xi3,
+    // xi2+xi3, xi3 (the path starts at the cube corner c)
+    const int64_t row0 = ((int64_t)s0 * a.n + corner(s0)) * 81;
+    const int64_t row1 = ((int64_t)s1 * a.n + corner(s1)) * 81 + 1;
+    const int64_t row2 = ((int64_t)s2 * a.n + corner(s2)) * 81 + 2;
     const double* E = a.etab + (int64_t)r * a.nbumps * 3 * a.n * 81;
-    for (int q = 0; q < 27; ++q) {
-      const double x1 = a.rule.xi[q][0], x2 = a.rule.xi[q][1], x3 = a.rule.xi[q][2];
-      const double lam[4] = {1.0 - x1 - x2 - x3, x1, x2, x3};
-      double2 F[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-      for (int b = 0; b < a.nbumps; ++b) {
-        // exp(-|x - c_b|^2 / w^2) = product over axes of exp(-(x_a - c_{b,a})^2 / w^2)
-        const double* Eb = E + (int64_t)b * 3 * a.n * 81;
-        double e = 1.0;
-        for (int t = 0; t < 3; ++t)
-          e *= Eb[((int64_t)a_perms[p][t] * a.n + cs[t]) * 81 + 3 * q + t];
-        for (int ax = 0; ax < 3; ++ax) {
-          F[ax].x += e * PL[3 * b + ax].x;
-          F[ax].y += e * PL[3 * b + ax].y;
-        }
+    const double2* PL = a.pol + (int64_t)r * a.nbumps * 3;
+    double2 acc[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) acc[e] = make_double2(0.0, 0.0);
+    for (int b = 0; b < a.nbumps; ++b) {
+      const double* Eb = E + (int64_t)b * 3 * a.n * 81;
+      double L[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 3
+      for (int q = 0; q < 27; ++q) {
+        const double e = Eb[row0 + 3 * q] * Eb[row1 + 3 * q] * Eb[row2 + 3 * q];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) L[k] = fma(a.rule.cw[q][k], e, L[k]);
       }
-      const double wq = a.rule.w[q] * a.h * a.h * a.h / a.h;  // 6|T| (h^3) times 1/h of grad
+      // p_b . g_k with g_0 = -e_s0, g_1 = e_s0 - e_s1, g_2 = e_s1 - e_s2, g_3 = e_s2
+      const double2 q0 = PL[3 * b + s0], q1 = PL[3 * b + s1], q2 = PL[3 * b + s2];
+      const double2 pi[4] = {make_double2(-q0.x, -q0.y), make_double2(q0.x - q1.x, q0.y - q1.y),
+                             make_double2(q1.x - q2.x, q1.y - q2.y), q2};
+#pragma unroll
       for (int e = 0; e < 6; ++e) {
-        const int P0 = a_ledge[e][0], Q0 = a_ledge[e][1];
-        double2 s = make_double2(0, 0);
-        for (int ax = 0; ax < 3; ++ax) {
-          const double wv = lam[P0] * g[Q0][ax] - lam[Q0] * g[P0][ax];
-          s.x += wv * F[ax].x;
-          s.y += wv * F[ax].y;
-        }
-        acc[e].x += wq * s.x;
-        acc[e].y += wq * s.y;
+        const int P0 = e < 3 ? 0 : (e < 5 ? 1 : 2), Q0 = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+        acc[e].x += L[P0] * pi[Q0].x - L[Q0] * pi[P0].x;
+        acc[e].y += L[P0] * pi[Q0].y - L[Q0] * pi[P0].y;
       }
     }
+#pragma unroll
     for (int e = 0; e < 6; ++e) a.contrib[(tet * 6 + e) * a.nrhs + r] = acc[e];
   }
 }
@@ -344,7 +339,7 @@ void load_vector(const Problem& P, int nrhs, int nbumps, const double* h_centres
     a.n = n; a.nrhs = nr; a.nbumps = nbumps;
     a.h = 1.0 / n;
     a.inv_w2 = 1.0 / (width * width);
-    a.rule = make_rule();
+    a.rule = make_rule(1.0 / n);
     a.centres = dc.p + (int64_t)r0 * nbumps * 3;
     a.pol = dp.p + (int64_t)r0 * nbumps * 3;
     a.contrib = contrib.p;
