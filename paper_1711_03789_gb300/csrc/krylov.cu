@@ -62,34 +62,47 @@ void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int
 // z[i][r] = sum_{q in inv(i)} loc[q][r] + sum_{p} (R^0)^T_{ip} y0[p][r]   (Eq. 3.4)
 // zc (optional): the stored z promoted to c128, so that the operator reads exactly the
 // stored vector without converting it once per nonzero.
-template <typename LT, typename CT, typename ZT>
+template <typename T2> __device__ inline T2 cvt2(float2 a);
+template <> __device__ inline float2 cvt2<float2>(float2 a) { return a; }
+template <> __device__ inline double2 cvt2<double2>(float2 a) { return to_c128(a); }
+template <typename T2> __device__ inline T2 cvt2(double2 a) { return conv<T2>(a); }
+
+// Accumulation in AT: FP32 for the mixed form, whose z is stored in c64 anyway; FP64
+// otherwise. The local solutions are summed in the fixed order of the inverse map.
+template <typename LT, typename CT, typename ZT, typename AT>
 __global__ void k_scatter(int64_t n, int nrhs, const int32_t* __restrict__ inv_ptr, const int32_t* __restrict__ inv_pos,
                           const LT* __restrict__ loc, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tcol,
-                          const double* __restrict__ tval, const CT* __restrict__ y0, int use_local, ZT* __restrict__ z,
+                          const AT* __restrict__ tval, const CT* __restrict__ y0, int use_local, ZT* __restrict__ z,
                           double2* __restrict__ zc) {
+  using A2 = typename cplx<AT>::type;
   const int64_t work = n * nrhs;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t % nrhs);
     const int64_t i = t / nrhs;
-    double2 acc = make_double2(0, 0);
+    A2 acc = czero<A2>();
     if (use_local)
       for (int32_t q = inv_ptr[i]; q < inv_ptr[i + 1]; ++q) {
         const int32_t pos = inv_pos[q];
         if (pos < 0) continue;
-        const double2 v = to_c128(loc[(int64_t)pos * nrhs + r]);
+        const A2 v = cvt2<A2>(loc[(int64_t)pos * nrhs + r]);
         acc.x += v.x;
         acc.y += v.y;
       }
     if (tptr)
       for (int32_t e = tptr[i]; e < tptr[i + 1]; ++e) {
-        const double2 v = to_c128(y0[(int64_t)tcol[e] * nrhs + r]);
+        const A2 v = cvt2<A2>(y0[(int64_t)tcol[e] * nrhs + r]);
         acc.x = fma(tval[e], v.x, acc.x);
         acc.y = fma(tval[e], v.y, acc.y);
       }
-    const ZT zv = conv<ZT>(acc);
+    const ZT zv = cvt2<ZT>(acc);
     z[t] = zv;
     if (zc) zc[t] = to_c128(zv);
   }
+}
+
+__global__ void k_to_f32(int64_t n, const double* a, float* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
 }
 
 struct Workspace {
@@ -184,15 +197,21 @@ void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, i
                    (coarse ? 12.0 * P.R0T.nnz + 4.0 * P.fine.n_dof + lsz * (double)P.n_c * nrhs : 0.0) +
                    zb * (double)work,
                (levels & 1 ? 2.0 * (double)P.sum_local * nrhs : 0.0) + (coarse ? 4.0 * (double)P.R0T.nnz * nrhs : 0.0));
-#define MX_SCATTER(LT, CT, ZT)                                                                            \
-  MX_LAUNCH(k_scatter<LT, CT, ZT><<<grid, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p, (const LT*)W.loc.p, tp, \
-                                             P.R0T.col.p, P.R0T.val.p, (const CT*)W.yc.p, levels & 1, (ZT*)z, zc))
+#define MX_SCATTER(LT, CT, ZT, AT, TV)                                                                        \
+  MX_LAUNCH(k_scatter<LT, CT, ZT, AT><<<grid, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p,            \
+                                                           (const LT*)W.loc.p, tp, P.R0T.col.p, TV,              \
+                                                           (const CT*)W.yc.p, levels & 1, (ZT*)z, zc))
   if (mixed) {
-    if (ztype == 0) MX_SCATTER(float2, float2, double2);
-    else MX_SCATTER(float2, float2, float2);
+    if (coarse && P.R0T_valf.n != (size_t)P.R0T.nnz) {
+      P.R0T_valf.alloc(P.R0T.nnz);
+      MX_LAUNCH(k_to_f32<<<grid_for(P.R0T.nnz, 256), 256, 0, s>>>(P.R0T.nnz, P.R0T.val.p, P.R0T_valf.p));
+      MX_CHECK_LAUNCH();
+    }
+    if (ztype == 0) MX_SCATTER(float2, float2, double2, float, P.R0T_valf.p);
+    else MX_SCATTER(float2, float2, float2, float, P.R0T_valf.p);
   } else {
-    if (ztype == 0) MX_SCATTER(double2, double2, double2);
-    else MX_SCATTER(double2, double2, float2);
+    if (ztype == 0) MX_SCATTER(double2, double2, double2, double, P.R0T.val.p);
+    else MX_SCATTER(double2, double2, float2, double, P.R0T.val.p);
   }
 #undef MX_SCATTER
   MX_CHECK_LAUNCH();

@@ -105,6 +105,7 @@ struct Problem {
   // coarse space (Eq. 3.2): R^0 [n_c x n], its transpose, dense A^0 and its LU (FP64),
   // and a c64 copy of the factors for the mixed-precision coarse solve.
   CsrR R0, R0T;
+  DevBuf<float> R0T_valf;  // FP32 copy of the R^0^T values (mixed-form scatter)
   int64_t n_c = 0;
   int coarse_band = 0;
   int64_t ld_c = 0;
