@@ -87,25 +87,40 @@ void factor_coarse(Problem& P) {
   MX_CUDA(cudaStreamSynchronize(s));
 }
 
-// r0[q][p] = sum_j R^0_pj v[q][j]  (FP64 accumulation), written as T2
-template <typename T2>
+// r0[q][p] = sum_j R^0_pj v[q][j], written as T2: FP64 accumulation for the FP64 form,
+// FP32 (values of R^0 in FP32) for the mixed form, whose coarse solve is c64.
+template <typename T2, typename AT>
 __global__ void k_coarse_restrict(int64_t nc, int64_t n, int nrhs, const int32_t* rowptr, const int32_t* col,
-                                  const double* val, const void* v, int vtype, T2* r0) {
+                                  const AT* val, const void* v, int vtype, T2* r0) {
+  using A2 = typename cplx<AT>::type;
   const int64_t work = nc * nrhs;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(t % nrhs);
     const int64_t p = t / nrhs;
-    double2 acc = make_double2(0, 0);
+    A2 acc = czero<A2>();
     for (int32_t e = rowptr[p]; e < rowptr[p + 1]; ++e) {
       const int64_t idx = (int64_t)col[e] * nrhs + q;
-      double2 x;
-      if (vtype == 0) x = reinterpret_cast<const double2*>(v)[idx];
-      else x = to_c128(reinterpret_cast<const float2*>(v)[idx]);
-      acc.x += val[e] * x.x;
-      acc.y += val[e] * x.y;
+      A2 x;
+      if (vtype == 0) {
+        const double2 d = reinterpret_cast<const double2*>(v)[idx];
+        x = mk((AT)d.x, (AT)d.y);
+      } else if (vtype == 3) {
+        const float4 d = reinterpret_cast<const float4*>(v)[idx];
+        x = mk((AT)d.x, (AT)d.y);
+      } else {
+        const float2 d = reinterpret_cast<const float2*>(v)[idx];
+        x = mk((AT)d.x, (AT)d.y);
+      }
+      acc.x = fma(val[e], x.x, acc.x);
+      acc.y = fma(val[e], x.y, acc.y);
     }
-    r0[p * nrhs + q] = conv<T2>(acc);
+    r0[p * nrhs + q] = conv<T2>(make_double2(acc.x, acc.y));
   }
+}
+
+__global__ void k_to_f32v(int64_t n, const double* a, float* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
 }
 
 // Band triangular sweeps on r [n][nrhs] (in place): forward with unit lower L, backward
@@ -204,12 +219,18 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
   float2* rf = reinterpret_cast<float2*>(yc);  // c64 view of the workspace (mixed)
   {
     ProfScope ps(K_COARSE_RESTRICT, s, 1, rb, 4.0 * P.R0.nnz * nrhs);
-    if (mixed)
-      MX_LAUNCH(k_coarse_restrict<float2><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
-          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, rf));
-    else
-      MX_LAUNCH(k_coarse_restrict<double2><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
+    if (mixed) {
+      if (P.R0_valf.n != (size_t)P.R0.nnz) {
+        P.R0_valf.alloc(P.R0.nnz);
+        MX_LAUNCH(k_to_f32v<<<grid_for(P.R0.nnz, 256), 256, 0, s>>>(P.R0.nnz, P.R0.val.p, P.R0_valf.p));
+        MX_CHECK_LAUNCH();
+      }
+      MX_LAUNCH(k_coarse_restrict<float2, float><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
+          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0_valf.p, v, vtype, rf));
+    } else {
+      MX_LAUNCH(k_coarse_restrict<double2, double><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
           nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, yc));
+    }
     MX_CHECK_LAUNCH();
   }
   if (mixed) sweep<float2>(P, P.A0f.p, P.c_dinvf.p, rf, nrhs);

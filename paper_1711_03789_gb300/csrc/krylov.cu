@@ -112,7 +112,8 @@ struct Workspace {
   DevBuf<double2> V;              // (m+1) [n][nrhs]
   DevBuf<unsigned char> Z;        // m [n][nrhs] of c64 / c128
   DevBuf<double2> w, b, x, r;     // [n][nrhs]
-  DevBuf<double2> zc;             // [n][nrhs] current z_j promoted to c128 (mixed)
+  DevBuf<double2> zc;             // [n][nrhs] current z_j promoted to c128 (unused by the solver)
+  DevBuf<float4> hs;              // [m+2][nrhs] h of the current pass as double-floats (mixed)
   DevBuf<unsigned char> loc;      // [sum_local][nrhs] local solutions
   DevBuf<double2> yc;             // [n_c][nrhs]
   DevBuf<double2> H;              // [m][m+1][nrhs]   column j, row i
@@ -159,7 +160,7 @@ static Workspace& workspace(Problem& P, int nrhs, int m) {
   W->b.alloc(nv);
   W->x.alloc(nv);
   W->r.alloc(nv);
-  if (P.precision == MX_MIXED) W->zc.alloc(nv);
+  if (P.precision == MX_MIXED) W->hs.alloc((size_t)(m + 2) * nrhs);
   W->loc.alloc((size_t)P.sum_local * nrhs * zsz);
   if (P.coarse_m) W->yc.alloc((size_t)P.n_c * nrhs);
   W->H.alloc((size_t)m * (m + 1) * nrhs);
@@ -181,13 +182,13 @@ static Workspace& workspace(Problem& P, int nrhs, int m) {
   return *W;
 }
 
-void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, int levels, double2* zc) {
+void precond_apply(Problem& P, const void* v, void* z, int ztype, int nrhs, int levels, double2* zc, int vtype) {
   Workspace& W = workspace(P, nrhs, P.ws ? std::max(P.ws->m, 1) : 1);
   cudaStream_t s = P.stream;
   const bool mixed = P.precision == MX_MIXED;
-  if (levels & 1) local_solves(P, v, 0, W.loc.p, nrhs);
+  if (levels & 1) local_solves(P, v, vtype, W.loc.p, nrhs);
   const bool coarse = (levels & 2) && P.coarse_m;
-  if (coarse) coarse_solve(P, v, 0, W.yc.p, nrhs);
+  if (coarse) coarse_solve(P, v, vtype, W.yc.p, nrhs);
   const int64_t work = P.fine.n_dof * nrhs;
   const int32_t* tp = coarse ? P.R0T.rowptr.p : nullptr;
   const unsigned grid = grid_for(work, 256, 152LL * 32);
@@ -502,6 +503,17 @@ static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t 
   MX_CHECK_LAUNCH();
 }
 
+// mixed form: double-float passes over the basis, FP64 reduction of the block partials
+static void dots_mixed(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s) {
+  dots_df(W.nblk, n, W.nrhs, nvec, with_norm, reinterpret_cast<const float4*>(W.V.p),
+          reinterpret_cast<const float4*>(W.w.p), W.active.p, W.hpart.p, s);
+  const int total = nvec + with_norm;
+  ProfScope ps(K_ARNOLDI_SMALL, s);
+  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * W.nrhs, 128), 128, 0, s>>>(W.nblk, total, W.nrhs, W.hpart.p,
+                                                                                   W.h2.p));
+  MX_CHECK_LAUNCH();
+}
+
 static void orth_update(Workspace& W, int64_t n, int nvec, cudaStream_t s) {
   const int nr = W.nrhs;
   // V_0..V_{nvec-1} read once, w read and written once
@@ -584,8 +596,12 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     if (!act[r]) { done[r] = 1; rel[r] = 0; estv[r] = 0; }
   }
   MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
-  MX_LAUNCH(k_scale_v0<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p));
-  MX_CHECK_LAUNCH();
+  if (mixed) {
+    scale_v0_df(nv, nrhs, beta.p, W.active.p, W.r.p, reinterpret_cast<float4*>(W.V.p), s);
+  } else {
+    MX_LAUNCH(k_scale_v0<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p));
+    MX_CHECK_LAUNCH();
+  }
   ++launches;
 
   int total_its = 0, restarts = 0;
@@ -594,11 +610,10 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     std::vector<int32_t> start_active = act;
     for (int j = 0; j < m; ++j) {
       unsigned char* zj = W.Z.p + (size_t)j * nv * zsz;
-      // z_j = B^{-1} v_j ; w = A z_j
-      // mixed: the scatter also writes the stored c64 z_j promoted to c128 for the operator
-      precond_apply(P, W.V.p + (int64_t)j * nv, zj, ztype, nrhs, 3, mixed ? W.zc.p : nullptr);
+      // z_j = B^{-1} v_j ; w = A z_j (mixed: v_j and w are double-floats, z_j is c64)
+      precond_apply(P, W.V.p + (int64_t)j * nv, zj, ztype, nrhs, 3, nullptr, mixed ? 3 : 0);
       launches += 1 + (P.coarse_m ? 2 : 0) + 1;
-      if (mixed) spmv(P, P.xi_prob, W.zc.p, 0, W.w.p, nrhs, s);
+      if (mixed) spmv_df(P, reinterpret_cast<const float2*>(zj), reinterpret_cast<float4*>(W.w.p), nrhs, s);
       else spmv(P, P.xi_prob, zj, ztype, W.w.p, nrhs, s);
       ++launches;
       // Arnoldi: classical Gram-Schmidt, second pass when needed
@@ -608,16 +623,29 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
           MX_CUDA(cudaStreamSynchronize(s));
           if (!W.h_flags[1]) break;
         }
-        dots(W, n, j + 1, pass == 0 ? 1 : 0, s);
-        orth_update(W, n, j + 1, s);
+        if (mixed) {
+          dots_mixed(W, n, j + 1, pass == 0 ? 1 : 0, s);
+          orth_update_df(W.nblk, n, nrhs, j + 1, reinterpret_cast<const float4*>(W.V.p), W.h2.p, W.hs.p, W.active.p,
+                         reinterpret_cast<float4*>(W.w.p), W.npart.p, s);
+        } else {
+          dots(W, n, j + 1, pass == 0 ? 1 : 0, s);
+          orth_update(W, n, j + 1, s);
+        }
         ProfScope ps(K_ARNOLDI_SMALL, s);
         MX_LAUNCH(k_arnoldi_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, pass, W.h2.p, W.npart.p, W.H.p, W.wnorm0.p,
                                           W.active.p, W.flags.p));
         MX_CHECK_LAUNCH();
         launches += 4;
       }
-      ProfScope ps(K_ARNOLDI_SMALL, s, 2, 32.0 * (double)nv, 2.0 * (double)nv);
-      MX_LAUNCH(k_normalize<<<gv, 256, 0, s>>>(nv, nrhs, j, m, W.H.p, W.active.p, W.w.p, W.V.p + (int64_t)(j + 1) * nv));
+      if (mixed) {
+        normalize_df(nv, nrhs, j, m, W.H.p, W.active.p, reinterpret_cast<const float4*>(W.w.p),
+                     reinterpret_cast<float4*>(W.V.p + (int64_t)(j + 1) * nv), s);
+      } else {
+        ProfScope ps(K_ARNOLDI_SMALL, s, 1, 32.0 * (double)nv, 2.0 * (double)nv);
+        MX_LAUNCH(k_normalize<<<gv, 256, 0, s>>>(nv, nrhs, j, m, W.H.p, W.active.p, W.w.p,
+                                                 W.V.p + (int64_t)(j + 1) * nv));
+      }
+      ProfScope ps(K_ARNOLDI_SMALL, s);
       MX_LAUNCH(k_givens<<<1, 32, 0, s>>>(nrhs, j, m, tol, W.bnorm.p, W.H.p, W.cs.p, W.sn.p, W.g.p, W.active.p, W.est.p,
                                 W.flags.p));
       MX_CHECK_LAUNCH();
@@ -672,8 +700,12 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     if (!any) break;
     ++restarts;
     MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
-    MX_LAUNCH(k_scale_v0<<<gv, 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p));
-    MX_CHECK_LAUNCH();
+    if (mixed) {
+      scale_v0_df(nv, nrhs, beta.p, W.active.p, W.r.p, reinterpret_cast<float4*>(W.V.p), s);
+    } else {
+      MX_LAUNCH(k_scale_v0<<<gv, 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p));
+      MX_CHECK_LAUNCH();
+    }
     ++launches;
   }
   MX_CUDA(cudaMemcpyAsync(x, W.x.p, nv * sizeof(double2), cudaMemcpyDeviceToDevice, s));

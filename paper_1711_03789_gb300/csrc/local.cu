@@ -486,6 +486,15 @@ struct SolveArgs {
 template <typename T2>
 __device__ inline T2 load_v(const void* v, int vtype, int64_t idx) {
   if (vtype == 0) return conv<T2>(reinterpret_cast<const double2*>(v)[idx]);
+  if (vtype == 3) {
+    if constexpr (std::is_same<T2, float2>::value) {
+      const float4 d = reinterpret_cast<const float4*>(v)[idx];
+      return make_float2(d.x, d.y);
+    } else {
+      const float4 d = reinterpret_cast<const float4*>(v)[idx];
+      return make_double2((double)d.x + (double)d.z, (double)d.y + (double)d.w);
+    }
+  }
   const float2 f = reinterpret_cast<const float2*>(v)[idx];
   return conv<T2>(make_double2(f.x, f.y));
 }

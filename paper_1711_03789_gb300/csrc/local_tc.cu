@@ -171,7 +171,7 @@ struct TcArgs {
   const int64_t* ptab;
   const float2* dinv;
   const int64_t* doff;
-  const void* v;  // [n][nrhs] c128 (vtype 0) or c64 (vtype 1)
+  const void* v;  // [n][nrhs] c128 (vtype 0), c64 (1) or complex double-float (3)
   int vtype;
   float2* out;    // [sum_local][nrhs]
   int32_t* status;
@@ -181,6 +181,10 @@ __device__ __forceinline__ float2 load_rhs(const void* v, int vtype, int64_t idx
   if (vtype == 0) {
     const double2 d = reinterpret_cast<const double2*>(v)[idx];
     return make_float2((float)d.x, (float)d.y);
+  }
+  if (vtype == 3) {  // complex double-float: the c64 rounding is the high half
+    const float4 d = reinterpret_cast<const float4*>(v)[idx];
+    return make_float2(d.x, d.y);
   }
   return reinterpret_cast<const float2*>(v)[idx];
 }

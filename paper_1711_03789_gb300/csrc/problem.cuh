@@ -106,6 +106,10 @@ struct Problem {
   // and a c64 copy of the factors for the mixed-precision coarse solve.
   CsrR R0, R0T;
   DevBuf<float> R0T_valf;  // FP32 copy of the R^0^T values (mixed-form scatter)
+  DevBuf<float> R0_valf;   // FP32 copy of the R^0 values (mixed-form coarse restriction)
+  // mixed-form operator coefficients a + i b = K - (k^2 + i xi_prob) M as double-floats
+  DevBuf<float4> A_coef_df;
+  double A_coef_xi = -1.0;
   int64_t n_c = 0;
   int coarse_band = 0;
   int64_t ld_c = 0;
@@ -156,7 +160,8 @@ void lu_update_tc(const BandBatch& B, float2* A, int k0, int max_span, int split
 template <typename T2>
 void invert_diag_blocks(const BandBatch& B, const T2* A, const int64_t* doff, T2* Dinv, int max_n, cudaStream_t s);
 // z_l = (A^l)^{-1} R^l v for every l, written at the subdomain positions of `loc`
-// (element type of the factors), v [nrhs][n] c128 or c64 (vtype 0: c128, 1: c64).
+// (element type of the factors), v [n][nrhs] c128 (vtype 0), c64 (1) or complex
+// double-float (3, whose c64 rounding is its high half).
 void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs);
 
 // ---- local_tc.cu --------------------------------------------------------------------
@@ -176,11 +181,24 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs);
 // y = A_{xi} x; x c128 or c64 [nrhs][n] (xtype 0/1), y c128
 void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int nrhs,
           cudaStream_t s);
-// z = B^{-1} v into z [nrhs][n] c128 (ztype 0) or c64 (ztype 1)
-void precond_apply(Problem& P, const double2* v, void* z, int ztype, int nrhs, int levels, double2* zc = nullptr);
+// z = B^{-1} v into z [nrhs][n] c128 (ztype 0) or c64 (ztype 1); v c128 (vtype 0) or
+// complex double-float (vtype 3, float4 {re_hi, im_hi, re_lo, im_lo})
+void precond_apply(Problem& P, const void* v, void* z, int ztype, int nrhs, int levels, double2* zc = nullptr,
+                   int vtype = 0);
 int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, int restart,
                 int max_it, mx_rhs_stats* stats);
 void free_workspace(Problem& P);
+
+// ---- krylov_df.cu: double-float Krylov kernels of the mixed form --------------------
+void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s);
+void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
+             const int32_t* active, double2* hpart, cudaStream_t s);
+void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float4* V, const double2* h, float4* hs,
+                    const int32_t* active, float4* w, double* npart, cudaStream_t s);
+void normalize_df(int64_t nv, int nrhs, int j, int m, const double2* H, const int32_t* active, const float4* w,
+                  float4* vnext, cudaStream_t s);
+void scale_v0_df(int64_t nv, int nrhs, const double* beta, const int32_t* active, const double2* r, float4* v0,
+                 cudaStream_t s);
 // h[i][r] = sum_x conj(V_i[x][r]) w[x][r], i < nvec; V [nvec][n][nrhs], w [n][nrhs] (device);
 // partials: nblk * nvec * nrhs entries of scratch; ones: nrhs flags equal to 1
 void batched_dots(const double2* V, const double2* w, int64_t n, int nrhs, int nvec, double2* h, double2* partials,

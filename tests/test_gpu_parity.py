@@ -313,3 +313,26 @@ def test_gmres_tensor_core_local_solves():
         err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
         assert err <= 1e-8, (r, err)
         assert st[r]["iterations"] <= 1.25 * ost[r][0], (st[r], ost[r])
+
+
+def test_mixed_gmres_tight_tolerance():
+    """The mixed form carries its Krylov basis, inner products and operator in double-float
+    arithmetic (about 48 bits): it still reaches a 1e-12 FP64 true residual, and its solution
+    agrees with the oracle's to the accuracy that residual implies."""
+    n, k, nrhs = 10, 6.0, 2
+    c, p = inputs.bump_batch(3, nrhs)
+    O = OracleProblem(n, k, k, k, 5, 1, coarse_m=5)
+    O.factor()
+    fo = O.load_vector(c, p, 0.1)
+    xo, ost = O.solve(fo, tol=1e-13, restart=0, max_it=300)
+    with _handle(n, k, k, k, 5, 1, cm=5, prec=mx.MX_MIXED) as P:
+        P.factor()
+        f = P.load_vector(c, p, 0.1)
+        x, st, rc = P.solve(f, tol=1e-12, restart=0, max_it=300)
+    assert rc == mx.MX_OK
+    for r in range(nrhs):
+        assert st[r]["converged"] and st[r]["rel_residual"] <= 1e-12
+        res = np.linalg.norm(fo[:, r] - O.A @ x[r]) / np.linalg.norm(fo[:, r])
+        assert res <= 1.05e-12, res
+        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
+        assert err <= 1e-9, err
