@@ -168,7 +168,7 @@ static Workspace& workspace(Problem& P, int nrhs, int m) {
   W->sn.alloc((size_t)m * nrhs);
   W->g.alloc((size_t)(m + 1) * nrhs);
   W->y.alloc((size_t)m * nrhs);
-  W->nblk = 2 * sm_count();
+  W->nblk = 4 * sm_count();
   W->hpart.alloc((size_t)W->nblk * (m + 2) * nrhs);
   W->h2.alloc((size_t)(m + 2) * nrhs);
   W->npart.alloc((size_t)W->nblk * nrhs);
@@ -505,11 +505,13 @@ static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t 
 
 // mixed form: double-float passes over the basis, FP64 reduction of the block partials
 static void dots_mixed(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s) {
-  dots_df(W.nblk, n, W.nrhs, nvec, with_norm, reinterpret_cast<const float4*>(W.V.p),
+  // one resident wave: the dots kernel holds 64 KB of accumulators per block (3 per SM)
+  const int nb = std::min(W.nblk, 3 * sm_count());
+  dots_df(nb, n, W.nrhs, nvec, with_norm, reinterpret_cast<const float4*>(W.V.p),
           reinterpret_cast<const float4*>(W.w.p), W.active.p, W.hpart.p, s);
   const int total = nvec + with_norm;
   ProfScope ps(K_ARNOLDI_SMALL, s);
-  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * W.nrhs, 128), 128, 0, s>>>(W.nblk, total, W.nrhs, W.hpart.p,
+  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * W.nrhs, 128), 128, 0, s>>>(nb, total, W.nrhs, W.hpart.p,
                                                                                    W.h2.p));
   MX_CHECK_LAUNCH();
 }

@@ -39,13 +39,20 @@ __global__ void k_spmv_df(int64_t rows, int nrhs, const int32_t* __restrict__ ro
   }
 }
 
-// hpart[blk][i][r] = sum_{x in block} conj(V_i[x][r]) w[x][r] (i == nvec: |w|^2 when
-// with_norm). Same work split as the FP64 kernel: warps over i, lanes (xl, r).
+// hpart[blk][i][r] = sum over the block's rows of conj(V_i[x][r]) w[x][r] (i == nvec:
+// |w|^2 when with_norm). Same row split as the update: lanes (xl, r), the block's warps
+// stride over its contiguous rows. A lane keeps DOTS_U steps of w in registers and streams
+// every basis vector against them, so V and w each leave HBM once (per chunk of DOTS_IC
+// basis vectors); the per-step sums are reduced across the row lanes and added into
+// warp-private compensated accumulators in shared memory (no block barrier in the loop).
+constexpr int DOTS_U = 8;
+constexpr int DOTS_IC = 32;
 template <int RP>
 __global__ void __launch_bounds__(256) k_dots_df(int64_t n, int nrhs, int nvec, int with_norm,
                                                  const float4* __restrict__ V, const float4* __restrict__ w,
                                                  const int32_t* __restrict__ active, double2* __restrict__ hpart) {
   constexpr int XL = 32 / RP;
+  extern __shared__ float4 acc_sm[];  // [8 warps][DOTS_IC][RP]: {re_s, re_e, im_s, im_e}
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = lane % RP, xl = lane / RP;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -53,26 +60,68 @@ __global__ void __launch_bounds__(256) k_dots_df(int64_t n, int nrhs, int nvec, 
   const int total = nvec + with_norm;
   const int64_t nv = n * nrhs;
   const bool on = r < nrhs && active[min(r, nrhs - 1)];
-  for (int i = warp; i < total; i += 8) {
-    const float4* Vi = (i < nvec) ? V + (int64_t)i * nv : w;
-    df::Acc are, aim;
-    if (on)
-      for (int64_t x = x0 + xl; x < x1; x += XL) {
-        const float4 a = Vi[x * nrhs + r];
-        const float4 c = w[x * nrhs + r];
-        // conj(a) c = (a.re c.re + a.im c.im) + i (a.re c.im - a.im c.re)
-        df::add_prod2(are, a.x, a.z, c.x, c.z);
-        df::add_prod2(are, a.y, a.w, c.y, c.w);
-        df::add_prod2(aim, a.x, a.z, c.y, c.w);
-        df::add_prod2(aim, -a.y, -a.w, c.x, c.z);
-      }
-    double sx = df::to_double(are), sy = df::to_double(aim);
+  float4* my = acc_sm + (size_t)warp * DOTS_IC * RP;
+  for (int ic = 0; ic < total; ic += DOTS_IC) {
+    const int icn = min(DOTS_IC, total - ic);
+    for (int t = lane; t < DOTS_IC * RP; t += 32) my[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    for (int64_t xb = x0 + warp * XL; xb < x1; xb += (int64_t)8 * XL * DOTS_U) {
+      float4 c[DOTS_U];
 #pragma unroll
-    for (int o = RP; o < 32; o <<= 1) {
-      sx += __shfl_xor_sync(0xffffffffu, sx, o);
-      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      for (int u = 0; u < DOTS_U; ++u) {
+        const int64_t x = xb + (int64_t)u * 8 * XL + xl;
+        c[u] = (on && x < x1) ? w[x * nrhs + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      for (int k = 0; k < icn; ++k) {
+        const int i = ic + k;
+        const float4* Vi = (i < nvec) ? V + (int64_t)i * nv : w;
+        df::Acc are, aim;
+#pragma unroll
+        for (int u = 0; u < DOTS_U; ++u) {
+          const int64_t x = xb + (int64_t)u * 8 * XL + xl;
+          const float4 a = (on && x < x1) ? Vi[x * nrhs + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+          // conj(a) c = (a.re c.re + a.im c.im) + i (a.re c.im - a.im c.re)
+          df::add_prod2(are, a.x, a.z, c[u].x, c[u].z);
+          df::add_prod2(are, a.y, a.w, c[u].y, c[u].w);
+          df::add_prod2(aim, a.x, a.z, c[u].y, c[u].w);
+          df::add_prod2(aim, -a.y, -a.w, c[u].x, c[u].z);
+        }
+        // fold the row lanes (same r) together, then into the warp's accumulator
+#pragma unroll
+        for (int o = RP; o < 32; o <<= 1) {
+          float s, e;
+          df::two_sum(are.s, __shfl_xor_sync(0xffffffffu, are.s, o), s, e);
+          are.e = __fadd_rn(__fadd_rn(are.e, __shfl_xor_sync(0xffffffffu, are.e, o)), e);
+          are.s = s;
+          df::two_sum(aim.s, __shfl_xor_sync(0xffffffffu, aim.s, o), s, e);
+          aim.e = __fadd_rn(__fadd_rn(aim.e, __shfl_xor_sync(0xffffffffu, aim.e, o)), e);
+          aim.s = s;
+        }
+        if (xl == 0) {
+          float4 m = my[k * RP + r];
+          float s, e;
+          df::two_sum(m.x, are.s, s, e);
+          m.y = __fadd_rn(m.y, __fadd_rn(are.e, e));
+          m.x = s;
+          df::two_sum(m.z, aim.s, s, e);
+          m.w = __fadd_rn(m.w, __fadd_rn(aim.e, e));
+          m.z = s;
+          my[k * RP + r] = m;
+        }
+      }
     }
-    if (xl == 0 && r < nrhs) hpart[((int64_t)blockIdx.x * total + i) * nrhs + r] = make_double2(sx, sy);
+    __syncthreads();
+    for (int t = threadIdx.x; t < icn * RP; t += blockDim.x) {
+      const int k = t / RP, rr = t % RP;
+      double sx = 0, sy = 0;
+      for (int wq = 0; wq < 8; ++wq) {
+        const float4 m = acc_sm[((size_t)wq * DOTS_IC + k) * RP + rr];
+        sx += (double)m.x + (double)m.y;
+        sy += (double)m.z + (double)m.w;
+      }
+      if (rr < nrhs) hpart[((int64_t)blockIdx.x * total + ic + k) * nrhs + rr] = make_double2(sx, sy);
+    }
+    __syncthreads();
   }
 }
 
@@ -99,6 +148,7 @@ __global__ void __launch_bounds__(256) k_orth_update_df(int64_t n, int nrhs, int
   if (on)
     for (int64_t x = x0 + warp * XL + xl; x < x1; x += 8 * XL) {
       df::Acc sre, sim;
+#pragma unroll 4
       for (int i = 0; i < nvec; ++i) {
         const float4 a = V[(int64_t)i * nv + x * nrhs + r];
         const float4 c = hs[i * nrhs + r];
@@ -171,7 +221,13 @@ void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s) {
 template <int RP>
 static void dots_rp(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
                     const int32_t* active, double2* hpart, cudaStream_t s) {
-  MX_LAUNCH(k_dots_df<RP><<<nblk, 256, 0, s>>>(n, nrhs, nvec, with_norm, V, w, active, hpart));
+  const size_t smem = (size_t)8 * DOTS_IC * RP * sizeof(float4);
+  static bool configured = false;
+  if (!configured) {
+    MX_CUDA(cudaFuncSetAttribute(k_dots_df<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  MX_LAUNCH(k_dots_df<RP><<<nblk, 256, smem, s>>>(n, nrhs, nvec, with_norm, V, w, active, hpart));
 }
 void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
              const int32_t* active, double2* hpart, cudaStream_t s) {
