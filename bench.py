@@ -46,6 +46,10 @@ WORKLOADS = {
     # 6^3 subdomains, 6^3 coarse mesh, 16 right-hand sides, xi = k^2
     "maxwell30_k15_2lvl": dict(n=30, k=15.0, xi_prob="k2", xi_prec="k2", core=5, overlap=1, coarse=6,
                                nrhs=16, restart=200, max_it=600, tol=1e-6, ref_iterations=35),
+    # profiling case for the coarse level of the 60^3 workload: the same 12^3 coarse mesh
+    # (10,836 coarse unknowns) under a 24^3 fine mesh, a few GB on the device
+    "maxwell24_k12_c12": dict(n=24, k=12.0, xi_prob="k2", xi_prec="k2", core=4, overlap=1, coarse=12,
+                              nrhs=16, restart=200, max_it=600, tol=1e-6, ref_iterations=30),
     # small case: 10^3 cells, k = xi = 6, 2^3 subdomains, unrestarted to 1e-10
     "maxwell10_k6_1lvl": dict(n=10, k=6.0, xi_prob=6.0, xi_prec="k", core=5, overlap=1, coarse=0,
                               nrhs=1, restart=0, max_it=300, tol=1e-10, ref_iterations=57),

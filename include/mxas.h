@@ -121,6 +121,11 @@ MX_API int mx_set_dense_local(mx_handle h, int dense);
  *   above 448 fall back to the CUDA cores. Changing it after mx_factor builds the panel
  *   images at the next solve. */
 #define MX_TUNE_LOCAL_TENSOR 4
+/*   MX_TUNE_COARSE_INVERSE: coarse solve of the MX_MIXED form; 1 (default) = mx_factor
+ *   forms the explicit c64 inverse of A^0 (n_c^2 complex entries, by band sweeps on the
+ *   identity) and every apply is one dense product, 0 = band triangular sweeps. Takes
+ *   effect at the next mx_factor. */
+#define MX_TUNE_COARSE_INVERSE 5
 MX_API int mx_set_tuning(mx_handle h, int key, int value);
 
 /* Message of the last error on the calling thread ("" if none). */

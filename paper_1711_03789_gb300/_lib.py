@@ -155,6 +155,7 @@ MX_TUNE_LOCAL_RHS_GROUP = 1
 MX_TUNE_LU_TENSOR = 2
 MX_TUNE_COARSE_BLOCKS = 3
 MX_TUNE_LOCAL_TENSOR = 4
+MX_TUNE_COARSE_INVERSE = 5
 
 
 def mx_set_tuning(h, key, value):

@@ -236,6 +236,9 @@ int mx_set_tuning(mx_handle h, int key, int value) {
     } else if (key == MX_TUNE_LU_TENSOR) {
       MX_REQUIRE(value == 0 || value == 1 || value == 3, MX_EINVAL, "LU tensor mode must be 0, 1 or 3");
       P.tune_lu_tc = value;
+    } else if (key == MX_TUNE_COARSE_INVERSE) {
+      MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "coarse inverse mode must be 0 or 1");
+      P.tune_coarse_inverse = value;
     } else if (key == MX_TUNE_LOCAL_TENSOR) {
       MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "local tensor mode must be 0 or 1");
       P.tune_local_tc = value;
@@ -320,7 +323,8 @@ int mx_info(mx_handle h, mx_problem_info* out) {
     out->sum_local = P.sum_local;
     out->n_coarse = P.coarse_m ? P.coarse.n_dof : 0;
     out->nnz_r0 = P.R0.nnz;
-    out->factor_bytes = (int64_t)P.factors.bytes() + (int64_t)P.A0.bytes() + (int64_t)P.A0f.bytes();
+    out->factor_bytes = (int64_t)P.factors.bytes() + (int64_t)P.dinv.bytes() + (int64_t)P.panels.bytes() +
+                        (int64_t)P.A0.bytes() + (int64_t)P.A0f.bytes() + (int64_t)P.A0inv.bytes();
     out->coarse_band = P.coarse_band;
     out->precision = P.precision;
   });

@@ -78,6 +78,12 @@ void factor_coarse(Problem& P) {
                     0);
     P.c_dinvf.alloc(nq * 2 * CB * CB);
     invert_diag_blocks<float2>(B, P.A0f.p, P.c_off.p, P.c_dinvf.p, (int)nc, s);
+    P.A0inv.reset();
+    if (P.tune_coarse_inverse) {
+      MX_CUDA(cudaStreamSynchronize(s));
+      P.A0inv.alloc((size_t)nc * nc);
+      coarse_inverse(P, P.A0inv.p);
+    }
   } else {
     band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU,
                      0);
@@ -210,13 +216,80 @@ static void sweep(Problem& P, T2* F, const T2* Dinv, T2* r, int nrhs) {
   MX_LAUNCH(MX_CUDA(cudaLaunchCooperativeKernel((void*)k_coarse_sweep<T2>, grid, 256, args, smem, P.stream)));
 }
 
+// Dense coarse apply with the explicit inverse (mixed form): part[ks][i][r] =
+// sum_{j in chunk ks} X[j][i] rc[j][r] (X symmetric, read along rows j). A thread owns two
+// adjacent columns i and up to 16 right-hand sides, so a block reads 4 KB of each row of
+// X contiguously and X leaves HBM once; the right-hand-side values are broadcast from L1.
+constexpr int CD_R = 16;
+__global__ void __launch_bounds__(256, 2) k_coarse_dense(int n, int nrhs, int jchunk, const float2* __restrict__ X,
+                                                         const float2* __restrict__ rc, float2* __restrict__ part) {
+  const int i0 = (blockIdx.x * 256 + threadIdx.x) * 2;
+  const int g0 = blockIdx.z * CD_R;
+  const int gn = min(CD_R, nrhs - g0);
+  const int j0 = blockIdx.y * jchunk, j1 = min(n, j0 + jchunk);
+  if (i0 >= n || gn <= 0) return;
+  const bool two = i0 + 1 < n;
+  float2 acc0[CD_R], acc1[CD_R];
+#pragma unroll
+  for (int g = 0; g < CD_R; ++g) acc0[g] = acc1[g] = make_float2(0.f, 0.f);
+  const bool vec = gn == CD_R && (nrhs % 2) == 0;
+#pragma unroll 2
+  for (int j = j0; j < j1; ++j) {
+    const float2* xr = X + (int64_t)j * n + i0;
+    const float2 a0 = xr[0];
+    const float2 a1 = two ? xr[1] : make_float2(0.f, 0.f);
+    const float2* r = rc + (int64_t)j * nrhs + g0;
+    if (vec) {
+      const float4* r4 = reinterpret_cast<const float4*>(r);
+#pragma unroll
+      for (int g = 0; g < CD_R / 2; ++g) {
+        const float4 q = r4[g];
+        cfma(acc0[2 * g], a0, make_float2(q.x, q.y));
+        cfma(acc1[2 * g], a1, make_float2(q.x, q.y));
+        cfma(acc0[2 * g + 1], a0, make_float2(q.z, q.w));
+        cfma(acc1[2 * g + 1], a1, make_float2(q.z, q.w));
+      }
+    } else {
+#pragma unroll
+      for (int g = 0; g < CD_R; ++g)
+        if (g < gn) {
+          const float2 q = r[g];
+          cfma(acc0[g], a0, q);
+          cfma(acc1[g], a1, q);
+        }
+    }
+  }
+  float2* o = part + ((int64_t)blockIdx.y * n + i0) * nrhs + g0;
+#pragma unroll
+  for (int g = 0; g < CD_R; ++g)
+    if (g < gn) {
+      o[g] = acc0[g];
+      if (two) o[nrhs + g] = acc1[g];
+    }
+}
+
+__global__ void k_coarse_sum(int64_t count, int ks, const float2* part, float2* y) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int k = 0; k < ks; ++k) {
+      const float2 v = part[(int64_t)k * count + t];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    y[t] = s;
+  }
+}
+
 void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
   cudaStream_t s = P.stream;
   const int64_t nc = P.n_c;
   // R^0 (12 B per entry) and one gather of v per entry (worst case), output once
   const double rb = 12.0 * P.R0.nnz + 4.0 * nc + 16.0 * (double)P.R0.nnz * nrhs + 16.0 * nc * nrhs;
   const bool mixed = P.precision == MX_MIXED;
-  float2* rf = reinterpret_cast<float2*>(yc);  // c64 view of the workspace (mixed)
+  const bool dense = mixed && P.A0inv.p;
+  float2* rf = reinterpret_cast<float2*>(yc);  // c64 view of the workspace (mixed): the coarse solution
+  // with the explicit inverse the restriction goes to the upper half of the workspace
+  float2* rin = dense ? rf + nc * nrhs : rf;
   {
     ProfScope ps(K_COARSE_RESTRICT, s, 1, rb, 4.0 * P.R0.nnz * nrhs);
     if (mixed) {
@@ -226,12 +299,30 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
         MX_CHECK_LAUNCH();
       }
       MX_LAUNCH(k_coarse_restrict<float2, float><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
-          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0_valf.p, v, vtype, rf));
+          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0_valf.p, v, vtype, rin));
     } else {
       MX_LAUNCH(k_coarse_restrict<double2, double><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
           nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, yc));
     }
     MX_CHECK_LAUNCH();
+  }
+  if (dense) {
+    // split the rows of X among ks chunks so that the grid fills about two blocks per SM
+    const int rows_blocks = (int)((nc + 511) / 512);
+    const int zgroups = (nrhs + CD_R - 1) / CD_R;
+    const int ks = std::max(1, std::min(64, (2 * sm_count() + rows_blocks * zgroups - 1) / (rows_blocks * zgroups)));
+    const int jchunk = (int)((nc + ks - 1) / ks);
+    P.c_part.ensure((size_t)ks * nc * nrhs);
+    {
+      ProfScope ps(K_COARSE_SWEEP, s, 1, 8.0 * (double)nc * nc + 8.0 * nc * nrhs * (1.0 + ks),
+                   8.0 * (double)nc * nc * nrhs);
+      MX_LAUNCH(k_coarse_dense<<<dim3(rows_blocks, ks, zgroups), 256, 0, s>>>((int)nc, nrhs, jchunk, P.A0inv.p, rin,
+                                                                             P.c_part.p));
+      MX_CHECK_LAUNCH();
+      MX_LAUNCH(k_coarse_sum<<<grid_for(nc * nrhs, 256), 256, 0, s>>>(nc * nrhs, ks, P.c_part.p, rf));
+      MX_CHECK_LAUNCH();
+    }
+    return;
   }
   if (mixed) sweep<float2>(P, P.A0f.p, P.c_dinvf.p, rf, nrhs);
   else sweep<double2>(P, P.A0.p, P.c_dinv.p, yc, nrhs);

@@ -332,7 +332,10 @@ int64_t local_factor_bytes(Problem& P) {
   int64_t blocks = 0;
   for (int l = 0; l < P.n_sub; ++l) blocks += (P.h_nl[l] + NB - 1) / NB;
   const int64_t panels = P.tune_local_tc ? panel_bytes_planned(P) : 0;
-  return esz * (P.h_mat_off[P.n_sub] + blocks * 2 * NB * NB) + panels;
+  // the explicit coarse inverse of the mixed form (the band factors of A^0 are smaller)
+  const int64_t cinv = (P.coarse_m && P.precision == MX_MIXED && P.tune_coarse_inverse)
+                           ? (int64_t)sizeof(float2) * P.coarse.n_dof * P.coarse.n_dof : 0;
+  return esz * (P.h_mat_off[P.n_sub] + blocks * 2 * NB * NB) + panels + cinv;
 }
 
 void extract_minors(Problem& P) {
@@ -499,6 +502,13 @@ __device__ inline T2 load_v(const void* v, int vtype, int64_t idx) {
   return conv<T2>(make_double2(f.x, f.y));
 }
 
+// right-hand side entry (row, column): from v, or the identity for vtype 2
+template <typename T2>
+__device__ inline T2 rhs_value(const SolveArgs& a, int64_t row, int col) {
+  if (a.vtype == 2) return row == col ? mk(decltype(T2::x)(1), decltype(T2::x)(0)) : czero<T2>();
+  return load_v<T2>(a.v, a.vtype, row * a.nrhs + col);
+}
+
 // x_blk = D r_blk for the kb x kb diagonal block (D = L_qq^{-1}, unit lower, or
 // D = U_qq^{-1}, upper; column-major NB x NB in global memory) on the window rows
 // c0..c0+kb-1, all G right-hand sides. Every thread of the block takes part (256 threads).
@@ -622,13 +632,20 @@ __global__ void __launch_bounds__(256, (sizeof(T2) == 8 && G < 16 ? 3 : 2)) k_lo
   const int win = a.win;
   const int tid = threadIdx.x, nt = blockDim.x;
 
-  // ---- forward sweep: L y = R^l v
-  for (int t = tid; t < win * G; t += nt) {
+  // ---- forward sweep: L y = R^l v. Identity right-hand sides (vtype 2, columns g0..)
+  // have y = 0 above row g0 (L is unit lower): the sweep starts at g0's block and writes
+  // those zeros directly.
+  const int cstart = a.vtype == 2 ? (g0 / NB) * NB : 0;
+  for (int t = tid; t < cstart * G; t += nt) {
     const int i = t / G, g = t % G;
-    W[t] = (i < n && g < gn) ? load_v<T2>(a.v, a.vtype, (int64_t)a.lists[pos0 + i] * a.nrhs + g0 + g) : czero<T2>();
+    if (g < gn) out[(pos0 + i) * a.nrhs + g0 + g] = czero<T2>();
+  }
+  for (int t = tid; t < win * G; t += nt) {
+    const int i = cstart + t / G, g = t % G;
+    W[(i % win) * G + g] = (i < n && g < gn) ? rhs_value<T2>(a, (int64_t)a.lists[pos0 + i], g0 + g) : czero<T2>();
   }
   __syncthreads();
-  for (int c0 = 0; c0 < n; c0 += NB) {
+  for (int c0 = cstart; c0 < n; c0 += NB) {
     const int c1 = min(c0 + NB, n);
     // diagonal block: x_blk = L_qq^{-1} r_blk with the precomputed inverse
     diag_apply<T2, G, false>(Dinv + doff + (int64_t)(c0 / NB) * 2 * NB * NB, c0, c1 - c0, W, win, Ds);
@@ -642,8 +659,7 @@ __global__ void __launch_bounds__(256, (sizeof(T2) == 8 && G < 16 ? 3 : 2)) k_lo
       const T2 y = W[(i % win) * G + g];
       if (g < gn) out[(pos0 + i) * a.nrhs + g0 + g] = y;
       const int inew = i + win;
-      if (inew < n)
-        W[(inew % win) * G + g] = (g < gn) ? load_v<T2>(a.v, a.vtype, (int64_t)a.lists[pos0 + inew] * a.nrhs + g0 + g) : czero<T2>();
+      if (inew < n) W[(inew % win) * G + g] = (g < gn) ? rhs_value<T2>(a, (int64_t)a.lists[pos0 + inew], g0 + g) : czero<T2>();
     }
     __syncthreads();
   }
@@ -689,6 +705,53 @@ static void launch_local_solve(const SolveArgs& a, int win, cudaStream_t s) {
   ProfScope ps(K_LOCAL_SOLVE, s, 1, a.alg_bytes, a.alg_flops);
   MX_LAUNCH(k_local_solve<T2, G><<<a.n_sub * groups, 256, smem, s>>>(a));
   MX_CHECK_LAUNCH();
+}
+
+__global__ void k_iota(int n, int32_t* p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+// X = (A^0)^{-1} (c64, row-major n_c x n_c) from the c64 band factors of the coarse
+// matrix: the band sweeps of the local solves on the identity columns, G at a time.
+void coarse_inverse(Problem& P, float2* X) {
+  const int nc = (int)P.n_c, b = P.coarse_band;
+  cudaStream_t s = P.stream;
+  DevBuf<int64_t> offs(2), moff(1), doff(1);
+  DevBuf<int32_t> lists(nc), nl(1), band(1), ld(1);
+  const int64_t h_offs[2] = {0, nc}, zero = 0;
+  const int32_t h_nl = nc, h_b = b, h_ld = (int32_t)P.ld_c;
+  MX_CUDA(cudaMemcpyAsync(offs.p, h_offs, 16, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemcpyAsync(moff.p, &zero, 8, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemcpyAsync(doff.p, &zero, 8, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemcpyAsync(nl.p, &h_nl, 4, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemcpyAsync(band.p, &h_b, 4, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemcpyAsync(ld.p, &h_ld, 4, cudaMemcpyHostToDevice, s));
+  MX_LAUNCH(k_iota<<<grid_for(nc, 256), 256, 0, s>>>(nc, lists.p));
+  MX_CHECK_LAUNCH();
+  SolveArgs a{};
+  a.n_sub = 1;
+  a.nrhs = nc;
+  a.n_dof = nc;
+  a.offsets = offs.p;
+  a.lists = lists.p;
+  a.nl = nl.p;
+  a.band = band.p;
+  a.ld = ld.p;
+  a.moff = moff.p;
+  a.factors = P.A0f.p;
+  a.dinv = P.c_dinvf.p;
+  a.doff = doff.p;
+  a.v = nullptr;
+  a.vtype = 2;
+  a.out = X;
+  a.win = std::max(NB, std::min(nc, b + NB));
+  MX_REQUIRE((size_t)a.win * 8 * sizeof(float2) <= 200 * 1024, MX_EINVAL, "coarse bandwidth too large for the inverse");
+  const double entries = (double)nc * (2.0 * b + 1.0) - (double)b * (b + 1.0);
+  a.alg_bytes = 8.0 * entries + 8.0 * (double)nc * nc;
+  a.alg_flops = 8.0 * entries * nc;
+  if ((size_t)a.win * 16 * sizeof(float2) <= 100 * 1024) launch_local_solve<float2, 16>(a, a.win, s);
+  else launch_local_solve<float2, 8>(a, a.win, s);
+  MX_CUDA(cudaStreamSynchronize(s));
 }
 
 void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs) {

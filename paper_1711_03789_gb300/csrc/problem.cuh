@@ -119,6 +119,11 @@ struct Problem {
   DevBuf<int64_t> c_off;
   DevBuf<double2> c_dinv; // inverted diagonal blocks of the coarse factors (FP64)
   DevBuf<float2> c_dinvf; // c64 copy (mixed)
+  // mixed form: the explicit c64 inverse of A^0 (row-major; A^0 is complex symmetric, so
+  // is its inverse), applied as one dense product instead of the band sweeps
+  int tune_coarse_inverse = 1;
+  DevBuf<float2> A0inv;
+  DevBuf<float2> c_part;  // split-K partial products of the dense coarse apply
   DevBuf<int32_t> status; // [4] device error words: 0 local pivot, 1 coarse pivot, 2 timeout
 
   Workspace* ws = nullptr;
@@ -163,6 +168,8 @@ void invert_diag_blocks(const BandBatch& B, const T2* A, const int64_t* doff, T2
 // (element type of the factors), v [n][nrhs] c128 (vtype 0), c64 (1) or complex
 // double-float (3, whose c64 rounding is its high half).
 void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs);
+// X = (A^0)^{-1} from the c64 coarse band factors (row-major n_c x n_c, c64)
+void coarse_inverse(Problem& P, float2* X);
 
 // ---- local_tc.cu --------------------------------------------------------------------
 // panel images of the c64 factors for the tensor-core solves (after factor_local)

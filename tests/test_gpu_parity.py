@@ -336,3 +336,26 @@ def test_mixed_gmres_tight_tolerance():
         assert res <= 1.05e-12, res
         err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
         assert err <= 1e-9, err
+
+
+@pytest.mark.parametrize("n,cm,nrhs", [(10, 5, 3), (20, 10, 16), (20, 4, 20)])
+def test_coarse_inverse_apply(n, cm, nrhs):
+    """Mixed-form coarse solve with the explicit c64 inverse of A^0 against the oracle's
+    pivoted sparse coarse solve (levels = 2: coarse correction only), and against the band
+    sweeps of the same c64 factors. The inverse carries the rounding of the c64 factors and
+    an FP32 dense product: bound 1e-4 relative, as for the other c64 preconditioner parts."""
+    k, xi = 6.0, 36.0
+    O = OracleProblem(n, k, 0.0, xi, 5, 1, coarse_m=cm)
+    O.factor()
+    v = inputs.random_complex(21, (nrhs, O.n_dof))
+    ze = O.dd.apply(v.T, levels=(0,)).T
+    out = {}
+    for mode in (1, 0):
+        with _handle(n, k, 0.0, xi, 5, 1, cm=cm, prec=mx.MX_MIXED) as P:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_COARSE_INVERSE, mode)
+            P.factor()
+            out[mode] = P.precond(v, levels=2)
+    for mode in (1, 0):
+        err = np.linalg.norm(out[mode] - ze) / np.linalg.norm(ze)
+        assert err <= 1e-4, (mode, err)
+    assert np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]) <= 1e-4
