@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(256, (sizeof(T2) == 8 && G < 16 ? 3 : 2)) k_lo
 }
 
 template <typename T2, int G>
-static void launch_local_solve(const SolveArgs& a, int win, cudaStream_t s) {
+static void launch_local_solve(const SolveArgs& a, int win, cudaStream_t s, int kid = K_LOCAL_SOLVE) {
   const size_t smem = (size_t)win * G * sizeof(T2);
   // dynamic window + the static diagonal-block tile must fit the 227 KB per-block limit
   MX_REQUIRE(smem + sizeof(T2) * NB * (NB + 1) <= 227 * 1024, MX_EINVAL, "local solve window exceeds shared memory");
@@ -702,7 +702,7 @@ static void launch_local_solve(const SolveArgs& a, int win, cudaStream_t s) {
     configured = smem;
   }
   const int groups = (a.nrhs + G - 1) / G;
-  ProfScope ps(K_LOCAL_SOLVE, s, 1, a.alg_bytes, a.alg_flops);
+  ProfScope ps(kid, s, 1, a.alg_bytes, a.alg_flops);
   MX_LAUNCH(k_local_solve<T2, G><<<a.n_sub * groups, 256, smem, s>>>(a));
   MX_CHECK_LAUNCH();
 }
@@ -749,8 +749,8 @@ void coarse_inverse(Problem& P, float2* X) {
   const double entries = (double)nc * (2.0 * b + 1.0) - (double)b * (b + 1.0);
   a.alg_bytes = 8.0 * entries + 8.0 * (double)nc * nc;
   a.alg_flops = 8.0 * entries * nc;
-  if ((size_t)a.win * 16 * sizeof(float2) <= 100 * 1024) launch_local_solve<float2, 16>(a, a.win, s);
-  else launch_local_solve<float2, 8>(a, a.win, s);
+  if ((size_t)a.win * 16 * sizeof(float2) <= 100 * 1024) launch_local_solve<float2, 16>(a, a.win, s, K_COARSE_INV);
+  else launch_local_solve<float2, 8>(a, a.win, s, K_COARSE_INV);
   MX_CUDA(cudaStreamSynchronize(s));
 }
 
