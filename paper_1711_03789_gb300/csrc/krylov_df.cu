@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_orth_update_df(int64_t n, int nrhs, int
   if (on)
     for (int64_t x = x0 + warp * XL + xl; x < x1; x += 8 * XL) {
       df::Acc sre, sim;
-#pragma unroll 4
+#pragma unroll 8
       for (int i = 0; i < nvec; ++i) {
         const float4 a = V[(int64_t)i * nv + x * nrhs + r];
         const float4 c = hs[i * nrhs + r];
