@@ -23,6 +23,10 @@ Readings:
     (R^0)_pj = w_p^H(midpoint_j) . (x_high - x_low).
   * local and coarse solves: sparse LU with partial pivoting (scipy SuperLU),
     like the paper's MUMPS direct solves (Sec. 6.1).
+  * partition of unity for the restricted variants (Sec. 6.3): D^l is the 0/1 diagonal
+    marking the DOFs that subdomain l owns, the owner being the core box that contains
+    the edge midpoint (per axis cell index floor(mid / core), clipped to the last box).
+    With overlap >= 1 the owner always holds the DOF, so sum_l (R^l)^T D^l R^l = I.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -122,6 +126,7 @@ class Schwarz:
 
     def __init__(self, mesh, A_prec, core, overlap, coarse_m=0, k=None, xi_prec=None):
         self.mesh = mesh
+        self.core, self.overlap = core, overlap
         self.boxes = subdomain_boxes(mesh.n, core, overlap)
         self.idx = [local_dofs(mesh, lo, hi) for lo, hi in self.boxes]
         self.A_prec = A_prec.tocsr()
@@ -133,6 +138,21 @@ class Schwarz:
             self.coarse_mesh = cm
             self.R0 = coarse_restriction(mesh, cm)
             self.A0 = fem.a_xi(Kc, Mc, k, xi_prec)  # Galerkin matrix on Q_H (Eq. 3.3, l = 0)
+
+    def owner(self):
+        """Owning subdomain of every DOF: the core box holding the edge midpoint."""
+        n, core = self.mesh.n, self.core
+        N = -(-n // core)
+        a = vertex_ijk(self.mesh.dof_edges[:, 0], n)
+        b = vertex_ijk(self.mesh.dof_edges[:, 1], n)
+        mid2 = a + b  # twice the midpoint, in vertex units
+        box = np.minimum(mid2 // (2 * core), N - 1)
+        return box[:, 0] + N * (box[:, 1] + N * box[:, 2])
+
+    def partition_of_unity(self):
+        """D^l of Sec. 6.3 as boolean masks over the local DOFs of every subdomain."""
+        own = self.owner()
+        return [own[i] == l for l, i in enumerate(self.idx)]
 
     def minor(self, l):
         """A^l = R^l A (R^l)^T (Eq. 3.3) as a sparse matrix."""
@@ -148,12 +168,42 @@ class Schwarz:
     def local_solve(self, l, r_l):
         return self.lus[l].solve(r_l)
 
-    def apply(self, v, levels=(1, 0)):
-        """z = sum_l (R^l)^T (A^l)^{-1} R^l v (Eq. 3.4). v [n] or [n, R]."""
+    def coarse_correction(self, v):
+        """G v with G = (R^0)^T (A^0)^{-1} R^0 (the coarse term of Eq. 3.4)."""
+        return self.R0.T @ self.coarse.solve(self.R0 @ v)
+
+    def ras1(self, v):
+        """One-level restricted additive Schwarz: sum_l (R^l)^T D^l (A^l)^{-1} R^l v (Sec. 6.3)."""
+        if not hasattr(self, "_pou"):
+            self._pou = self.partition_of_unity()
+        z = np.zeros_like(v, dtype=np.complex128)
+        for l, i in enumerate(self.idx):
+            zl = self.local_solve(l, v[i])
+            d = self._pou[l]
+            z[i[d]] += zl[d]
+        return z
+
+    def apply(self, v, levels=(1, 0), kind="as"):
+        """Preconditioner application, v [n] or [n, R].
+
+        kind "as": sum_l (R^l)^T (A^l)^{-1} R^l v over the levels given (Eq. 3.4);
+        "ras": the restricted local sum plus the coarse term if level 0 is given (Eq. RAS2);
+        "hras": (I - G A) B_RAS1^{-1} (I - A G) + G (Eq. HRAS);
+        "adef1": B_RAS1^{-1} (I - A G) + G (Eq. ADEF1ras); A = A_{xi_prec}."""
+        if kind in ("hras", "adef1"):
+            A = self.A_prec
+            gv = self.coarse_correction(v)
+            u = self.ras1(v - A @ gv)
+            if kind == "adef1":
+                return u + gv
+            return u - self.coarse_correction(A @ u) + gv
         z = np.zeros_like(v, dtype=np.complex128)
         if 1 in levels:
-            for l, i in enumerate(self.idx):
-                z[i] += self.local_solve(l, v[i])
+            if kind == "ras":
+                z += self.ras1(v)
+            else:
+                for l, i in enumerate(self.idx):
+                    z[i] += self.local_solve(l, v[i])
         if 0 in levels and self.coarse is not None:
-            z += self.R0.T @ self.coarse.solve(self.R0 @ v)
+            z += self.coarse_correction(v)
         return z

@@ -13,7 +13,8 @@ class Problem:
     """curl curl E - (k^2 + i xi_prob) E = F, PEC, preconditioned by AS built from
     A_{xi_prec} (Sec. 6.2: B^{-1}_{xi_prec} preconditions A_{xi_prob})."""
 
-    def __init__(self, n, k, xi_prob, xi_prec, core, overlap, coarse_m=0):
+    def __init__(self, n, k, xi_prob, xi_prec, core, overlap, coarse_m=0, kind="as"):
+        self.kind = kind  # "as" (Eq. 3.4), "ras" (Eq. RAS2), "hras" (Eq. HRAS), "adef1" (Eq. ADEF1ras)
         self.mesh = KuhnMesh(n)
         self.k, self.xi_prob, self.xi_prec = k, xi_prob, xi_prec
         self.K, self.M = fem.assemble_KM(self.mesh)
@@ -40,7 +41,7 @@ class Problem:
         xs, stats = [], []
         for r in range(B.shape[1]):
             hist = [] if history is not None else None
-            x, its, rel, ok = _gmres.gmres(lambda v: self.A @ v, self.dd.apply, B[:, r],
+            x, its, rel, ok = _gmres.gmres(lambda v: self.A @ v, lambda v: self.dd.apply(v, kind=self.kind), B[:, r],
                                            tol, restart, max_it, history=hist)
             if history is not None:
                 history.append(hist)

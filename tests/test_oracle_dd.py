@@ -6,6 +6,7 @@ single subdomain."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from oracle.mesh import KuhnMesh, count_interior_edges, vertex_ijk
 from oracle import fem, dd
@@ -159,3 +160,84 @@ def test_as_complex_symmetric():
     v = rng.standard_normal(m.n_dof) + 1j * rng.standard_normal(m.n_dof)
     a, b = u @ S.apply(v), v @ S.apply(u)
     assert abs(a - b) < 1e-10 * abs(a)
+
+
+# ---- restricted and hybrid variants (Sec. 6.3) ---------------------------------------
+def _rs(n=6, core=3, overlap=1, cm=3):
+    m = KuhnMesh(n)
+    K, M = fem.assemble_KM(m)
+    A = fem.a_xi(K, M, 3.0, 9.0)
+    S = dd.Schwarz(m, A, core, overlap, cm, 3.0, 9.0)
+    S.factor()
+    return m, A, S
+
+
+def test_partition_of_unity_sums_to_identity():
+    """sum_l (R^l)^T D^l R^l = I (the identity that defines D^l in Sec. 6.3): every DOF is
+    owned by exactly one subdomain, and that subdomain holds it."""
+    for n, core in ((6, 3), (7, 3), (10, 5)):
+        m = KuhnMesh(n)
+        K, M = fem.assemble_KM(m)
+        S = dd.Schwarz(m, fem.a_xi(K, M, 1.0, 1.0), core, 1)
+        pou = S.partition_of_unity()
+        total = np.zeros(m.n_dof)
+        for l, i in enumerate(S.idx):
+            total[i[pou[l]]] += 1
+        assert np.array_equal(total, np.ones(m.n_dof))
+
+
+def test_ras_single_subdomain_is_the_inverse():
+    """One subdomain covering the cube: D = I and RAS = AS = A^{-1}."""
+    m = KuhnMesh(4)
+    K, M = fem.assemble_KM(m)
+    A = fem.a_xi(K, M, 2.0, 4.0)
+    S = dd.Schwarz(m, A, 4, 1)
+    S.factor()
+    v = np.random.default_rng(0).standard_normal(m.n_dof) + 0j
+    z = S.apply(v, levels=(1,), kind="ras")
+    assert np.allclose(A @ z, v, atol=1e-11 * np.abs(v).max())
+
+
+def test_ras_restricts_each_local_solution_to_its_owned_dofs():
+    """RAS1 v equals the sum of the local solutions masked by D^l, written out DOF by DOF."""
+    m, A, S = _rs()
+    v = np.random.default_rng(1).standard_normal(m.n_dof) + 1j * np.random.default_rng(2).standard_normal(m.n_dof)
+    z = S.apply(v, levels=(1,), kind="ras")
+    own = S.owner()
+    ref = np.zeros(m.n_dof, dtype=complex)
+    for l, i in enumerate(S.idx):
+        zl = spla.spsolve(A[i][:, i].tocsc(), v[i])
+        for a, dof in enumerate(i):
+            if own[dof] == l:
+                ref[dof] = zl[a]
+    assert np.allclose(z, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def test_coarse_projection_and_hybrid_identities():
+    """With the Galerkin coarse matrix G A is a projection (G A G = G), and both hybrid
+    forms reproduce the coarse correction on its range: B^{-1} A G w = G w for Eq. HRAS and
+    Eq. ADEF1ras."""
+    m, A, S = _rs()
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal(m.n_dof) + 1j * rng.standard_normal(m.n_dof)
+    gw = S.coarse_correction(w)
+    scale = np.abs(gw).max()
+    assert np.allclose(S.coarse_correction(A @ gw), gw, atol=1e-10 * scale)
+    for kind in ("hras", "adef1"):
+        z = S.apply(A @ gw, kind=kind)
+        assert np.allclose(z, gw, atol=1e-9 * scale), kind
+
+
+def test_hybrid_forms_against_their_definitions():
+    """HRAS and ADEF1 recomposed from dense matrices of G, A and RAS1 (small mesh)."""
+    m, A, S = _rs(n=4, core=2, overlap=1, cm=2)
+    nd = m.n_dof
+    I = np.eye(nd)
+    R1 = np.column_stack([S.ras1(I[:, j].astype(complex)) for j in range(nd)])
+    G = np.column_stack([S.coarse_correction(I[:, j].astype(complex)) for j in range(nd)])
+    Ad = A.toarray()
+    v = np.random.default_rng(4).standard_normal(nd) + 0j
+    h = (I - G @ Ad) @ R1 @ (I - Ad @ G) + G
+    a = R1 @ (I - Ad @ G) + G
+    assert np.allclose(S.apply(v, kind="hras"), h @ v, atol=1e-10 * np.abs(h @ v).max())
+    assert np.allclose(S.apply(v, kind="adef1"), a @ v, atol=1e-10 * np.abs(a @ v).max())
