@@ -128,6 +128,22 @@ MX_API int mx_set_dense_local(mx_handle h, int dense);
 #define MX_TUNE_COARSE_INVERSE 5
 MX_API int mx_set_tuning(mx_handle h, int key, int value);
 
+/* Preconditioner variant (Sec. 6.3), applied by mx_solve and mx_precond:
+ *   MX_PREC_AS    additive Schwarz of Eq. 3.4 (default);
+ *   MX_PREC_RAS   restricted additive Schwarz (Eq. RAS2): every DOF takes the local solution
+ *                 of the subdomain that owns it (partition of unity D^l: the core box holding
+ *                 the edge midpoint), plus the coarse term when there is a coarse level;
+ *   MX_PREC_HRAS  hybrid two-level RAS (Eq. HRAS): (I - G A) B_RAS1^{-1} (I - A G) + G;
+ *   MX_PREC_ADEF1 adapted deflation (Eq. ADEF1ras): B_RAS1^{-1} (I - A G) + G;
+ * with G = (R^0)^T (A^0)^{-1} R^0 and A = A_{xi_prec}. The restricted variants need an
+ * overlap of at least one cell (MX_EINVAL otherwise); HRAS and ADEF1 need a coarse level
+ * and apply both levels whatever `levels` mx_precond gets. Takes effect at the next apply. */
+#define MX_PREC_AS 0
+#define MX_PREC_RAS 1
+#define MX_PREC_HRAS 2
+#define MX_PREC_ADEF1 3
+MX_API int mx_set_preconditioner(mx_handle h, int kind);
+
 /* Message of the last error on the calling thread ("" if none). */
 MX_API const char* mx_last_error(void);
 

@@ -62,6 +62,7 @@ _sig = {
     "mx_set_allocator": (C.c_int, [_ALLOC, _FREE, C.c_void_p]),
     "mx_set_dense_local": (C.c_int, [H, C.c_int]),
     "mx_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
+    "mx_set_preconditioner": (C.c_int, [H, C.c_int]),
     "mx_build_problem": (C.c_int, [C.POINTER(MeshDesc), C.c_double, C.c_double, C.c_double, C.POINTER(DdDesc),
                                    C.POINTER(CoarseDesc), C.c_int, C.POINTER(H)]),
     "mx_set_xi_prob": (C.c_int, [H, C.c_double]),
@@ -160,6 +161,13 @@ MX_TUNE_COARSE_INVERSE = 5
 
 def mx_set_tuning(h, key, value):
     _check(lib.mx_set_tuning(h, int(key), int(value)))
+
+
+MX_PREC_AS, MX_PREC_RAS, MX_PREC_HRAS, MX_PREC_ADEF1 = 0, 1, 2, 3
+
+
+def mx_set_preconditioner(h, kind):
+    _check(lib.mx_set_preconditioner(h, int(kind)))
 
 
 def mx_factor(h):

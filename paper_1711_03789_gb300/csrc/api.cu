@@ -248,6 +248,19 @@ int mx_set_tuning(mx_handle h, int key, int value) {
   });
 }
 
+int mx_set_preconditioner(mx_handle h, int kind) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    MX_REQUIRE(kind >= MX_PREC_AS && kind <= MX_PREC_ADEF1, MX_EINVAL, "unknown preconditioner variant");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    if (kind != MX_PREC_AS) {
+      MX_REQUIRE(P.overlap >= 1, MX_EINVAL, "the restricted variants need an overlap of at least one cell");
+      MX_REQUIRE(kind == MX_PREC_RAS || P.coarse_m > 0, MX_EINVAL, "HRAS and ADEF1 need a coarse level");
+    }
+    P.prec_kind = kind;
+  });
+}
+
 int mx_factor(mx_handle h) {
   return guard([&] {
     MX_REQUIRE(h, MX_EINVAL, "null handle");

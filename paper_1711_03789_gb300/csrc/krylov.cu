@@ -71,7 +71,8 @@ template <typename T2> __device__ inline T2 cvt2(double2 a) { return conv<T2>(a)
 // otherwise. The local solutions are summed in the fixed order of the inverse map.
 template <typename LT, typename CT, typename ZT, typename AT>
 __global__ void k_scatter(int64_t n, int nrhs, const int32_t* __restrict__ inv_ptr, const int32_t* __restrict__ inv_pos,
-                          const LT* __restrict__ loc, const int32_t* __restrict__ tptr, const int32_t* __restrict__ tcol,
+                          const int32_t* __restrict__ own, const LT* __restrict__ loc,
+                          const int32_t* __restrict__ tptr, const int32_t* __restrict__ tcol,
                           const AT* __restrict__ tval, const CT* __restrict__ y0, int use_local, ZT* __restrict__ z,
                           double2* __restrict__ zc) {
   using A2 = typename cplx<AT>::type;
@@ -80,7 +81,9 @@ __global__ void k_scatter(int64_t n, int nrhs, const int32_t* __restrict__ inv_p
     const int r = (int)(t % nrhs);
     const int64_t i = t / nrhs;
     A2 acc = czero<A2>();
-    if (use_local)
+    if (use_local && own) {
+      acc = cvt2<A2>(loc[(int64_t)own[i] * nrhs + r]);  // restricted: the owner's solution only
+    } else if (use_local)
       for (int32_t q = inv_ptr[i]; q < inv_ptr[i + 1]; ++q) {
         const int32_t pos = inv_pos[q];
         if (pos < 0) continue;
@@ -114,6 +117,7 @@ struct Workspace {
   DevBuf<double2> w, b, x, r;     // [n][nrhs]
   DevBuf<double2> zc;             // [n][nrhs] current z_j promoted to c128 (unused by the solver)
   DevBuf<float4> hs;              // [m+2][nrhs] h of the current pass as double-floats (mixed)
+  DevBuf<double2> pv;             // 3 [n][nrhs] work vectors of the hybrid preconditioners
   DevBuf<unsigned char> loc;      // [sum_local][nrhs] local solutions
   DevBuf<double2> yc;             // [n_c][nrhs]
   DevBuf<double2> H;              // [m][m+1][nrhs]   column j, row i
@@ -182,26 +186,25 @@ static Workspace& workspace(Problem& P, int nrhs, int m) {
   return *W;
 }
 
-void precond_apply(Problem& P, const void* v, void* z, int ztype, int nrhs, int levels, double2* zc, int vtype) {
-  Workspace& W = workspace(P, nrhs, P.ws ? std::max(P.ws->m, 1) : 1);
+// z = sum of the local solutions held in W.loc (all of them, or the owner's only when `own`
+// is given) + (R^0)^T y0 when `coarse` (y0 in W.yc); z in ztype, zc the promoted copy.
+static void scatter(Problem& P, Workspace& W, void* z, int ztype, int nrhs, bool local, bool coarse,
+                    const int32_t* own, double2* zc) {
   cudaStream_t s = P.stream;
   const bool mixed = P.precision == MX_MIXED;
-  if (levels & 1) local_solves(P, v, vtype, W.loc.p, nrhs);
-  const bool coarse = (levels & 2) && P.coarse_m;
-  if (coarse) coarse_solve(P, v, vtype, W.yc.p, nrhs);
   const int64_t work = P.fine.n_dof * nrhs;
   const int32_t* tp = coarse ? P.R0T.rowptr.p : nullptr;
   const unsigned grid = grid_for(work, 256, 152LL * 32);
   const double lsz = mixed ? 8.0 : 16.0, zb = ztype == 0 ? 16.0 : 8.0;
   ProfScope ps(K_SCATTER, s, 1,
-               (levels & 1 ? (lsz * nrhs + 4.0) * (double)P.sum_local : 0.0) + 4.0 * (P.fine.n_dof + 1) +
+               (local ? (lsz * nrhs + 4.0) * (double)P.sum_local : 0.0) + 4.0 * (P.fine.n_dof + 1) +
                    (coarse ? 12.0 * P.R0T.nnz + 4.0 * P.fine.n_dof + lsz * (double)P.n_c * nrhs : 0.0) +
                    zb * (double)work,
-               (levels & 1 ? 2.0 * (double)P.sum_local * nrhs : 0.0) + (coarse ? 4.0 * (double)P.R0T.nnz * nrhs : 0.0));
+               (local ? 2.0 * (double)P.sum_local * nrhs : 0.0) + (coarse ? 4.0 * (double)P.R0T.nnz * nrhs : 0.0));
 #define MX_SCATTER(LT, CT, ZT, AT, TV)                                                                        \
-  MX_LAUNCH(k_scatter<LT, CT, ZT, AT><<<grid, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p,            \
+  MX_LAUNCH(k_scatter<LT, CT, ZT, AT><<<grid, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p, own,       \
                                                            (const LT*)W.loc.p, tp, P.R0T.col.p, TV,              \
-                                                           (const CT*)W.yc.p, levels & 1, (ZT*)z, zc))
+                                                           (const CT*)W.yc.p, local ? 1 : 0, (ZT*)z, zc))
   if (mixed) {
     if (coarse && P.R0T_valf.n != (size_t)P.R0T.nnz) {
       P.R0T_valf.alloc(P.R0T.nnz);
@@ -216,6 +219,89 @@ void precond_apply(Problem& P, const void* v, void* z, int ztype, int nrhs, int 
   }
 #undef MX_SCATTER
   MX_CHECK_LAUNCH();
+}
+
+// t = v - t (v c128 or complex double-float)
+__global__ void k_sub_from(int64_t nv, const void* v, int vtype, double2* t) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 a;
+    if (vtype == 3) {
+      const float4 d = reinterpret_cast<const float4*>(v)[i];
+      a = make_double2((double)d.x + (double)d.z, (double)d.y + (double)d.w);
+    } else {
+      a = reinterpret_cast<const double2*>(v)[i];
+    }
+    t[i] = make_double2(a.x - t[i].x, a.y - t[i].y);
+  }
+}
+
+// z = u + g in ztype; zc the promoted copy of the stored z
+template <typename ZT, typename UT>
+__global__ void k_add_out(int64_t nv, const UT* u, const UT* g, ZT* z, double2* zc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = to_c128(u[i]), b = to_c128(g[i]);
+    const ZT zv = conv<ZT>(make_double2(a.x + b.x, a.y + b.y));
+    z[i] = zv;
+    if (zc) zc[i] = to_c128(zv);
+  }
+}
+
+void precond_apply(Problem& P, const void* v, void* z, int ztype, int nrhs, int levels, double2* zc, int vtype) {
+  Workspace& W = workspace(P, nrhs, P.ws ? std::max(P.ws->m, 1) : 1);
+  cudaStream_t s = P.stream;
+  const int kind = P.prec_kind;
+  const int32_t* own = nullptr;
+  if (kind != MX_PREC_AS) {
+    build_owner(P);
+    own = P.own_pos.p;
+  }
+  if ((kind == MX_PREC_HRAS || kind == MX_PREC_ADEF1) && P.coarse_m) {
+    // two-level hybrid forms (Sec. 6.3): G v, t = v - A G v, u = B_RAS1^{-1} t, then
+    // ADEF1: z = u + G v;  HRAS: z = u + G (v - A u)  (= (I - G A) u + G v)
+    // mixed form: G v and u are c64 (their parts are), so the products with A_{xi_prec}
+    // run on the double-float operator; FP64 form: c128 and the FP64 operator
+    const bool mixed = P.precision == MX_MIXED;
+    const int64_t nv = P.fine.n_dof * nrhs;
+    W.pv.ensure((size_t)3 * nv);
+    double2* gv = W.pv.p;
+    double2* t = W.pv.p + nv;
+    double2* u = W.pv.p + 2 * nv;
+    const int ut = mixed ? 1 : 0;  // storage type of gv and u
+    auto apply_a = [&](const double2* x, double2* y) {
+      if (mixed) spmv_df_c128(P, P.xi_prec, reinterpret_cast<const float2*>(x), y, nrhs, s);
+      else spmv(P, P.xi_prec, x, 0, y, nrhs, s);
+    };
+    const unsigned gv_grid = grid_for(nv, 256);
+    coarse_solve(P, v, vtype, W.yc.p, nrhs);
+    scatter(P, W, gv, ut, nrhs, false, true, nullptr, nullptr);
+    apply_a(gv, t);
+    MX_LAUNCH(k_sub_from<<<gv_grid, 256, 0, s>>>(nv, v, vtype, t));
+    MX_CHECK_LAUNCH();
+    local_solves(P, t, 0, W.loc.p, nrhs);
+    scatter(P, W, u, ut, nrhs, true, false, own, nullptr);
+    if (kind == MX_PREC_HRAS) {
+      apply_a(u, t);
+      MX_LAUNCH(k_sub_from<<<gv_grid, 256, 0, s>>>(nv, v, vtype, t));
+      MX_CHECK_LAUNCH();
+      coarse_solve(P, t, 0, W.yc.p, nrhs);
+      scatter(P, W, gv, ut, nrhs, false, true, nullptr, nullptr);
+    }
+    if (mixed) {
+      const float2* uf = reinterpret_cast<const float2*>(u);
+      const float2* gf = reinterpret_cast<const float2*>(gv);
+      if (ztype == 0) MX_LAUNCH(k_add_out<double2, float2><<<gv_grid, 256, 0, s>>>(nv, uf, gf, (double2*)z, zc));
+      else MX_LAUNCH(k_add_out<float2, float2><<<gv_grid, 256, 0, s>>>(nv, uf, gf, (float2*)z, zc));
+    } else {
+      if (ztype == 0) MX_LAUNCH(k_add_out<double2, double2><<<gv_grid, 256, 0, s>>>(nv, u, gv, (double2*)z, zc));
+      else MX_LAUNCH(k_add_out<float2, double2><<<gv_grid, 256, 0, s>>>(nv, u, gv, (float2*)z, zc));
+    }
+    MX_CHECK_LAUNCH();
+    return;
+  }
+  if (levels & 1) local_solves(P, v, vtype, W.loc.p, nrhs);
+  const bool coarse = (levels & 2) && P.coarse_m;
+  if (coarse) coarse_solve(P, v, vtype, W.yc.p, nrhs);
+  scatter(P, W, z, ztype, nrhs, (levels & 1) != 0, coarse, own, zc);
 }
 
 // ---- Arnoldi kernels ----------------------------------------------------------------

@@ -200,21 +200,59 @@ __global__ void k_scale_v0_df(int64_t nv, int nrhs, const double* beta, const in
   }
 }
 
+// y = A z with y in FP64 (hi + lo of the double-float sums), z c64
+__global__ void k_spmv_df_c128(int64_t rows, int nrhs, const int32_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ col, const float4* __restrict__ coef,
+                               const float2* __restrict__ z, double2* __restrict__ y) {
+  const int64_t work = rows * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nrhs);
+    const int64_t i = t / nrhs;
+    df::Acc re, im;
+    const int32_t e1 = rowptr[i + 1];
+    for (int32_t e = rowptr[i]; e < e1; ++e) {
+      const float2 x = z[(int64_t)col[e] * nrhs + r];
+      const float4 c = coef[e];
+      df::add_prod(re, c.x, c.y, x.x);
+      df::add_prod(re, c.z, c.w, -x.y);
+      df::add_prod(im, c.x, c.y, x.y);
+      df::add_prod(im, c.z, c.w, x.x);
+    }
+    y[t] = make_double2(df::to_double(re), df::to_double(im));
+  }
+}
+
+// double-float coefficients of A_xi, cached per value of xi (slot 0: xi_prob, 1: xi_prec)
+static const float4* coef_df(Problem& P, double xi, int slot, cudaStream_t s) {
+  if (P.A_coef_df[slot].n != (size_t)P.A.nnz || P.A_coef_xi[slot] != xi) {
+    P.A_coef_df[slot].alloc(P.A.nnz);
+    MX_LAUNCH(k_coef_df<<<grid_for(P.A.nnz, 256), 256, 0, s>>>(P.A.nnz, P.A.K.p, P.A.M.p, P.k * P.k, xi,
+                                                              P.A_coef_df[slot].p));
+    MX_CHECK_LAUNCH();
+    P.A_coef_xi[slot] = xi;
+  }
+  return P.A_coef_df[slot].p;
+}
+
+void spmv_df_c128(Problem& P, double xi, const float2* z, double2* y, int nrhs, cudaStream_t s) {
+  const float4* coef = coef_df(P, xi, xi == P.xi_prob ? 0 : 1, s);
+  const int64_t work = P.A.rows * nrhs;
+  ProfScope ps(K_SPMV, s, 1, 20.0 * P.A.nnz + 4.0 * (P.A.rows + 1) + 24.0 * (double)P.A.rows * nrhs,
+               8.0 * (double)P.A.nnz * nrhs);
+  MX_LAUNCH(k_spmv_df_c128<<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p,
+                                                                           coef, z, y));
+  MX_CHECK_LAUNCH();
+}
+
 // ---- host launchers ----------------------------------------------------------------------
 void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s) {
-  if (P.A_coef_df.n != (size_t)P.A.nnz || P.A_coef_xi != P.xi_prob) {
-    P.A_coef_df.alloc(P.A.nnz);
-    MX_LAUNCH(k_coef_df<<<grid_for(P.A.nnz, 256), 256, 0, s>>>(P.A.nnz, P.A.K.p, P.A.M.p, P.k * P.k, P.xi_prob,
-                                                              P.A_coef_df.p));
-    MX_CHECK_LAUNCH();
-    P.A_coef_xi = P.xi_prob;
-  }
+  const float4* coef = coef_df(P, P.xi_prob, 0, s);
   const int64_t work = P.A.rows * nrhs;
   // coefficients (16 B) and column indices once, z (c64) once, w (16 B) once
   ProfScope ps(K_SPMV, s, 1, 20.0 * P.A.nnz + 4.0 * (P.A.rows + 1) + 24.0 * (double)P.A.rows * nrhs,
                8.0 * (double)P.A.nnz * nrhs);
   MX_LAUNCH(k_spmv_df<<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p,
-                                                                      P.A_coef_df.p, z, w));
+                                                                      coef, z, w));
   MX_CHECK_LAUNCH();
 }
 

@@ -220,6 +220,49 @@ __global__ void k_inverse_map(InvArgs a) {
   }
 }
 
+// Owner of every DOF for the restricted variants (Sec. 6.3): the core box holding the
+// edge midpoint (twice the midpoint is 2c + D in vertex units), and the position of the DOF
+// in the owner's list (-1 if the owner does not hold it, which overlap >= 1 rules out).
+__global__ void k_owner_pos(int n, int core, int N, int64_t n_dof, const int32_t* dof_key, const int64_t* offsets,
+                            const int32_t* nl, const int32_t* lists, int32_t* own_pos, int32_t* missing) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_dof; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t key = dof_key[i];
+    const int d = key % 7;
+    const int64_t v = key / 7;
+    const int c[3] = {(int)(v % (n + 1)), (int)((v / (n + 1)) % (n + 1)), (int)(v / ((int64_t)(n + 1) * (n + 1)))};
+    int b[3];
+    for (int ax = 0; ax < 3; ++ax) b[ax] = min((2 * c[ax] + c_dirs[d][ax]) / (2 * core), N - 1);
+    const int l = b[0] + N * (b[1] + N * b[2]);
+    const int32_t* L = lists + offsets[l];
+    int lo = 0, hi = nl[l] - 1, at = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int32_t val = L[mid];
+      if (val == (int32_t)i) { at = mid; break; }
+      if (val < (int32_t)i) lo = mid + 1; else hi = mid - 1;
+    }
+    own_pos[i] = at >= 0 ? (int32_t)(offsets[l] + at) : -1;
+    if (at < 0) atomicAdd(missing, 1);
+  }
+}
+
+void build_owner(Problem& P) {
+  if (P.own_pos.p) return;
+  MX_REQUIRE(P.overlap >= 1, MX_EINVAL, "the restricted variants need an overlap of at least one cell");
+  cudaStream_t s = P.stream;
+  const int64_t nd = P.fine.n_dof;
+  DevBuf<int32_t> own(nd), missing(1);
+  MX_CUDA(cudaMemsetAsync(missing.p, 0, 4, s));
+  MX_LAUNCH(k_owner_pos<<<grid_for(nd, 256), 256, 0, s>>>(P.n, P.core, P.n_per_axis, nd, P.fine.dof_key.p, P.offsets.p,
+                                                         P.nl.p, P.lists.p, own.p, missing.p));
+  MX_CHECK_LAUNCH();
+  int32_t h_missing = 0;
+  MX_CUDA(cudaMemcpyAsync(&h_missing, missing.p, 4, cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  MX_REQUIRE(h_missing == 0, MX_EINVAL, "a DOF is not held by the subdomain that owns it");
+  P.own_pos = std::move(own);
+}
+
 void build_subdomains(Problem& P) {
   cudaStream_t s = P.stream;
   const int n = P.n;

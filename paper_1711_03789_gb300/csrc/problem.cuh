@@ -74,6 +74,10 @@ struct Problem {
   DevBuf<int32_t> lists;           // [sum_local]
   DevBuf<int32_t> inv_ptr;         // [n_dof + 1]
   DevBuf<int32_t> inv_pos;         // [sum_local]
+  // preconditioner variant (Sec. 6.3): MX_PREC_AS, MX_PREC_RAS, MX_PREC_HRAS, MX_PREC_ADEF1;
+  // the restricted ones scatter only the owner's local solution of every DOF
+  int prec_kind = MX_PREC_AS;
+  DevBuf<int32_t> own_pos;         // [n_dof] position of the DOF in its owner's list
 
   // local factors: band storage (see local.cu), element type float2 (mixed) or double2
   // (plain), matrix l at mat_off[l] elements.
@@ -108,8 +112,8 @@ struct Problem {
   DevBuf<float> R0T_valf;  // FP32 copy of the R^0^T values (mixed-form scatter)
   DevBuf<float> R0_valf;   // FP32 copy of the R^0 values (mixed-form coarse restriction)
   // mixed-form operator coefficients a + i b = K - (k^2 + i xi_prob) M as double-floats
-  DevBuf<float4> A_coef_df;
-  double A_coef_xi = -1.0;
+  DevBuf<float4> A_coef_df[2];     // slot 0: xi_prob (operator), 1: xi_prec (hybrid preconditioners)
+  double A_coef_xi[2] = {-1.0, -1.0};
   int64_t n_c = 0;
   int coarse_band = 0;
   int64_t ld_c = 0;
@@ -147,6 +151,8 @@ void transpose_to_user(const double2* in, double2* user, int64_t n, int nrhs, cu
 // ---- mesh.cu ------------------------------------------------------------------------
 void build_mesh(MeshDev& m, int n, cudaStream_t s);
 void build_subdomains(Problem& P);
+// owner positions of the partition of unity of the restricted variants (once)
+void build_owner(Problem& P);
 
 // ---- assemble.cu --------------------------------------------------------------------
 void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s);
@@ -198,6 +204,8 @@ void free_workspace(Problem& P);
 
 // ---- krylov_df.cu: double-float Krylov kernels of the mixed form --------------------
 void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s);
+// y = A_xi z, z c64, y c128 (double-float accumulation)
+void spmv_df_c128(Problem& P, double xi, const float2* z, double2* y, int nrhs, cudaStream_t s);
 void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
              const int32_t* active, double2* hpart, cudaStream_t s);
 void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float4* V, const double2* h, float4* hs,

@@ -359,3 +359,53 @@ def test_coarse_inverse_apply(n, cm, nrhs):
         err = np.linalg.norm(out[mode] - ze) / np.linalg.norm(ze)
         assert err <= 1e-4, (mode, err)
     assert np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", [mx.MX_PLAIN_FP64, mx.MX_MIXED])
+@pytest.mark.parametrize("kind,name", [(mx.MX_PREC_RAS, "ras"), (mx.MX_PREC_HRAS, "hras"),
+                                       (mx.MX_PREC_ADEF1, "adef1")])
+def test_restricted_and_hybrid_preconditioners(prec, kind, name):
+    """RAS (one and two level), HRAS and ADEF1-RAS (Sec. 6.3) against the oracle's
+    definitions; bounds as for the additive form (FP64: rounding; mixed: c64 local and
+    coarse solves, CUDA-core local solves here)."""
+    n, k, xi = 10, 5.0, 25.0
+    O = OracleProblem(n, k, 0.0, xi, 5, 1, coarse_m=5)
+    O.factor()
+    nrhs = 3
+    v = inputs.random_complex(31, (nrhs, O.n_dof))
+    with _handle(n, k, 0.0, xi, 5, 1, cm=5, prec=prec) as P:
+        mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, 0)
+        P.factor()
+        mx.mx_set_preconditioner(P.h, kind)
+        z = P.precond(v, levels=3)
+        z1 = P.precond(v, levels=1) if kind == mx.MX_PREC_RAS else None
+    tol = 1e-11 if prec == mx.MX_PLAIN_FP64 else 1e-4
+    ze = O.dd.apply(v.T, levels=(1, 0), kind=name).T
+    assert np.linalg.norm(z - ze) / np.linalg.norm(ze) <= tol
+    if z1 is not None:
+        z1e = O.dd.apply(v.T, levels=(1,), kind="ras").T
+        assert np.linalg.norm(z1 - z1e) / np.linalg.norm(z1e) <= tol
+
+
+@pytest.mark.parametrize("kind,name", [(mx.MX_PREC_RAS, "ras"), (mx.MX_PREC_HRAS, "hras"),
+                                       (mx.MX_PREC_ADEF1, "adef1")])
+def test_gmres_with_restricted_and_hybrid_preconditioners(kind, name):
+    """Right-preconditioned GMRES with each variant reaches the oracle's solution (FP64 form,
+    1e-10) in the same number of iterations (+-1)."""
+    n, k, nrhs = 10, 6.0, 2
+    c, p = inputs.bump_batch(5, nrhs)
+    O = OracleProblem(n, k, k, k, 5, 1, coarse_m=5, kind=name)
+    O.factor()
+    fo = O.load_vector(c, p, 0.1)
+    xo, ost = O.solve(fo, tol=1e-10, restart=0, max_it=300)
+    with _handle(n, k, k, k, 5, 1, cm=5, prec=mx.MX_PLAIN_FP64) as P:
+        P.factor()
+        mx.mx_set_preconditioner(P.h, kind)
+        f = P.load_vector(c, p, 0.1)
+        x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
+    assert rc == mx.MX_OK
+    for r in range(nrhs):
+        assert st[r]["converged"]
+        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
+        assert err <= 1e-8, (r, err)
+        assert abs(st[r]["iterations"] - ost[r][0]) <= 1, (st[r], ost[r])
