@@ -14,6 +14,10 @@ Readings:
     residual b - A x is recomputed;
   * Arnoldi by modified Gram-Schmidt; the small least-squares problem by complex
     Givens rotations (Saad, Iterative Methods, Alg. 6.9 and Prop. 6.9).
+  * weighted GMRES (Sec. 5.2): with a Hermitian positive definite weight D, the Arnoldi
+    process runs in <v, w>_D = w^* D v and the residual is minimised in ||.||_D; the
+    stopping test is then on ||b - A x||_D / ||b||_D. The paper's weight is
+    D_k = K + k^2 M, the matrix of the (.,.)_{curl,k} inner product (Eq. 2.3, Eq. 5.1).
 """
 import numpy as np
 
@@ -30,21 +34,30 @@ def givens(a, b):
     return c, s
 
 
-def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=None):
+def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=None, weight=None):
     """Solve A x = b with right preconditioner B^{-1}.
 
-    matvec(v) = A v, precond(v) = B^{-1} v for 1-D complex vectors.
+    matvec(v) = A v, precond(v) = B^{-1} v for 1-D complex vectors; weight(v) = D v for
+    weighted GMRES (None: the Euclidean inner product).
     Returns (x, iterations, final relative true residual, converged)."""
     b = np.asarray(b, dtype=np.complex128)
     n = b.shape[0]
     x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
-    bnorm = np.linalg.norm(b)
+    D = weight if weight is not None else (lambda v: v)
+
+    def dot(u, v):  # <v, u>_D = u^* D v (first argument conjugated, like np.vdot)
+        return np.vdot(u, D(v))
+
+    def norm(v):
+        return float(np.sqrt(max(dot(v, v).real, 0.0)))
+
+    bnorm = norm(b)
     if bnorm == 0.0:
         return np.zeros(n, dtype=np.complex128), 0, 0.0, True
     m = restart if restart > 0 else max_it
     its = 0
     r = b - matvec(x) if np.any(x) else b.copy()
-    beta = np.linalg.norm(r)
+    beta = norm(r)
     if beta / bnorm <= tol:
         return x, 0, beta / bnorm, True
     while True:
@@ -60,9 +73,9 @@ def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=
         for j in range(m):
             w = matvec(precond(V[j]))
             for i in range(j + 1):  # modified Gram-Schmidt
-                H[i, j] = np.vdot(V[i], w)
+                H[i, j] = dot(V[i], w)
                 w = w - H[i, j] * V[i]
-            H[j + 1, j] = np.linalg.norm(w)
+            H[j + 1, j] = norm(w)
             if H[j + 1, j] != 0:
                 V[j + 1] = w / H[j + 1, j]
             for i in range(j):  # previous rotations on the new column
@@ -85,7 +98,7 @@ def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=
         y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])  # upper-triangular back substitution
         x = x + precond(V[:k].T @ y)
         r = b - matvec(x)
-        beta = np.linalg.norm(r)
+        beta = norm(r)
         rel = beta / bnorm
         if rel <= tol:
             return x, its, rel, True

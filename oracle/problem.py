@@ -33,8 +33,11 @@ class Problem:
         """f for bump parameters centres [R, B, 3], pol [R, B, 3]; returns [n, R]."""
         return fem.load_vector(self.mesh, fem.bump_field(centres, pol, width), q)
 
-    def solve(self, rhs, tol=1e-6, restart=0, max_it=200, history=None):
-        """rhs [n] or [n, R]; each column solved independently."""
+    def solve(self, rhs, tol=1e-6, restart=0, max_it=200, history=None, weighted=False):
+        """rhs [n] or [n, R]; each column solved independently. weighted: GMRES in the
+        D_k = K + k^2 M inner product (Sec. 5.2)."""
+        Dk = (self.K + self.k ** 2 * self.M).tocsr() if weighted else None
+        weight = (lambda v: Dk @ v) if weighted else None
         rhs = np.asarray(rhs, dtype=np.complex128)
         single = rhs.ndim == 1
         B = rhs[:, None] if single else rhs
@@ -42,7 +45,7 @@ class Problem:
         for r in range(B.shape[1]):
             hist = [] if history is not None else None
             x, its, rel, ok = _gmres.gmres(lambda v: self.A @ v, lambda v: self.dd.apply(v, kind=self.kind), B[:, r],
-                                           tol, restart, max_it, history=hist)
+                                           tol, restart, max_it, history=hist, weight=weight)
             if history is not None:
                 history.append(hist)
             xs.append(x)
