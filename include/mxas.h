@@ -144,6 +144,13 @@ MX_API int mx_set_tuning(mx_handle h, int key, int value);
 #define MX_PREC_ADEF1 3
 MX_API int mx_set_preconditioner(mx_handle h, int kind);
 
+/* Weighted GMRES (Sec. 5.2): 1 = the Arnoldi process and the residual minimisation of
+ * mx_solve use the inner product <v, w>_D = w^H D_k v with D_k = K + k^2 M, the matrix of
+ * the (.,.)_{curl,k} inner product (Eq. 5.1); the stopping test is then on
+ * ||b - A x||_{D_k} / ||b||_{D_k} (true residual, FP64) and rel_residual reports that ratio.
+ * Two products with D_k per iteration. 0 (default) = the Euclidean inner product. */
+MX_API int mx_set_weighted_gmres(mx_handle h, int weighted);
+
 /* Message of the last error on the calling thread ("" if none). */
 MX_API const char* mx_last_error(void);
 

@@ -63,6 +63,7 @@ _sig = {
     "mx_set_dense_local": (C.c_int, [H, C.c_int]),
     "mx_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
     "mx_set_preconditioner": (C.c_int, [H, C.c_int]),
+    "mx_set_weighted_gmres": (C.c_int, [H, C.c_int]),
     "mx_build_problem": (C.c_int, [C.POINTER(MeshDesc), C.c_double, C.c_double, C.c_double, C.POINTER(DdDesc),
                                    C.POINTER(CoarseDesc), C.c_int, C.POINTER(H)]),
     "mx_set_xi_prob": (C.c_int, [H, C.c_double]),
@@ -168,6 +169,10 @@ MX_PREC_AS, MX_PREC_RAS, MX_PREC_HRAS, MX_PREC_ADEF1 = 0, 1, 2, 3
 
 def mx_set_preconditioner(h, kind):
     _check(lib.mx_set_preconditioner(h, int(kind)))
+
+
+def mx_set_weighted_gmres(h, weighted):
+    _check(lib.mx_set_weighted_gmres(h, int(bool(weighted))))
 
 
 def mx_factor(h):

@@ -261,6 +261,14 @@ int mx_set_preconditioner(mx_handle h, int kind) {
   });
 }
 
+int mx_set_weighted_gmres(mx_handle h, int weighted) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    MX_REQUIRE(weighted == 0 || weighted == 1, MX_EINVAL, "weighted must be 0 or 1");
+    reinterpret_cast<Problem*>(h)->weighted = weighted != 0;
+  });
+}
+
 int mx_factor(mx_handle h) {
   return guard([&] {
     MX_REQUIRE(h, MX_EINVAL, "null handle");

@@ -42,9 +42,17 @@ __global__ void k_spmv(int64_t rows, int nrhs, const int32_t* __restrict__ rowpt
   }
 }
 
+static void spmv_km(const Problem& P, double sr, double si, const void* x, int xtype, double2* y, int nrhs,
+                    cudaStream_t s);
+
 void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int nrhs, cudaStream_t s) {
+  spmv_km(P, P.k * P.k, xi, x, xtype, y, nrhs, s);
+}
+
+// y = (K - (sr + i si) M) x
+static void spmv_km(const Problem& P, double sr, double si, const void* x, int xtype, double2* y, int nrhs,
+                    cudaStream_t s) {
   const int64_t work = P.A.rows * nrhs;
-  const double sr = P.k * P.k, si = xi;
   // K, M values and column indices once, x once, y once (algorithmic minimum)
   const double xb = xtype == 0 ? 16.0 : 8.0;
   ProfScope ps(K_SPMV, s, 1, 20.0 * P.A.nnz + 4.0 * (P.A.rows + 1) + (xb + 16.0) * (double)P.A.rows * nrhs,
@@ -127,6 +135,7 @@ struct Workspace {
   DevBuf<double2> y;              // [m][nrhs]
   DevBuf<double2> hpart;          // [nblk][m+2][nrhs] partial dot products
   DevBuf<double2> h2;             // [m+2][nrhs] reduced dots of the current pass
+  DevBuf<double2> h1;             // [m+2][nrhs] first-pass dots (weighted Arnoldi)
   DevBuf<double> npart;           // [nblk][nrhs]
   DevBuf<double> bnorm, wnorm0;   // [nrhs]
   DevBuf<int32_t> active;         // [nrhs] 1 while the right-hand side iterates
@@ -175,6 +184,7 @@ static Workspace& workspace(Problem& P, int nrhs, int m) {
   W->nblk = 4 * sm_count();
   W->hpart.alloc((size_t)W->nblk * (m + 2) * nrhs);
   W->h2.alloc((size_t)(m + 2) * nrhs);
+  W->h1.alloc((size_t)(m + 2) * nrhs);
   W->npart.alloc((size_t)W->nblk * nrhs);
   W->bnorm.alloc(nrhs);
   W->wnorm0.alloc(nrhs);
@@ -312,7 +322,7 @@ void precond_apply(Problem& P, const void* v, void* z, int ztype, int nrhs, int 
 template <int RP>
 __global__ void __launch_bounds__(256) k_dots(int64_t n, int nrhs, int nvec, int with_norm, const double2* __restrict__ V,
                                               const double2* __restrict__ w, const int32_t* __restrict__ active,
-                                              double2* __restrict__ hpart) {
+                                              double2* __restrict__ hpart, const double2* __restrict__ extra = nullptr) {
   constexpr int XL = 32 / RP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = lane % RP, xl = lane / RP;
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(256) k_dots(int64_t n, int nrhs, int nvec, int
   const int64_t nv = n * nrhs;
   const bool on = r < nrhs && active[min(r, nrhs - 1)];
   for (int i = warp; i < total; i += 8) {
-    const double2* Vi = (i < nvec) ? V + (int64_t)i * nv : w;
+    const double2* Vi = (i < nvec) ? V + (int64_t)i * nv : (extra ? extra : w);
     double ax = 0, ay = 0;
     if (on)
       for (int64_t x = x0 + xl; x < x1; x += XL) {
@@ -416,6 +426,59 @@ __global__ void k_arnoldi_finish(int nblk, int nrhs, int j, int m, int pass, con
   if (pass == 0) wnorm0[r] = sqrt(h2[(j + 1) * nrhs + r].x);  // ||w|| before orthogonalisation
   Hc[(j + 1) * nrhs + r] = make_double2(nw, 0.0);
   if (pass == 0 && nw < 0.7071067811865476 * wnorm0[r]) atomicOr(&flags[1], 1);
+}
+
+// Weighted Arnoldi (D-inner product), per right-hand side. stage 0, after the inner products
+// of w (h1, entry j+1 = ||w||_D^2) and of the updated w' (h2, entry j+1 = ||w'||_D^2): store
+// column j, its subdiagonal ||w'||_D and the DGKS decision. stage 1, after the second update
+// with h2: add h2 to the column and take the norm by Pythagoras, ||w''||^2 = ||w'||^2 - |h2|^2
+// (the correction is small when it is needed).
+__global__ void k_arnoldi_finish_w(int nrhs, int j, int m, int stage, const double2* h1, const double2* h2, double2* H,
+                                   const int32_t* active, int32_t* flags) {
+  const int r = threadIdx.x;
+  if (r == 0 && stage == 0) flags[1] = 0;
+  __syncthreads();
+  if (r >= nrhs || !active[r]) return;
+  double2* Hc = H + (int64_t)j * (m + 1) * nrhs;
+  const double n1 = sqrt(fmax(h2[(j + 1) * nrhs + r].x, 0.0));
+  if (stage == 0) {
+    for (int i = 0; i <= j; ++i) Hc[i * nrhs + r] = h1[i * nrhs + r];
+    const double n0 = sqrt(fmax(h1[(j + 1) * nrhs + r].x, 0.0));
+    Hc[(j + 1) * nrhs + r] = make_double2(n1, 0.0);
+    if (n1 < 0.7071067811865476 * n0) atomicOr(&flags[1], 1);
+  } else {
+    double c = 0;
+    for (int i = 0; i <= j; ++i) {
+      const double2 v = h2[i * nrhs + r];
+      Hc[i * nrhs + r] = make_double2(Hc[i * nrhs + r].x + v.x, Hc[i * nrhs + r].y + v.y);
+      c += v.x * v.x + v.y * v.y;
+    }
+    Hc[(j + 1) * nrhs + r] = make_double2(sqrt(fmax(n1 * n1 - c, 0.0)), 0.0);
+  }
+}
+
+// npart[blk][q] = partial sums of Re(conj(r) y) (y = D r): the D-norm of r squared
+__global__ void k_wnorm_partials(int64_t n, int nrhs, const double2* r, const double2* y, double* npart) {
+  __shared__ double sh[256];
+  const int64_t nv = n * nrhs;
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x) * nrhs;
+  const int64_t t0 = blockIdx.x * chunk, t1 = min(nv, t0 + chunk);
+  double acc = 0;
+  const int q = threadIdx.x % nrhs;
+  const int lanes = 256 / nrhs;
+  const int li = threadIdx.x / nrhs;
+  if (li < lanes)
+    for (int64_t t = t0 + (int64_t)li * nrhs + q; t < t1; t += (int64_t)lanes * nrhs) {
+      acc = fma(r[t].x, y[t].x, acc);
+      acc = fma(r[t].y, y[t].y, acc);
+    }
+  sh[threadIdx.x] = (li < lanes) ? acc : 0.0;
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double s = 0;
+    for (int l = 0; l < lanes; ++l) s += sh[l * nrhs + threadIdx.x];
+    npart[(int64_t)blockIdx.x * nrhs + threadIdx.x] = s;
+  }
 }
 
 // v_{j+1} = w / h_{j+1,j}
@@ -562,25 +625,30 @@ __global__ void k_copy_norm(int nrhs, const double* beta, double* bnorm) {
 }
 
 template <int RP>
-static void launch_dots(Workspace& W, int64_t n, int nvec, int with_norm, const double2* V, cudaStream_t s) {
-  MX_LAUNCH(k_dots<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, with_norm, V, W.w.p, W.active.p, W.hpart.p));
+static void launch_dots(Workspace& W, int64_t n, int nvec, int with_norm, const double2* V, cudaStream_t s,
+                        const double2* target, const double2* extra) {
+  MX_LAUNCH(k_dots<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, with_norm, V, target, W.active.p, W.hpart.p, extra));
 }
 template <int RP>
 static void launch_update(Workspace& W, int64_t n, int nvec, cudaStream_t s) {
   MX_LAUNCH(k_orth_update<RP><<<W.nblk, 256, 0, s>>>(n, W.nrhs, nvec, W.V.p, W.h2.p, W.active.p, W.w.p, W.npart.p));
 }
 
-static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s) {
+// h = V^H target (+ extra^H target, or |target|^2 when extra is null, as entry nvec when
+// with_norm); target defaults to w
+static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s, const double2* target = nullptr,
+                 const double2* extra = nullptr) {
   const int nr = W.nrhs;
+  if (!target) target = W.w.p;
   {
     // V_0..V_{nvec-1} and w read once each
     ProfScope ps(K_DOTS, s, 1, 16.0 * (nvec + 1) * (double)n * nr, 8.0 * (nvec + with_norm) * (double)n * nr);
-    if (nr <= 1) launch_dots<1>(W, n, nvec, with_norm, W.V.p, s);
-    else if (nr <= 2) launch_dots<2>(W, n, nvec, with_norm, W.V.p, s);
-    else if (nr <= 4) launch_dots<4>(W, n, nvec, with_norm, W.V.p, s);
-    else if (nr <= 8) launch_dots<8>(W, n, nvec, with_norm, W.V.p, s);
-    else if (nr <= 16) launch_dots<16>(W, n, nvec, with_norm, W.V.p, s);
-    else launch_dots<32>(W, n, nvec, with_norm, W.V.p, s);
+    if (nr <= 1) launch_dots<1>(W, n, nvec, with_norm, W.V.p, s, target, extra);
+    else if (nr <= 2) launch_dots<2>(W, n, nvec, with_norm, W.V.p, s, target, extra);
+    else if (nr <= 4) launch_dots<4>(W, n, nvec, with_norm, W.V.p, s, target, extra);
+    else if (nr <= 8) launch_dots<8>(W, n, nvec, with_norm, W.V.p, s, target, extra);
+    else if (nr <= 16) launch_dots<16>(W, n, nvec, with_norm, W.V.p, s, target, extra);
+    else launch_dots<32>(W, n, nvec, with_norm, W.V.p, s, target, extra);
     MX_CHECK_LAUNCH();
   }
   const int total = nvec + with_norm;
@@ -590,11 +658,13 @@ static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t 
 }
 
 // mixed form: double-float passes over the basis, FP64 reduction of the block partials
-static void dots_mixed(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s) {
+static void dots_mixed(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s,
+                       const double2* target = nullptr, const double2* extra = nullptr) {
   // one resident wave: the dots kernel holds 64 KB of accumulators per block (3 per SM)
   const int nb = std::min(W.nblk, 3 * sm_count());
   dots_df(nb, n, W.nrhs, nvec, with_norm, reinterpret_cast<const float4*>(W.V.p),
-          reinterpret_cast<const float4*>(W.w.p), W.active.p, W.hpart.p, s);
+          reinterpret_cast<const float4*>(target ? target : W.w.p), W.active.p, W.hpart.p, s,
+          reinterpret_cast<const float4*>(extra));
   const int total = nvec + with_norm;
   ProfScope ps(K_ARNOLDI_SMALL, s);
   MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * W.nrhs, 128), 128, 0, s>>>(nb, total, W.nrhs, W.hpart.p,
@@ -615,11 +685,23 @@ static void orth_update(Workspace& W, int64_t n, int nvec, cudaStream_t s) {
   MX_CHECK_LAUNCH();
 }
 
+// weighted GMRES: replace the Euclidean partials of r in npart by those of ||r||_D^2
+// (D r formed in W.w, which is free at restarts)
+static void weighted_norm_partials(Problem& P, Workspace& W, cudaStream_t s) {
+  spmv_km(P, -P.k * P.k, 0.0, W.r.p, 0, W.w.p, W.nrhs, s);
+  ProfScope ps(K_RESIDUAL, s);
+  MX_LAUNCH(k_wnorm_partials<<<W.nblk, 256, 0, s>>>(W.n, W.nrhs, W.r.p, W.w.p, W.npart.p));
+  MX_CHECK_LAUNCH();
+}
+
 static void true_residual(Problem& P, Workspace& W, cudaStream_t s) {
   spmv(P, P.xi_prob, W.x.p, 0, W.r.p, W.nrhs, s);
-  ProfScope ps(K_RESIDUAL, s, 1, 48.0 * (double)W.n * W.nrhs, 6.0 * (double)W.n * W.nrhs);
-  MX_LAUNCH(k_residual<<<W.nblk, 256, 0, s>>>(W.n, W.nrhs, W.b.p, W.r.p, W.npart.p));
-  MX_CHECK_LAUNCH();
+  {
+    ProfScope ps(K_RESIDUAL, s, 1, 48.0 * (double)W.n * W.nrhs, 6.0 * (double)W.n * W.nrhs);
+    MX_LAUNCH(k_residual<<<W.nblk, 256, 0, s>>>(W.n, W.nrhs, W.b.p, W.r.p, W.npart.p));
+    MX_CHECK_LAUNCH();
+  }
+  if (P.weighted) weighted_norm_partials(P, W, s);
 }
 
 __global__ void k_fill_i32(int n, int32_t v, int32_t* p) {
@@ -670,6 +752,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
   // ||b||: residual of x = 0
   MX_CUDA(cudaMemsetAsync(W.r.p, 0, nv * sizeof(double2), s));
   MX_LAUNCH(k_residual<<<W.nblk, 256, 0, s>>>(n, nrhs, W.b.p, W.r.p, W.npart.p));
+  if (P.weighted) weighted_norm_partials(P, W, s);  // ||b||_D
   MX_CUDA(cudaMemsetAsync(W.active.p, 0, nrhs * 4, s));
   MX_LAUNCH(k_restart<<<1, 32, 0, s>>>(W.nblk, nrhs, m, W.npart.p, W.bnorm.p, -1.0, W.active.p, beta.p, W.g.p));
   MX_LAUNCH(k_copy_norm<<<1, 32, 0, s>>>(nrhs, beta.p, W.bnorm.p));
@@ -704,8 +787,46 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
       if (mixed) spmv_df(P, reinterpret_cast<const float2*>(zj), reinterpret_cast<float4*>(W.w.p), nrhs, s);
       else spmv(P, P.xi_prob, zj, ztype, W.w.p, nrhs, s);
       ++launches;
+      if (P.weighted) {
+        // weighted Arnoldi (Sec. 5.2): inner products <v_i, w>_D = v_i^H (D w)
+        auto dmul = [&](double2* in, double2* out) {
+          if (mixed) dmul_df(P, reinterpret_cast<const float4*>(in), reinterpret_cast<float4*>(out), nrhs, s);
+          else spmv_km(P, -P.k * P.k, 0.0, in, 0, out, nrhs, s);
+        };
+        auto wdots = [&]() {  // h = V^H (D w), entry j+1 = w^H D w
+          if (mixed) dots_mixed(W, n, j + 1, 1, s, W.r.p, W.w.p);
+          else dots(W, n, j + 1, 1, s, W.r.p, W.w.p);
+        };
+        auto update = [&]() {
+          if (mixed)
+            orth_update_df(W.nblk, n, nrhs, j + 1, reinterpret_cast<const float4*>(W.V.p), W.h2.p, W.hs.p,
+                           W.active.p, reinterpret_cast<float4*>(W.w.p), W.npart.p, s);
+          else
+            orth_update(W, n, j + 1, s);
+        };
+        dmul(W.w.p, W.r.p);
+        wdots();
+        MX_CUDA(cudaMemcpyAsync(W.h1.p, W.h2.p, (size_t)(j + 2) * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        update();
+        dmul(W.w.p, W.r.p);
+        wdots();
+        {
+          ProfScope ps(K_ARNOLDI_SMALL, s);
+          MX_LAUNCH(k_arnoldi_finish_w<<<1, 32, 0, s>>>(nrhs, j, m, 0, W.h1.p, W.h2.p, W.H.p, W.active.p, W.flags.p));
+          MX_CHECK_LAUNCH();
+        }
+        MX_CUDA(cudaMemcpyAsync(W.h_flags, W.flags.p, 8, cudaMemcpyDeviceToHost, s));
+        MX_CUDA(cudaStreamSynchronize(s));
+        if (W.h_flags[1]) {
+          update();
+          ProfScope ps(K_ARNOLDI_SMALL, s);
+          MX_LAUNCH(k_arnoldi_finish_w<<<1, 32, 0, s>>>(nrhs, j, m, 1, W.h1.p, W.h2.p, W.H.p, W.active.p, W.flags.p));
+          MX_CHECK_LAUNCH();
+        }
+        launches += 8;
+      }
       // Arnoldi: classical Gram-Schmidt, second pass when needed
-      for (int pass = 0; pass < 2; ++pass) {
+      for (int pass = 0; pass < 2 && !P.weighted; ++pass) {
         if (pass == 1) {
           MX_CUDA(cudaMemcpyAsync(W.h_flags, W.flags.p, 8, cudaMemcpyDeviceToHost, s));
           MX_CUDA(cudaStreamSynchronize(s));

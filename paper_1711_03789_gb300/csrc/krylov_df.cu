@@ -50,7 +50,8 @@ constexpr int DOTS_IC = 32;
 template <int RP>
 __global__ void __launch_bounds__(256) k_dots_df(int64_t n, int nrhs, int nvec, int with_norm,
                                                  const float4* __restrict__ V, const float4* __restrict__ w,
-                                                 const int32_t* __restrict__ active, double2* __restrict__ hpart) {
+                                                 const int32_t* __restrict__ active, double2* __restrict__ hpart,
+                                                 const float4* __restrict__ extra) {
   constexpr int XL = 32 / RP;
   extern __shared__ float4 acc_sm[];  // [8 warps][DOTS_IC][RP]: {re_s, re_e, im_s, im_e}
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(256) k_dots_df(int64_t n, int nrhs, int nvec, 
       }
       for (int k = 0; k < icn; ++k) {
         const int i = ic + k;
-        const float4* Vi = (i < nvec) ? V + (int64_t)i * nv : w;
+        const float4* Vi = (i < nvec) ? V + (int64_t)i * nv : (extra ? extra : w);
         df::Acc are, aim;
 #pragma unroll
         for (int u = 0; u < DOTS_U; ++u) {
@@ -222,6 +223,26 @@ __global__ void k_spmv_df_c128(int64_t rows, int nrhs, const int32_t* __restrict
   }
 }
 
+// y = D w for a real D (coefficients {a_hi, a_lo, 0, 0}), w and y complex double-floats
+__global__ void k_dmul_df(int64_t rows, int nrhs, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                          const float4* __restrict__ coef, const float4* __restrict__ w, float4* __restrict__ y) {
+  const int64_t work = rows * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nrhs);
+    const int64_t i = t / nrhs;
+    df::Acc re, im;
+    const int32_t e1 = rowptr[i + 1];
+    for (int32_t e = rowptr[i]; e < e1; ++e) {
+      const float4 x = w[(int64_t)col[e] * nrhs + r];
+      const float4 c = coef[e];
+      df::add_prod2(re, c.x, c.y, x.x, x.z);
+      df::add_prod2(im, c.x, c.y, x.y, x.w);
+    }
+    const float2 a = df::value(re), b = df::value(im);
+    y[t] = make_float4(a.x, b.x, a.y, b.y);
+  }
+}
+
 // double-float coefficients of A_xi, cached per value of xi (slot 0: xi_prob, 1: xi_prec)
 static const float4* coef_df(Problem& P, double xi, int slot, cudaStream_t s) {
   if (P.A_coef_df[slot].n != (size_t)P.A.nnz || P.A_coef_xi[slot] != xi) {
@@ -232,6 +253,23 @@ static const float4* coef_df(Problem& P, double xi, int slot, cudaStream_t s) {
     P.A_coef_xi[slot] = xi;
   }
   return P.A_coef_df[slot].p;
+}
+
+// y = D_k w with D_k = K + k^2 M (the weight of weighted GMRES), double-float vectors
+void dmul_df(Problem& P, const float4* w, float4* y, int nrhs, cudaStream_t s) {
+  if (P.A_coef_df[2].n != (size_t)P.A.nnz) {
+    P.A_coef_df[2].alloc(P.A.nnz);
+    // K - (sr + i si) M with sr = -k^2, si = 0
+    MX_LAUNCH(k_coef_df<<<grid_for(P.A.nnz, 256), 256, 0, s>>>(P.A.nnz, P.A.K.p, P.A.M.p, -P.k * P.k, 0.0,
+                                                              P.A_coef_df[2].p));
+    MX_CHECK_LAUNCH();
+  }
+  const int64_t work = P.A.rows * nrhs;
+  ProfScope ps(K_SPMV, s, 1, 20.0 * P.A.nnz + 4.0 * (P.A.rows + 1) + 32.0 * (double)P.A.rows * nrhs,
+               4.0 * (double)P.A.nnz * nrhs);
+  MX_LAUNCH(k_dmul_df<<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p,
+                                                                      P.A_coef_df[2].p, w, y));
+  MX_CHECK_LAUNCH();
 }
 
 void spmv_df_c128(Problem& P, double xi, const float2* z, double2* y, int nrhs, cudaStream_t s) {
@@ -258,24 +296,24 @@ void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s) {
 
 template <int RP>
 static void dots_rp(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
-                    const int32_t* active, double2* hpart, cudaStream_t s) {
+                    const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra) {
   const size_t smem = (size_t)8 * DOTS_IC * RP * sizeof(float4);
   static bool configured = false;
   if (!configured) {
     MX_CUDA(cudaFuncSetAttribute(k_dots_df<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = true;
   }
-  MX_LAUNCH(k_dots_df<RP><<<nblk, 256, smem, s>>>(n, nrhs, nvec, with_norm, V, w, active, hpart));
+  MX_LAUNCH(k_dots_df<RP><<<nblk, 256, smem, s>>>(n, nrhs, nvec, with_norm, V, w, active, hpart, extra));
 }
 void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
-             const int32_t* active, double2* hpart, cudaStream_t s) {
+             const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra) {
   ProfScope ps(K_DOTS, s, 1, 16.0 * (nvec + 1) * (double)n * nrhs, 8.0 * (nvec + with_norm) * (double)n * nrhs);
-  if (nrhs <= 1) dots_rp<1>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s);
-  else if (nrhs <= 2) dots_rp<2>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s);
-  else if (nrhs <= 4) dots_rp<4>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s);
-  else if (nrhs <= 8) dots_rp<8>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s);
-  else if (nrhs <= 16) dots_rp<16>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s);
-  else dots_rp<32>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s);
+  if (nrhs <= 1) dots_rp<1>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
+  else if (nrhs <= 2) dots_rp<2>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
+  else if (nrhs <= 4) dots_rp<4>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
+  else if (nrhs <= 8) dots_rp<8>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
+  else if (nrhs <= 16) dots_rp<16>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
+  else dots_rp<32>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
   MX_CHECK_LAUNCH();
 }
 

@@ -112,8 +112,9 @@ struct Problem {
   DevBuf<float> R0T_valf;  // FP32 copy of the R^0^T values (mixed-form scatter)
   DevBuf<float> R0_valf;   // FP32 copy of the R^0 values (mixed-form coarse restriction)
   // mixed-form operator coefficients a + i b = K - (k^2 + i xi_prob) M as double-floats
-  DevBuf<float4> A_coef_df[2];     // slot 0: xi_prob (operator), 1: xi_prec (hybrid preconditioners)
-  double A_coef_xi[2] = {-1.0, -1.0};
+  DevBuf<float4> A_coef_df[3];     // 0: xi_prob (operator), 1: xi_prec (hybrid preconditioners), 2: D_k
+  double A_coef_xi[3] = {-1.0, -1.0, -1.0};
+  bool weighted = false;           // weighted GMRES in the D_k = K + k^2 M inner product (Sec. 5.2)
   int64_t n_c = 0;
   int coarse_band = 0;
   int64_t ld_c = 0;
@@ -207,7 +208,9 @@ void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s);
 // y = A_xi z, z c64, y c128 (double-float accumulation)
 void spmv_df_c128(Problem& P, double xi, const float2* z, double2* y, int nrhs, cudaStream_t s);
 void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
-             const int32_t* active, double2* hpart, cudaStream_t s);
+             const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra = nullptr);
+// y = D_k w, D_k = K + k^2 M, double-float vectors
+void dmul_df(Problem& P, const float4* w, float4* y, int nrhs, cudaStream_t s);
 void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float4* V, const double2* h, float4* hs,
                     const int32_t* active, float4* w, double* npart, cudaStream_t s);
 void normalize_df(int64_t nv, int nrhs, int j, int m, const double2* H, const int32_t* active, const float4* w,

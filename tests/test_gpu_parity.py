@@ -409,3 +409,48 @@ def test_gmres_with_restricted_and_hybrid_preconditioners(kind, name):
         err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
         assert err <= 1e-8, (r, err)
         assert abs(st[r]["iterations"] - ost[r][0]) <= 1, (st[r], ost[r])
+
+
+@pytest.mark.parametrize("prec", [mx.MX_PLAIN_FP64, mx.MX_MIXED])
+def test_weighted_gmres_matches_oracle(prec):
+    """Weighted GMRES in the D_k = K + k^2 M inner product (Sec. 5.2) against the oracle's
+    weighted GMRES: same solution (both to a 1e-10 D_k-norm residual), the reported residual
+    is the D_k-norm ratio, and the FP64 form takes the same number of iterations (+-1)."""
+    n, k, nrhs = 10, 6.0, 2
+    c, p = inputs.bump_batch(7, nrhs)
+    O = OracleProblem(n, k, k, k, 5, 1, coarse_m=5)
+    O.factor()
+    fo = O.load_vector(c, p, 0.1)
+    xo, ost = O.solve(fo, tol=1e-10, restart=0, max_it=300, weighted=True)
+    Dk = (O.K + k * k * O.M).tocsr()
+    with _handle(n, k, k, k, 5, 1, cm=5, prec=prec) as P:
+        P.factor()
+        mx.mx_set_weighted_gmres(P.h, 1)
+        f = P.load_vector(c, p, 0.1)
+        x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
+    assert rc == mx.MX_OK
+    for r in range(nrhs):
+        assert st[r]["converged"]
+        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
+        assert err <= 1e-8, (r, err)
+        res = fo[:, r] - O.A @ x[r]
+        rel = np.sqrt(abs(np.vdot(res, Dk @ res))) / np.sqrt(abs(np.vdot(fo[:, r], Dk @ fo[:, r])))
+        assert rel <= 1.05e-10 and abs(rel - st[r]["rel_residual"]) <= 1e-12, (rel, st[r])
+        if prec == mx.MX_PLAIN_FP64:
+            assert abs(st[r]["iterations"] - ost[r][0]) <= 1, (st[r], ost[r])
+
+
+def test_weighted_gmres_restarted():
+    """Weighted GMRES(8) with restarts reaches the direct solution."""
+    n, k = 10, 6.0
+    c, p = inputs.bump_batch(8, 1)
+    O = OracleProblem(n, k, k, k, 5, 1, coarse_m=5)
+    fo = O.load_vector(c, p, 0.1)
+    import scipy.sparse.linalg as spla
+    xd = spla.spsolve(O.A.tocsc(), fo[:, 0])
+    with _handle(n, k, k, k, 5, 1, cm=5, prec=mx.MX_MIXED) as P:
+        P.factor()
+        mx.mx_set_weighted_gmres(P.h, 1)
+        x, st, rc = P.solve(fo.T.copy(), tol=1e-9, restart=8, max_it=400)
+    assert rc == mx.MX_OK and st[0]["converged"]
+    assert np.linalg.norm(x[0] - xd) / np.linalg.norm(xd) <= 1e-7
