@@ -27,6 +27,14 @@ Readings:
     marking the DOFs that subdomain l owns, the owner being the core box that contains
     the edge midpoint (per axis cell index floor(mid / core), clipped to the last box).
     With overlap >= 1 the owner always holds the DOF, so sum_l (R^l)^T D^l R^l = I.
+  * inexact coarse solve (Sec. 6.4): (A^0)^{-1} R^0 v is replaced by the result of an
+    inner right-preconditioned GMRES on A^0 y = R^0 v -- unrestarted, y0 = 0, stopped at
+    a relative Euclidean residual tol (the paper takes 1e-1) or after max_it iterations --
+    preconditioned by a one-level Schwarz method on subdomains of the coarse mesh (boxes
+    of the coarse mesh built by the same rules as on the fine mesh). The paper's inner
+    preconditioner is the one-level ImpRAS (impedance conditions on the subdomain
+    boundaries); here the subdomain problems keep the PEC conditions of Eq. 3.1 (one-level
+    RAS or AS).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -132,6 +140,7 @@ class Schwarz:
         self.A_prec = A_prec.tocsr()
         self.lus = None
         self.coarse = None
+        self.inner = None  # one-level Schwarz on the coarse mesh (inexact coarse solve)
         if coarse_m:
             cm = KuhnMesh(coarse_m)
             Kc, Mc = fem.assemble_KM(cm)
@@ -159,18 +168,41 @@ class Schwarz:
         i = self.idx[l]
         return self.A_prec[i][:, i]
 
+    def set_inner_coarse(self, core, overlap, tol=0.1, max_it=100, kind="ras"):
+        """Solve the coarse problem inexactly by inner GMRES (Sec. 6.4), preconditioned by
+        one-level Schwarz (kind "as" or "ras") on boxes of `core` coarse cells widened by
+        `overlap` coarse cells."""
+        if not hasattr(self, "A0"):
+            raise ValueError("no coarse level")
+        self.inner = Schwarz(self.coarse_mesh, self.A0, core, overlap)
+        self.inner_tol, self.inner_max_it, self.inner_kind = tol, max_it, kind
+        self.inner_its = []  # inner iterations of every coarse solve, in order
+
     def factor(self, subset=None):
         ls = range(len(self.idx)) if subset is None else subset
         self.lus = {l: spla.splu(self.minor(l).tocsc()) for l in ls}
-        if hasattr(self, "A0"):
+        if self.inner is not None:
+            self.inner.factor()
+        elif hasattr(self, "A0"):
             self.coarse = spla.splu(self.A0.tocsc())
 
     def local_solve(self, l, r_l):
         return self.lus[l].solve(r_l)
 
+    def coarse_solve(self, rc):
+        """(A^0)^{-1} rc: direct, or the inner GMRES of Sec. 6.4 when set."""
+        if self.inner is None:
+            return self.coarse.solve(rc)
+        from .gmres import gmres
+        A0, inner, kind = self.A0, self.inner, self.inner_kind
+        y, its, _, _ = gmres(lambda u: A0 @ u, lambda u: inner.apply(u, levels=(1,), kind=kind), rc,
+                             self.inner_tol, 0, self.inner_max_it)
+        self.inner_its.append(its)
+        return y
+
     def coarse_correction(self, v):
         """G v with G = (R^0)^T (A^0)^{-1} R^0 (the coarse term of Eq. 3.4)."""
-        return self.R0.T @ self.coarse.solve(self.R0 @ v)
+        return self.R0.T @ self.coarse_solve(self.R0 @ v)
 
     def ras1(self, v):
         """One-level restricted additive Schwarz: sum_l (R^l)^T D^l (A^l)^{-1} R^l v (Sec. 6.3)."""
@@ -204,6 +236,6 @@ class Schwarz:
             else:
                 for l, i in enumerate(self.idx):
                     z[i] += self.local_solve(l, v[i])
-        if 0 in levels and self.coarse is not None:
+        if 0 in levels and (self.coarse is not None or self.inner is not None):
             z += self.coarse_correction(v)
         return z

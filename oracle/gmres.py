@@ -18,6 +18,11 @@ Readings:
     process runs in <v, w>_D = w^* D v and the residual is minimised in ||.||_D; the
     stopping test is then on ||b - A x||_D / ||b||_D. The paper's weight is
     D_k = K + k^2 M, the matrix of the (.,.)_{curl,k} inner product (Eq. 2.3, Eq. 5.1).
+  * flexible GMRES (Saad, SIAM J. Sci. Comput. 14 (1993), FGMRES): the preconditioned
+    vectors z_j = B_j^{-1} v_j are kept and the iterate is x0 + Z_m y, which stays the
+    minimal-residual solution over span(Z_m) when the preconditioner changes from one
+    iteration to the next -- as it does when the coarse problem is solved only roughly by
+    an inner iteration (Sec. 6.4). With a fixed preconditioner it equals GMRES.
 """
 import numpy as np
 
@@ -34,11 +39,12 @@ def givens(a, b):
     return c, s
 
 
-def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=None, weight=None):
+def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=None, weight=None,
+          flexible=False):
     """Solve A x = b with right preconditioner B^{-1}.
 
     matvec(v) = A v, precond(v) = B^{-1} v for 1-D complex vectors; weight(v) = D v for
-    weighted GMRES (None: the Euclidean inner product).
+    weighted GMRES (None: the Euclidean inner product); flexible: keep Z_m (FGMRES).
     Returns (x, iterations, final relative true residual, converged)."""
     b = np.asarray(b, dtype=np.complex128)
     n = b.shape[0]
@@ -68,10 +74,14 @@ def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=
         g = np.zeros(m + 1, dtype=np.complex128)
         g[0] = beta
         V[0] = r / beta
+        Z = np.zeros((m, n), dtype=np.complex128) if flexible else None
         j_done = 0
         converged = False
         for j in range(m):
-            w = matvec(precond(V[j]))
+            z = precond(V[j])
+            if flexible:
+                Z[j] = z
+            w = matvec(z)
             for i in range(j + 1):  # modified Gram-Schmidt
                 H[i, j] = dot(V[i], w)
                 w = w - H[i, j] * V[i]
@@ -96,7 +106,7 @@ def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=
                 break
         k = j_done
         y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])  # upper-triangular back substitution
-        x = x + precond(V[:k].T @ y)
+        x = x + (Z[:k].T @ y if flexible else precond(V[:k].T @ y))
         r = b - matvec(x)
         beta = norm(r)
         rel = beta / bnorm

@@ -13,7 +13,9 @@ class Problem:
     """curl curl E - (k^2 + i xi_prob) E = F, PEC, preconditioned by AS built from
     A_{xi_prec} (Sec. 6.2: B^{-1}_{xi_prec} preconditions A_{xi_prob})."""
 
-    def __init__(self, n, k, xi_prob, xi_prec, core, overlap, coarse_m=0, kind="as"):
+    def __init__(self, n, k, xi_prob, xi_prec, core, overlap, coarse_m=0, kind="as", inner_coarse=None):
+        """inner_coarse: None (direct coarse solve) or a dict with core, overlap, tol, max_it,
+        kind of the inner GMRES coarse solve (Sec. 6.4); the outer GMRES is then flexible."""
         self.kind = kind  # "as" (Eq. 3.4), "ras" (Eq. RAS2), "hras" (Eq. HRAS), "adef1" (Eq. ADEF1ras)
         self.mesh = KuhnMesh(n)
         self.k, self.xi_prob, self.xi_prec = k, xi_prob, xi_prec
@@ -21,6 +23,9 @@ class Problem:
         self.A = fem.a_xi(self.K, self.M, k, xi_prob)
         self.A_prec = fem.a_xi(self.K, self.M, k, xi_prec)
         self.dd = dd.Schwarz(self.mesh, self.A_prec, core, overlap, coarse_m, k, xi_prec)
+        self.flexible = inner_coarse is not None
+        if inner_coarse is not None:
+            self.dd.set_inner_coarse(**inner_coarse)
 
     @property
     def n_dof(self):
@@ -45,7 +50,7 @@ class Problem:
         for r in range(B.shape[1]):
             hist = [] if history is not None else None
             x, its, rel, ok = _gmres.gmres(lambda v: self.A @ v, lambda v: self.dd.apply(v, kind=self.kind), B[:, r],
-                                           tol, restart, max_it, history=hist, weight=weight)
+                                           tol, restart, max_it, history=hist, weight=weight, flexible=self.flexible)
             if history is not None:
                 history.append(hist)
             xs.append(x)
