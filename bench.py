@@ -146,6 +146,10 @@ def run_ours(args, W, rank, world):
         if args.precond != "as":
             mx.mx_set_preconditioner(P.h, {"ras": mx.MX_PREC_RAS, "hras": mx.MX_PREC_HRAS,
                                            "adef1": mx.MX_PREC_ADEF1}[args.precond])
+        if args.coarse_gmres:
+            # inexact coarse solve (Sec. 6.4): inner GMRES with one-level Schwarz on the coarse mesh
+            P.set_coarse_solver(mx.MX_COARSE_GMRES, args.coarse_gmres, 1, args.coarse_tol, args.coarse_max_it,
+                                mx.MX_PREC_RAS if args.coarse_inner == "ras" else mx.MX_PREC_AS)
         P.factor()
         n = P.n_dof
         if host:
@@ -399,6 +403,11 @@ def main():
                     help="Schwarz variant: additive (Eq. 3.4), restricted, hybrid, adapted deflation (Sec. 6.3)")
     ap.add_argument("--weighted", action="store_true",
                     help="weighted GMRES in the D_k = K + k^2 M inner product (Sec. 5.2)")
+    ap.add_argument("--coarse-gmres", type=int, default=0, metavar="CORE",
+                    help="solve the coarse problem by inner GMRES (Sec. 6.4) on subdomains of CORE coarse cells")
+    ap.add_argument("--coarse-tol", type=float, default=0.1)
+    ap.add_argument("--coarse-max-it", type=int, default=100)
+    ap.add_argument("--coarse-inner", default="ras", choices=["ras", "as"])
     ap.add_argument("--local-tensor", type=int, default=None, choices=[0, 1],
                     help="local solves on the tensor cores (1) or CUDA cores (0); default: library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -428,6 +437,9 @@ def main():
               "coarse_cells": W["coarse"], "nrhs_per_gpu": W["nrhs"], "gmres_restart": W["restart"],
               "max_it": W["max_it"], "tol": W["tol"], "form": args.form, "preconditioner": args.precond,
               "gmres_inner_product": "D_k" if args.weighted else "euclidean",
+              "coarse_solver": ({"kind": "inner_gmres", "core_cells": args.coarse_gmres, "overlap_cells": 1,
+                                 "tol": args.coarse_tol, "max_it": args.coarse_max_it,
+                                 "preconditioner": args.coarse_inner} if args.coarse_gmres else "direct"),
               "l2": "inputs larger than L2 (factors and Krylov basis > 129 MB)"}
 
     if args.impl == "reference":
@@ -490,6 +502,8 @@ def main():
         "iterations": iters,
         "rel_residual_max": max(s["rel_residual"] for s in r["stats"]),
         "phases_ms": {"build": ph["build_ms"], "factor": ph["factor_ms"], "solve": ph["solve_ms"]},
+        "coarse_inner": ({"iterations": ph["coarse_inner_iterations"], "solves": ph["coarse_inner_solves"]}
+                         if args.coarse_gmres else None),
         "gmres_s": ph["solve_ms"] / 1e3,
         "rhs_per_s": world * nrhs / (r["ms"] / 1e3),
         "n_dof": n_dof,

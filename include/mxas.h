@@ -87,6 +87,9 @@ typedef struct {
   int64_t solve_launches;                 /* kernels launched by the last mx_solve */
   int32_t restarts;
   int32_t max_iterations;
+  int64_t coarse_inner_iterations;        /* MX_COARSE_GMRES: inner iterations of the last mx_solve
+                                             (for each coarse solve, the most any right-hand side took) */
+  int64_t coarse_inner_solves;            /* MX_COARSE_GMRES: coarse solves of the last mx_solve */
 } mx_timing;
 
 /* Library version string. */
@@ -150,6 +153,28 @@ MX_API int mx_set_preconditioner(mx_handle h, int kind);
  * ||b - A x||_{D_k} / ||b||_{D_k} (true residual, FP64) and rel_residual reports that ratio.
  * Two products with D_k per iteration. 0 (default) = the Euclidean inner product. */
 MX_API int mx_set_weighted_gmres(mx_handle h, int weighted);
+
+/* Coarse solver of the two-level preconditioners (Sec. 6.4).
+ *   MX_COARSE_DIRECT (default): the FP64 band LU of A^0 (and, in the mixed form, its
+ *     explicit c64 inverse), built by mx_factor.
+ *   MX_COARSE_GMRES: every coarse solve (A^0)^{-1} R^0 v is replaced by an inner
+ *     right-preconditioned GMRES on A^0 y = R^0 v with y0 = 0, unrestarted, stopped at the
+ *     relative Euclidean residual `tol` (0 < tol < 1; the paper takes 1e-1) or after
+ *     `max_it` (1..1000) iterations, whichever comes first (a solution that misses tol is
+ *     used as it is). Its preconditioner is one-level Schwarz, `prec_kind` MX_PREC_AS or
+ *     MX_PREC_RAS, on subdomains of the coarse mesh described by `dd` (boxes of
+ *     dd->core_cells coarse cells widened by dd->overlap_cells; RAS needs an overlap >= 1).
+ *     The inner problem is built here with A^0 = K_c - (k^2 + i xi_prec) M_c and the
+ *     handle's precision, and factored by mx_factor (or here, if the handle is already
+ *     factored); the direct coarse factors are then not built. The outer GMRES of mx_solve
+ *     keeps the preconditioned vectors z_j (flexible GMRES), so the varying inner solves
+ *     are allowed.
+ * MX_EINVAL for a handle without a coarse level or out-of-range arguments (the setting is
+ * then unchanged). Switching back to MX_COARSE_DIRECT on a factored handle builds the
+ * direct factors at once. */
+#define MX_COARSE_DIRECT 0
+#define MX_COARSE_GMRES 1
+MX_API int mx_set_coarse_solver(mx_handle h, int kind, const mx_dd_desc* dd, double tol, int max_it, int prec_kind);
 
 /* Message of the last error on the calling thread ("" if none). */
 MX_API const char* mx_last_error(void);

@@ -193,6 +193,8 @@ class Schwarz:
         """(A^0)^{-1} rc: direct, or the inner GMRES of Sec. 6.4 when set."""
         if self.inner is None:
             return self.coarse.solve(rc)
+        if rc.ndim == 2:  # one inner solve per column
+            return np.stack([self.coarse_solve(rc[:, q]) for q in range(rc.shape[1])], axis=1)
         from .gmres import gmres
         A0, inner, kind = self.A0, self.inner, self.inner_kind
         y, its, _, _ = gmres(lambda u: A0 @ u, lambda u: inner.apply(u, levels=(1,), kind=kind), rc,

@@ -49,7 +49,8 @@ class RhsStats(C.Structure):
 
 class Timing(C.Structure):
     _fields_ = [("build_ms", C.c_double), ("factor_ms", C.c_double), ("solve_ms", C.c_double),
-                ("solve_launches", C.c_int64), ("restarts", C.c_int32), ("max_iterations", C.c_int32)]
+                ("solve_launches", C.c_int64), ("restarts", C.c_int32), ("max_iterations", C.c_int32),
+                ("coarse_inner_iterations", C.c_int64), ("coarse_inner_solves", C.c_int64)]
 
 
 H = C.c_void_p
@@ -64,6 +65,7 @@ _sig = {
     "mx_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
     "mx_set_preconditioner": (C.c_int, [H, C.c_int]),
     "mx_set_weighted_gmres": (C.c_int, [H, C.c_int]),
+    "mx_set_coarse_solver": (C.c_int, [H, C.c_int, C.POINTER(DdDesc), C.c_double, C.c_int, C.c_int]),
     "mx_build_problem": (C.c_int, [C.POINTER(MeshDesc), C.c_double, C.c_double, C.c_double, C.POINTER(DdDesc),
                                    C.POINTER(CoarseDesc), C.c_int, C.POINTER(H)]),
     "mx_set_xi_prob": (C.c_int, [H, C.c_double]),
@@ -173,6 +175,14 @@ def mx_set_preconditioner(h, kind):
 
 def mx_set_weighted_gmres(h, weighted):
     _check(lib.mx_set_weighted_gmres(h, int(bool(weighted))))
+
+
+MX_COARSE_DIRECT, MX_COARSE_GMRES = 0, 1
+
+
+def mx_set_coarse_solver(h, kind, core_cells=1, overlap_cells=1, tol=0.1, max_it=100, prec_kind=MX_PREC_RAS):
+    dd = DdDesc(int(core_cells), int(overlap_cells))
+    _check(lib.mx_set_coarse_solver(h, int(kind), C.byref(dd), float(tol), int(max_it), int(prec_kind)))
 
 
 def mx_factor(h):

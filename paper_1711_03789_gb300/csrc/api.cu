@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/mxas.h). Every entry point catches all
 // exceptions, records a message for mx_last_error() and returns an MX_E* code.
 #include <cstring>
+#include <memory>
 
 #include "problem.cuh"
 
@@ -11,7 +12,10 @@ void prof_reset(bool on);
 void prof_read(double* ms, int64_t* launches, double* bytes, double* flops);
 int64_t launch_count();
 
-Problem::~Problem() { free_workspace(*this); }
+Problem::~Problem() {
+  free_workspace(*this);
+  delete coarse_inner;
+}
 
 // ---- layout helpers -----------------------------------------------------------------
 // user layout [nrhs][n] <-> solver layout [n][nrhs]
@@ -169,7 +173,13 @@ void factor_problem(Problem& P) {
   EventTimer t(P.stream);
   extract_minors(P);
   factor_local(P);
-  factor_coarse(P);
+  if (P.coarse_inner) {
+    P.coarse_inner->stream = P.stream;
+    factor_problem(*P.coarse_inner);  // the inner coarse GMRES replaces the direct factors
+  } else {
+    factor_coarse(P);
+    P.coarse_factored = P.coarse_m > 0;
+  }
   P.timing.factor_ms = t.stop();
   check_status(P);
 }
@@ -208,7 +218,9 @@ int mx_set_xi_prob(mx_handle h, double xi_prob) {
 int mx_set_stream(mx_handle h, void* stream) {
   return guard([&] {
     MX_REQUIRE(h, MX_EINVAL, "null handle");
-    reinterpret_cast<Problem*>(h)->stream = reinterpret_cast<cudaStream_t>(stream);
+    auto& P = *reinterpret_cast<Problem*>(h);
+    P.stream = reinterpret_cast<cudaStream_t>(stream);
+    if (P.coarse_inner) P.coarse_inner->stream = P.stream;
   });
 }
 
@@ -261,6 +273,41 @@ int mx_set_preconditioner(mx_handle h, int kind) {
   });
 }
 
+int mx_set_coarse_solver(mx_handle h, int kind, const mx_dd_desc* dd, double tol, int max_it, int prec_kind) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    MX_REQUIRE(kind == MX_COARSE_DIRECT || kind == MX_COARSE_GMRES, MX_EINVAL, "unknown coarse solver");
+    MX_REQUIRE(P.coarse_m > 0, MX_EINVAL, "the handle has no coarse level");
+    if (kind == MX_COARSE_DIRECT) {
+      if (P.factored && !P.coarse_factored) {
+        MX_CUDA(cudaMemsetAsync(P.status.p, 0, 16, P.stream));
+        factor_coarse(P);
+        check_status(P);
+        P.coarse_factored = true;
+      }
+      delete P.coarse_inner;
+      P.coarse_inner = nullptr;
+      return;
+    }
+    MX_REQUIRE(dd, MX_EINVAL, "null subdomain description");
+    MX_REQUIRE(tol > 0 && tol < 1, MX_EINVAL, "inner tolerance must be in (0, 1)");
+    MX_REQUIRE(max_it >= 1 && max_it <= 1000, MX_EINVAL, "inner max_it must be in 1..1000");
+    MX_REQUIRE(prec_kind == MX_PREC_AS || prec_kind == MX_PREC_RAS, MX_EINVAL,
+               "the inner preconditioner is one-level AS or RAS");
+    MX_REQUIRE(prec_kind == MX_PREC_AS || dd->overlap_cells >= 1, MX_EINVAL,
+               "RAS needs an overlap of at least one cell");
+    std::unique_ptr<Problem> Q(create_problem(P.coarse_m, P.k, P.xi_prec, P.xi_prec, dd->core_cells,
+                                              dd->overlap_cells, 0, P.precision, P.stream));
+    Q->prec_kind = prec_kind;
+    if (P.factored) factor_problem(*Q);
+    delete P.coarse_inner;
+    P.coarse_inner = Q.release();
+    P.c_tol = tol;
+    P.c_max_it = max_it;
+  });
+}
+
 int mx_set_weighted_gmres(mx_handle h, int weighted) {
   return guard([&] {
     MX_REQUIRE(h, MX_EINVAL, "null handle");
@@ -301,6 +348,8 @@ int mx_solve(mx_handle h, const void* rhs, int nrhs, double tol, int restart, in
     const int64_t n = P.fine.n_dof;
     const size_t bytes = (size_t)nrhs * n * sizeof(double2);
     EventTimer t(P.stream);
+    P.timing.coarse_inner_iterations = 0;
+    P.timing.coarse_inner_solves = 0;
     DevView in(rhs, bytes, true, P.stream);
     DevView out(x, bytes, false, P.stream);
     const int batch = 32;
@@ -346,6 +395,8 @@ int mx_info(mx_handle h, mx_problem_info* out) {
     out->nnz_r0 = P.R0.nnz;
     out->factor_bytes = (int64_t)P.factors.bytes() + (int64_t)P.dinv.bytes() + (int64_t)P.panels.bytes() +
                         (int64_t)P.A0.bytes() + (int64_t)P.A0f.bytes() + (int64_t)P.A0inv.bytes();
+    if (const Problem* Q = P.coarse_inner)
+      out->factor_bytes += (int64_t)Q->factors.bytes() + (int64_t)Q->dinv.bytes() + (int64_t)Q->panels.bytes();
     out->coarse_band = P.coarse_band;
     out->precision = P.precision;
   });
@@ -361,6 +412,8 @@ int mx_timings(mx_handle h, mx_timing* out) {
     out->solve_launches = P.timing.solve_launches;
     out->restarts = P.timing.restarts;
     out->max_iterations = P.timing.max_iterations;
+    out->coarse_inner_iterations = P.timing.coarse_inner_iterations;
+    out->coarse_inner_solves = P.timing.coarse_inner_solves;
   });
 }
 

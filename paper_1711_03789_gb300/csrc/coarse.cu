@@ -280,11 +280,72 @@ __global__ void k_coarse_sum(int64_t count, int ks, const float2* part, float2* 
   }
 }
 
+__global__ void k_c128_to_c64(int64_t count, const double2* a, float2* b) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    b[t] = make_float2((float)a[t].x, (float)a[t].y);
+}
+
+// FP32 copy of the R^0 values (mixed-form restriction), made on first use
+static const float* r0_valf(Problem& P) {
+  if (P.R0_valf.n != (size_t)P.R0.nnz) {
+    P.R0_valf.alloc(P.R0.nnz);
+    MX_LAUNCH(k_to_f32v<<<grid_for(P.R0.nnz, 256), 256, 0, P.stream>>>(P.R0.nnz, P.R0.val.p, P.R0_valf.p));
+    MX_CHECK_LAUNCH();
+  }
+  return P.R0_valf.p;
+}
+
+// Inexact coarse solve (Sec. 6.4): y = result of the inner GMRES on A^0 y = R^0 v (y0 = 0,
+// relative tolerance c_tol, at most c_max_it iterations, unrestarted), preconditioned by the
+// inner problem's one-level Schwarz method. R^0 v is formed in FP64 (FP32 products in the
+// mixed form, whose coarse solve is c64 anyway); the inner iteration runs in the handle's
+// precision; a solution that misses c_tol after c_max_it iterations is used as it is. The
+// inner kernels are booked under coarse_gmres.
+static void coarse_solve_inner(Problem& P, const void* v, int vtype, double2* yc, int nrhs, double rb) {
+  cudaStream_t s = P.stream;
+  const int64_t nc = P.n_c;
+  P.c_rhs.ensure((size_t)nc * nrhs);
+  P.c_sol.ensure((size_t)nc * nrhs);
+  {
+    ProfScope ps(K_COARSE_RESTRICT, s, 1, rb, 4.0 * P.R0.nnz * nrhs);
+    if (P.precision == MX_MIXED)
+      MX_LAUNCH(k_coarse_restrict<double2, float><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
+          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, r0_valf(P), v, vtype, P.c_rhs.p));
+    else
+      MX_LAUNCH(k_coarse_restrict<double2, double><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
+          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, P.c_rhs.p));
+    MX_CHECK_LAUNCH();
+  }
+  Problem& Q = *P.coarse_inner;
+  Q.stream = s;
+  const int saved = prof_redirect(K_COARSE_GMRES);
+  try {
+    (void)gmres_solve(Q, P.c_rhs.p, P.c_sol.p, nrhs, P.c_tol, 0, P.c_max_it, nullptr);  // MX_ENOCONV allowed
+  } catch (...) {
+    prof_redirect(saved);
+    throw;
+  }
+  prof_redirect(saved);
+  P.timing.coarse_inner_iterations += Q.timing.max_iterations;
+  ++P.timing.coarse_inner_solves;
+  if (P.precision == MX_MIXED) {
+    MX_LAUNCH(k_c128_to_c64<<<grid_for(nc * nrhs, 256), 256, 0, s>>>(nc * nrhs, P.c_sol.p, reinterpret_cast<float2*>(yc)));
+    MX_CHECK_LAUNCH();
+  } else {
+    MX_CUDA(cudaMemcpyAsync(yc, P.c_sol.p, (size_t)nc * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  }
+}
+
 void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
   cudaStream_t s = P.stream;
   const int64_t nc = P.n_c;
   // R^0 (12 B per entry) and one gather of v per entry (worst case), output once
   const double rb = 12.0 * P.R0.nnz + 4.0 * nc + 16.0 * (double)P.R0.nnz * nrhs + 16.0 * nc * nrhs;
+  if (P.coarse_inner) {
+    coarse_solve_inner(P, v, vtype, yc, nrhs, rb);
+    return;
+  }
+  MX_REQUIRE(P.coarse_factored, MX_ENOTFACTORED, "the direct coarse factors are not built");
   const bool mixed = P.precision == MX_MIXED;
   const bool dense = mixed && P.A0inv.p;
   float2* rf = reinterpret_cast<float2*>(yc);  // c64 view of the workspace (mixed): the coarse solution
@@ -293,13 +354,8 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
   {
     ProfScope ps(K_COARSE_RESTRICT, s, 1, rb, 4.0 * P.R0.nnz * nrhs);
     if (mixed) {
-      if (P.R0_valf.n != (size_t)P.R0.nnz) {
-        P.R0_valf.alloc(P.R0.nnz);
-        MX_LAUNCH(k_to_f32v<<<grid_for(P.R0.nnz, 256), 256, 0, s>>>(P.R0.nnz, P.R0.val.p, P.R0_valf.p));
-        MX_CHECK_LAUNCH();
-      }
       MX_LAUNCH(k_coarse_restrict<float2, float><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
-          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0_valf.p, v, vtype, rin));
+          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, r0_valf(P), v, vtype, rin));
     } else {
       MX_LAUNCH(k_coarse_restrict<double2, double><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
           nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, yc));

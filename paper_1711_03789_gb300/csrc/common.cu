@@ -49,7 +49,8 @@ int64_t launch_count() { return g_launches.load(); }
 static const char* k_names[K_COUNT] = {
     "mesh", "subdomains", "assemble", "coarse_r0", "load_vector", "extract_minors", "lu_diag", "lu_panel",
     "lu_update", "coarse_lu", "local_solve", "coarse_restrict", "coarse_sweep", "scatter", "spmv",
-    "arnoldi_dots", "arnoldi_update", "arnoldi_small", "update_x", "residual", "layout", "coarse_inverse"};
+    "arnoldi_dots", "arnoldi_update", "arnoldi_small", "update_x", "residual", "layout", "coarse_inverse",
+    "coarse_gmres"};
 const char* kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? k_names[id] : ""; }
 
 struct Pending {
@@ -77,7 +78,16 @@ cudaEvent_t prof_event() {
   return g_pool[g_pool_used++];
 }
 
+static thread_local int g_prof_redirect = -1;
+
+int prof_redirect(int id) {
+  const int old = g_prof_redirect;
+  g_prof_redirect = id;
+  return old;
+}
+
 void prof_push(int id, cudaEvent_t a, cudaEvent_t b, int launches, double bytes, double flops) {
+  if (g_prof_redirect >= 0) id = g_prof_redirect;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_pending.push_back({id, launches, bytes, flops, a, b});
 }

@@ -46,11 +46,14 @@ void note_launch();
 enum KernelId {
   K_MESH = 0, K_SUBDOMAINS, K_ASSEMBLE, K_COARSE_R0, K_LOAD, K_EXTRACT, K_LU_DIAG, K_LU_PANEL,
   K_LU_UPDATE, K_COARSE_LU, K_LOCAL_SOLVE, K_COARSE_RESTRICT, K_COARSE_SWEEP, K_SCATTER, K_SPMV,
-  K_DOTS, K_ORTH_UPDATE, K_ARNOLDI_SMALL, K_UPDATE_X, K_RESIDUAL, K_LAYOUT, K_COARSE_INV, K_COUNT
+  K_DOTS, K_ORTH_UPDATE, K_ARNOLDI_SMALL, K_UPDATE_X, K_RESIDUAL, K_LAYOUT, K_COARSE_INV, K_COARSE_GMRES, K_COUNT
 };
 const char* kernel_name(int id);
 bool prof_enabled();
 void prof_push(int id, cudaEvent_t a, cudaEvent_t b, int launches, double bytes, double flops);
+// book every scope under `id` until restored (-1: each scope's own id); returns the previous
+// setting. Used to charge a nested solve (the inner coarse GMRES) to one entry.
+int prof_redirect(int id);
 cudaEvent_t prof_event();
 
 struct ProfScope {

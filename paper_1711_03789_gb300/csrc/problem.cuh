@@ -34,6 +34,7 @@ struct Timing {
   double build_ms = 0, factor_ms = 0, solve_ms = 0;
   int64_t solve_launches = 0;
   int restarts = 0, max_iterations = 0;
+  int64_t coarse_inner_iterations = 0, coarse_inner_solves = 0;
 };
 
 struct Workspace;  // solve buffers (krylov.cu)
@@ -130,6 +131,14 @@ struct Problem {
   DevBuf<float2> A0inv;
   DevBuf<float2> c_part;  // split-K partial products of the dense coarse apply
   DevBuf<int32_t> status; // [4] device error words: 0 local pivot, 1 coarse pivot, 2 timeout
+  bool coarse_factored = false;  // direct coarse factors built
+  // inexact coarse solve (Sec. 6.4): an inner GMRES on A^0 y = R^0 v, preconditioned by
+  // one-level Schwarz on subdomains of the coarse mesh -- a problem of its own, built on
+  // the coarse mesh with xi_prob = xi_prec of this one
+  Problem* coarse_inner = nullptr;
+  double c_tol = 0.1;
+  int c_max_it = 100;
+  DevBuf<double2> c_rhs, c_sol;  // [n_c][nrhs] R^0 v and the inner solution (FP64)
 
   Workspace* ws = nullptr;
   Timing timing;

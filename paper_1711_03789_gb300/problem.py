@@ -30,6 +30,15 @@ class Problem:
     def set_xi_prob(self, xi):
         L.mx_set_xi_prob(self.h, xi)
 
+    def set_preconditioner(self, kind):
+        L.mx_set_preconditioner(self.h, kind)
+
+    def set_weighted_gmres(self, weighted=True):
+        L.mx_set_weighted_gmres(self.h, weighted)
+
+    def set_coarse_solver(self, kind, core_cells=1, overlap_cells=1, tol=0.1, max_it=100, prec_kind=L.MX_PREC_RAS):
+        L.mx_set_coarse_solver(self.h, kind, core_cells, overlap_cells, tol, max_it, prec_kind)
+
     def factor(self):
         L.mx_factor(self.h)
         self.factored = True
