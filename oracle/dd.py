@@ -35,12 +35,21 @@ Readings:
     preconditioner is the one-level ImpRAS (impedance conditions on the subdomain
     boundaries); here the subdomain problems keep the PEC conditions of Eq. 3.1 (one-level
     RAS or AS).
+  * impedance problems (Eq. imp, mesh bc "imp"): the local problems are those of ImpRAS
+    (Sec. 6.3): the Maxwell problem on the box with the impedance condition on its whole
+    boundary -- on the part inside the domain by the definition of ImpRAS, on the part on
+    the domain boundary because the global problem has it there. The local DOFs are then all
+    edges of the closed box (its faces included), and A^l is the Galerkin matrix of the box:
+    element matrices of the tetrahedra inside the box, minus i sign(xi) k times the
+    tangential mass of the box-surface triangles (not a minor of A). The additive, restricted
+    and hybrid forms are built from these local solves as before (ImpAS, ImpRAS, ImpHRAS,
+    ADEF1-ImpRAS); the coarse problem is the impedance problem on the coarse mesh.
 """
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .mesh import KuhnMesh, vertex_ijk, DIRS, LOCAL_EDGES
+from .mesh import KuhnMesh, vertex_ijk, boundary_faces, DIRS, LOCAL_EDGES
 from . import fem
 
 
@@ -61,11 +70,14 @@ def subdomain_boxes(n, core, overlap):
     return boxes
 
 
-def local_dofs(mesh, lo, hi):
-    """Sorted global DOFs of the box [lo, hi] (vertex indices), Eq. 3.1 reading."""
+def local_dofs(mesh, lo, hi, closed=False):
+    """Sorted global DOFs of the box [lo, hi] (vertex indices), Eq. 3.1 reading; closed:
+    the edges on the box faces included (impedance local problems)."""
     a = vertex_ijk(mesh.dof_edges[:, 0], mesh.n)
     b = vertex_ijk(mesh.dof_edges[:, 1], mesh.n)
     inside = np.all((a >= lo) & (a <= hi) & (b >= lo) & (b <= hi), axis=1)
+    if closed:
+        return np.nonzero(inside)[0]
     on_face = np.zeros_like(inside)
     for ax in range(3):
         for val in (lo[ax], hi[ax]):
@@ -134,19 +146,22 @@ class Schwarz:
 
     def __init__(self, mesh, A_prec, core, overlap, coarse_m=0, k=None, xi_prec=None):
         self.mesh = mesh
+        self.imp = getattr(mesh, "bc", "pec") == "imp"
+        self.k, self.xi_prec = k, xi_prec
         self.core, self.overlap = core, overlap
         self.boxes = subdomain_boxes(mesh.n, core, overlap)
-        self.idx = [local_dofs(mesh, lo, hi) for lo, hi in self.boxes]
+        self.idx = [local_dofs(mesh, lo, hi, closed=self.imp) for lo, hi in self.boxes]
         self.A_prec = A_prec.tocsr()
         self.lus = None
         self.coarse = None
         self.inner = None  # one-level Schwarz on the coarse mesh (inexact coarse solve)
         if coarse_m:
-            cm = KuhnMesh(coarse_m)
+            cm = KuhnMesh(coarse_m, "imp" if self.imp else "pec")
             Kc, Mc = fem.assemble_KM(cm)
             self.coarse_mesh = cm
             self.R0 = coarse_restriction(mesh, cm)
-            self.A0 = fem.a_xi(Kc, Mc, k, xi_prec)  # Galerkin matrix on Q_H (Eq. 3.3, l = 0)
+            # Galerkin matrix on Q_H (Eq. 3.3, l = 0), with the boundary term when impedance
+            self.A0 = fem.a_xi(Kc, Mc, k, xi_prec, fem.assemble_B(cm) if self.imp else None)
 
     def owner(self):
         """Owning subdomain of every DOF: the core box holding the edge midpoint."""
@@ -164,9 +179,35 @@ class Schwarz:
         return [own[i] == l for l, i in enumerate(self.idx)]
 
     def minor(self, l):
-        """A^l = R^l A (R^l)^T (Eq. 3.3) as a sparse matrix."""
+        """A^l = R^l A (R^l)^T (Eq. 3.3) as a sparse matrix; for impedance problems the
+        Galerkin matrix of the box with the impedance condition on its boundary."""
         i = self.idx[l]
+        if self.imp:
+            return self.box_matrix(l)
         return self.A_prec[i][:, i]
+
+    def box_matrix(self, l):
+        """ImpRAS local matrix (Sec. 6.3): K - (k^2 + i xi) M - i sign(xi) k B assembled over
+        the tetrahedra inside box l and the triangles on its surface, on its closed-box DOFs."""
+        mesh, (lo, hi) = self.mesh, self.boxes[l]
+        idx = self.idx[l]
+        ijk = vertex_ijk(mesh.tets, mesh.n)
+        inside = np.all((ijk >= lo) & (ijk <= hi), axis=(1, 2))
+        tets = mesh.tets[inside]
+        Ke, Me = fem.element_matrices(mesh.coords(tets))
+        d = np.searchsorted(idx, mesh.tet2dof[inside])
+        nl = len(idx)
+        rows = np.repeat(d[:, :, None], 6, axis=2).ravel()
+        cols = np.repeat(d[:, None, :], 6, axis=1).ravel()
+        K = sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(nl, nl)).tocsr()
+        M = sp.coo_matrix((Me.ravel(), (rows, cols)), shape=(nl, nl)).tocsr()
+        faces = boundary_faces(tets, mesh.n, tuple(lo), tuple(hi))
+        Be = fem.face_matrices(mesh.coords(faces))
+        fd = np.stack([np.searchsorted(idx, mesh.dof_of_pairs(faces[:, a], faces[:, b]))
+                       for a, b in fem.FACE_EDGES], axis=1)
+        B = sp.coo_matrix((Be.ravel(), (np.repeat(fd[:, :, None], 3, axis=2).ravel(),
+                                        np.repeat(fd[:, None, :], 3, axis=1).ravel())), shape=(nl, nl)).tocsr()
+        return fem.a_xi(K, M, self.k, self.xi_prec, B)
 
     def set_inner_coarse(self, core, overlap, tol=0.1, max_it=100, kind="ras"):
         """Solve the coarse problem inexactly by inner GMRES (Sec. 6.4), preconditioned by
@@ -174,7 +215,7 @@ class Schwarz:
         `overlap` coarse cells."""
         if not hasattr(self, "A0"):
             raise ValueError("no coarse level")
-        self.inner = Schwarz(self.coarse_mesh, self.A0, core, overlap)
+        self.inner = Schwarz(self.coarse_mesh, self.A0, core, overlap, k=self.k, xi_prec=self.xi_prec)
         self.inner_tol, self.inner_max_it, self.inner_kind = tol, max_it, kind
         self.inner_its = []  # inner iterations of every coarse solve, in order
 

@@ -17,6 +17,16 @@ Readings:
     weight = W_u W_v W_w (1-u)^2 (1-v); reference vertex m <-> path vertex P_m.
     q = 3 is the default (exact for total degree 3).
 
+  * impedance boundary condition (Eq. imp): curl E x n - i sign(xi) k (n x E) x n = 0 on
+    the boundary. Integrating curl curl E . v by parts leaves the boundary integral
+    int (n x curl E) . v = -i sign(xi) k int E_T . v_T, so
+    A_xi = K - (k^2 + i xi) M - i sign(xi) k B, B_ij = int_{boundary} (w_j)_T . (w_i)_T.
+    sign(0) is read as +1 (the paper runs the impedance problem with xi = 0; +1 is the
+    outgoing condition for the time dependence exp(-i omega t) of Sec. 1.1). On a boundary
+    triangle the tangential trace of w_pq is the triangle's own Whitney form
+    lam_p grad_F lam_q - lam_q grad_F lam_p (grad_F the surface gradient, the tangential
+    part of the tetrahedron's gradient), with int_F lam_i lam_j = |F| (1 + delta_ij) / 12.
+
 Element matrices are computed per tetrahedron from its vertex coordinates
 (barycentric gradients by inverting the 4x4 affine system), not from a closed form.
 """
@@ -97,9 +107,58 @@ def assemble_full_KM(mesh):
     return K, M
 
 
-def a_xi(K, M, k, xi):
-    """A_xi = K - (k^2 + i xi) M (Eq. 2.2 with the real Whitney basis)."""
-    return (K.astype(np.complex128) - (k * k + 1j * xi) * M.astype(np.complex128)).tocsr()
+FACE_EDGES = [(0, 1), (0, 2), (1, 2)]
+
+
+def face_matrices(P):
+    """Tangential Whitney mass B_F [F, 3, 3] of triangles P [F, 3, 3] (vertex coordinates,
+    vertices in increasing id order, edges (0,1), (0,2), (1,2) oriented low -> high).
+    Surface gradients from the 2x2 metric of the edge vectors."""
+    E = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]], axis=2)  # [F, 3, 2]
+    Gm = np.einsum("fia,fib->fab", E, E)
+    W = E @ np.linalg.inv(Gm)  # columns: grad lam_1, grad lam_2 (in the plane)
+    g1, g2 = W[:, :, 0], W[:, :, 1]
+    G = [-(g1 + g2), g1, g2]
+    area = 0.5 * np.linalg.norm(np.cross(E[:, :, 0], E[:, :, 1]), axis=1)
+    mass = lambda i, j: area * (1.0 + (i == j)) / 12.0
+    dot = lambda i, j: np.einsum("fi,fi->f", G[i], G[j])
+    B = np.empty((P.shape[0], 3, 3))
+    for a, (p, q) in enumerate(FACE_EDGES):
+        for b, (r, s) in enumerate(FACE_EDGES):
+            B[:, a, b] = (dot(q, s) * mass(p, r) - dot(q, r) * mass(p, s)
+                          - dot(p, s) * mass(q, r) + dot(p, r) * mass(q, s))
+    return B
+
+
+def assemble_B(mesh, faces=None):
+    """Boundary mass B over the mesh DOFs from the given triangles (default: the boundary
+    of the unit cube). Edges without a DOF are skipped."""
+    from .mesh import boundary_faces
+    if faces is None:
+        faces = boundary_faces(mesh.tets, mesh.n)
+    Be = face_matrices(mesh.coords(faces))
+    d = np.stack([mesh.dof_of_pairs(faces[:, a], faces[:, b]) for a, b in FACE_EDGES], axis=1)
+    rows = np.repeat(d[:, :, None], 3, axis=2)
+    cols = np.repeat(d[:, None, :], 3, axis=1)
+    keep = (rows >= 0) & (cols >= 0)
+    B = sp.coo_matrix((Be[keep], (rows[keep], cols[keep])), shape=(mesh.n_dof, mesh.n_dof)).tocsr()
+    B.sum_duplicates()
+    B.sort_indices()
+    return B
+
+
+def imp_sign(xi):
+    """sign(xi) of Eq. imp with sign(0) = +1."""
+    return -1.0 if xi < 0 else 1.0
+
+
+def a_xi(K, M, k, xi, B=None):
+    """A_xi = K - (k^2 + i xi) M (Eq. 2.2 with the real Whitney basis), minus
+    i sign(xi) k B with the impedance condition (Eq. imp)."""
+    A = K.astype(np.complex128) - (k * k + 1j * xi) * M.astype(np.complex128)
+    if B is not None:
+        A = A - 1j * imp_sign(xi) * k * B.astype(np.complex128)
+    return A.tocsr()
 
 
 def gauss_legendre01(q):

@@ -17,6 +17,9 @@ Readings where the paper is silent (it used FreeFem++ meshes):
     those DOFs are removed.
   * DOF numbering: interior edges sorted by key 7 * v_low + d, d the index of
     v_high - v_low in DIRS.
+  * impedance boundary condition (Eq. imp, bc="imp"): the condition is natural, so every
+    edge of the mesh carries a DOF (same key order); the boundary enters the matrix
+    through the boundary triangles (fem.assemble_B).
 
 This module derives everything from the tetrahedra by brute force (unique vertex
 pairs), not from a per-vertex enumeration.
@@ -93,16 +96,20 @@ def is_pec_edge(pairs, n):
 
 
 class KuhnMesh:
-    """Mesh, edges and DOF numbering for n cells per side."""
+    """Mesh, edges and DOF numbering for n cells per side; bc "pec" (Eq. 1.4: boundary
+    edges carry no DOF) or "imp" (Eq. imp: every edge is a DOF)."""
 
-    def __init__(self, n):
+    def __init__(self, n, bc="pec"):
+        if bc not in ("pec", "imp"):
+            raise ValueError(bc)
         self.n = int(n)
         self.h = 1.0 / n
+        self.bc = bc
         self.tets = kuhn_tets(n)
         self.edges = all_edges(self.tets)  # [E, 2], sorted by (low, high)
         self.edge_dir = edge_dir(self.edges, n)
         self.key = 7 * self.edges[:, 0] + self.edge_dir
-        interior = ~is_pec_edge(self.edges, n)
+        interior = ~is_pec_edge(self.edges, n) if bc == "pec" else np.ones(self.edges.shape[0], dtype=bool)
         order = np.argsort(self.key[interior], kind="stable")
         self.dof_edges = self.edges[interior][order]  # [n_dof, 2]
         self.dof_key = self.key[interior][order]
@@ -131,6 +138,31 @@ class KuhnMesh:
             pairs = np.stack([lo, hi], axis=1)
             out[:, k] = lut[7 * lo + edge_dir(pairs, self.n)]
         return out
+
+
+def boundary_faces(tets, n, lo=(0, 0, 0), hi=None):
+    """Triangles of the given tetrahedra lying on a face of the box [lo, hi] (vertex
+    indices; default the unit cube): [F, 3] vertex ids in increasing order. Found by brute
+    force: a tetrahedron face whose three vertices share a coordinate equal to a box bound."""
+    hi = (n, n, n) if hi is None else hi
+    out = []
+    for t in tets:
+        for drop in range(4):
+            f = np.sort(np.delete(t, drop))
+            ijk = vertex_ijk(f, n)
+            for ax in range(3):
+                col = ijk[:, ax]
+                if np.all(col == col[0]) and col[0] in (lo[ax], hi[ax]):
+                    out.append(f)
+                    break
+    return np.array(out, dtype=np.int64).reshape(-1, 3)
+
+
+def count_closed_box_edges(a, b, c):
+    """Closed form for all edges of an a x b x c Kuhn box (its faces included): per
+    direction D the number of start vertices, prod over axes of (len + 1 - D)."""
+    L = (a, b, c)
+    return int(sum(np.prod([L[ax] + 1 - D[ax] for ax in range(3)]) for D in DIRS))
 
 
 def count_all_edges(n):

@@ -13,15 +13,17 @@ class Problem:
     """curl curl E - (k^2 + i xi_prob) E = F, PEC, preconditioned by AS built from
     A_{xi_prec} (Sec. 6.2: B^{-1}_{xi_prec} preconditions A_{xi_prob})."""
 
-    def __init__(self, n, k, xi_prob, xi_prec, core, overlap, coarse_m=0, kind="as", inner_coarse=None):
+    def __init__(self, n, k, xi_prob, xi_prec, core, overlap, coarse_m=0, kind="as", inner_coarse=None, bc="pec"):
         """inner_coarse: None (direct coarse solve) or a dict with core, overlap, tol, max_it,
-        kind of the inner GMRES coarse solve (Sec. 6.4); the outer GMRES is then flexible."""
+        kind of the inner GMRES coarse solve (Sec. 6.4); the outer GMRES is then flexible.
+        bc: "pec" (Eq. 1.4) or "imp" (Eq. imp; local problems with impedance conditions)."""
         self.kind = kind  # "as" (Eq. 3.4), "ras" (Eq. RAS2), "hras" (Eq. HRAS), "adef1" (Eq. ADEF1ras)
-        self.mesh = KuhnMesh(n)
+        self.mesh = KuhnMesh(n, bc)
         self.k, self.xi_prob, self.xi_prec = k, xi_prob, xi_prec
         self.K, self.M = fem.assemble_KM(self.mesh)
-        self.A = fem.a_xi(self.K, self.M, k, xi_prob)
-        self.A_prec = fem.a_xi(self.K, self.M, k, xi_prec)
+        self.B = fem.assemble_B(self.mesh) if bc == "imp" else None
+        self.A = fem.a_xi(self.K, self.M, k, xi_prob, self.B)
+        self.A_prec = fem.a_xi(self.K, self.M, k, xi_prec, self.B)
         self.dd = dd.Schwarz(self.mesh, self.A_prec, core, overlap, coarse_m, k, xi_prec)
         self.flexible = inner_coarse is not None
         if inner_coarse is not None:
