@@ -138,7 +138,8 @@ def run_ours(args, W, rank, world):
     centres, pol = inputs.bump_batch(1 + 1000 * rank, nrhs)
 
     def step(host):
-        P = mx.Problem(W["n"], k, xp, xq, W["core"], W["overlap"], W["coarse"], prec, stream=stream.cuda_stream)
+        P = mx.Problem(W["n"], k, xp, xq, W["core"], W["overlap"], W["coarse"], prec, stream=stream.cuda_stream,
+                       bc=mx.MX_BC_IMPEDANCE if args.bc == "imp" else mx.MX_BC_PEC)
         if args.local_tensor is not None:
             mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, args.local_tensor)
         if args.weighted:
@@ -403,6 +404,8 @@ def main():
                     help="Schwarz variant: additive (Eq. 3.4), restricted, hybrid, adapted deflation (Sec. 6.3)")
     ap.add_argument("--weighted", action="store_true",
                     help="weighted GMRES in the D_k = K + k^2 M inner product (Sec. 5.2)")
+    ap.add_argument("--bc", default="pec", choices=["pec", "imp"],
+                    help="boundary condition: PEC (Eq. 1.4) or impedance (Eq. imp) with ImpRAS local problems")
     ap.add_argument("--coarse-gmres", type=int, default=0, metavar="CORE",
                     help="solve the coarse problem by inner GMRES (Sec. 6.4) on subdomains of CORE coarse cells")
     ap.add_argument("--coarse-tol", type=float, default=0.1)
@@ -437,6 +440,7 @@ def main():
               "coarse_cells": W["coarse"], "nrhs_per_gpu": W["nrhs"], "gmres_restart": W["restart"],
               "max_it": W["max_it"], "tol": W["tol"], "form": args.form, "preconditioner": args.precond,
               "gmres_inner_product": "D_k" if args.weighted else "euclidean",
+              "boundary": "impedance (ImpRAS local problems)" if args.bc == "imp" else "pec",
               "coarse_solver": ({"kind": "inner_gmres", "core_cells": args.coarse_gmres, "overlap_cells": 1,
                                  "tol": args.coarse_tol, "max_it": args.coarse_max_it,
                                  "preconditioner": args.coarse_inner} if args.coarse_gmres else "direct"),
@@ -517,7 +521,7 @@ def main():
                     for k, v in sorted(r["prof"].items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
         "clocks": r["clocks"],
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.bc == "pec":
         line["cpu_baseline"] = cpu_baseline(W, iters)
     print(json.dumps(line))
     if world > 1:

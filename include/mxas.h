@@ -45,8 +45,22 @@ extern "C" {
 #define MX_ECUDA (-7)         /* a CUDA runtime error; see mx_last_error() */
 
 /* Mesh: the unit cube split into n_cells^3 cubes, each cut into 6 Kuhn tetrahedra
- * (Sec. 2.2; uniform mesh and Kuhn split are this library's reading). */
-typedef struct { int n_cells; } mx_mesh_desc;
+ * (Sec. 2.2; uniform mesh and Kuhn split are this library's reading).
+ * boundary: MX_BC_PEC (Eq. 1.4; the edges on the boundary carry no DOF) or
+ * MX_BC_IMPEDANCE (Eq. imp: curl E x n - i sign(xi) k (n x E) x n = 0 with sign(0) = +1;
+ * every edge is a DOF and A_xi = K - (k^2 + i xi) M - i sign(xi) k B, B the tangential
+ * Whitney mass of the boundary triangles). With MX_BC_IMPEDANCE the local problems of the
+ * preconditioner are those of ImpRAS (Sec. 6.3): the Maxwell problem on each closed
+ * subdomain box with the impedance condition on the whole box boundary, on the DOFs of
+ * all edges of the closed box; every preconditioner variant is built from them (ImpAS,
+ * ImpRAS, ImpHRAS, ADEF1-ImpRAS), and the coarse problem is the impedance problem on the
+ * coarse mesh. */
+#define MX_BC_PEC 0
+#define MX_BC_IMPEDANCE 1
+typedef struct {
+  int n_cells;
+  int boundary;
+} mx_mesh_desc;
 
 /* Overlapping subdomains (Sec. 3.1, Sec. 6.1): boxes of core_cells^3 cells widened by
  * overlap_cells on each side, clipped to the cube. */
@@ -180,13 +194,16 @@ MX_API int mx_set_coarse_solver(mx_handle h, int kind, const mx_dd_desc* dd, dou
 MX_API const char* mx_last_error(void);
 
 /* Assemble the problem (Sec. 2.2, Eq. 2.2; Sec. 3, Eq. 3.1-3.3):
- * Kuhn mesh and PEC-interior edge numbering, CSR K and M (real FP64) with
- * A_xi = K - (k^2 + i xi) M, subdomain index lists, and (two-level) the coarse mesh,
- * its Galerkin matrix A^0_{xi_prec} and the restriction R^0 of Eq. 3.2.
+ * Kuhn mesh and edge numbering (PEC-interior edges, or all edges with the impedance
+ * condition), CSR K and M (real FP64; and B with the impedance condition) with
+ * A_xi = K - (k^2 + i xi) M [- i sign(xi) k B], subdomain index lists, and (two-level) the
+ * coarse mesh, its Galerkin matrix A^0_{xi_prec} and the restriction R^0 of Eq. 3.2.
  * The preconditioner uses xi_prec, the operator xi_prob (Sec. 6.2).
- * Returns MX_EINVAL for n_cells < 1, core_cells < 1, overlap_cells < 0, k <= 0,
- * xi_prec == 0 (local matrices are only guaranteed invertible for xi != 0, Sec. 3.3)
- * or a coarse n_cells that does not divide the fine one. *out is set on success only. */
+ * Returns MX_EINVAL for n_cells < 1, core_cells < 1, overlap_cells < 0, k <= 0, an unknown
+ * boundary, xi_prec == 0 with PEC (local matrices are only guaranteed invertible for
+ * xi != 0, Sec. 3.3; the impedance local problems are well posed for xi = 0, as the
+ * paper's Table 7 uses) or a coarse n_cells that does not divide the fine one. *out is
+ * set on success only. */
 MX_API int mx_build_problem(const mx_mesh_desc* mesh, double k, double xi_prob, double xi_prec,
                      const mx_dd_desc* dd, const mx_coarse_desc* coarse, int precision,
                      mx_handle* out);
@@ -252,6 +269,10 @@ MX_API int mx_get_subdomains(mx_handle h, int64_t* offsets, int32_t* lists, int3
 /* CSR of K and M (which = 0 fine, 1 coarse), host outputs rowptr [rows + 1],
  * col [nnz], K [nnz], M [nnz] (FP64). Any pointer may be NULL. */
 MX_API int mx_get_csr(mx_handle h, int which, int32_t* rowptr, int32_t* col, double* K, double* M);
+
+/* Values of the boundary mass B (Eq. imp) on the same CSR pattern as mx_get_csr (which = 0
+ * fine, 1 coarse), host output B [nnz]; zeros for a PEC problem. */
+MX_API int mx_get_boundary_mass(mx_handle h, int which, double* B);
 
 /* R^0 of Eq. 3.2 as CSR [n_coarse x n_dof], host outputs. */
 MX_API int mx_get_coarse_restriction(mx_handle h, int32_t* rowptr, int32_t* col, double* val);

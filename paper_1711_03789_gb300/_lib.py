@@ -25,7 +25,7 @@ class MxError(RuntimeError):
 
 
 class MeshDesc(C.Structure):
-    _fields_ = [("n_cells", C.c_int)]
+    _fields_ = [("n_cells", C.c_int), ("boundary", C.c_int)]
 
 
 class DdDesc(C.Structure):
@@ -80,6 +80,7 @@ _sig = {
     "mx_get_mesh": (C.c_int, [H, P, P]),
     "mx_get_subdomains": (C.c_int, [H, P, P, P, P]),
     "mx_get_csr": (C.c_int, [H, C.c_int, P, P, P, P]),
+    "mx_get_boundary_mass": (C.c_int, [H, C.c_int, P]),
     "mx_get_coarse_restriction": (C.c_int, [H, P, P, P]),
     "mx_spmv": (C.c_int, [H, P, P, C.c_int]),
     "mx_precond": (C.c_int, [H, P, P, C.c_int, C.c_int]),
@@ -133,10 +134,13 @@ def mx_last_error():
     return lib.mx_last_error().decode()
 
 
+MX_BC_PEC, MX_BC_IMPEDANCE = 0, 1
+
+
 def mx_build_problem(n_cells, k, xi_prob, xi_prec, core_cells=5, overlap_cells=1, coarse_cells=0,
-                     precision=MX_MIXED):
+                     precision=MX_MIXED, bc=MX_BC_PEC):
     h = H()
-    _check(lib.mx_build_problem(C.byref(MeshDesc(n_cells)), k, xi_prob, xi_prec,
+    _check(lib.mx_build_problem(C.byref(MeshDesc(n_cells, bc)), k, xi_prob, xi_prec,
                                 C.byref(DdDesc(core_cells, overlap_cells)), C.byref(CoarseDesc(coarse_cells)),
                                 precision, C.byref(h)))
     return h
@@ -266,6 +270,14 @@ def mx_get_csr(h, which=0):
     M = np.empty(nnz)
     _check(lib.mx_get_csr(h, which, None, _ptr(col), _ptr(K), _ptr(M)))
     return rowptr, col, K, M
+
+
+def mx_get_boundary_mass(h, which=0):
+    """B values on the pattern of mx_get_csr(h, which) (zeros with PEC)."""
+    rowptr = mx_get_csr(h, which)[0]
+    B = np.empty(int(rowptr[-1]))
+    _check(lib.mx_get_boundary_mass(h, which, _ptr(B)))
+    return B
 
 
 def mx_get_coarse_restriction(h):

@@ -126,13 +126,15 @@ void transpose_to_user(const double2* in, double2* user, int64_t n, int nrhs, cu
 }
 
 Problem* create_problem(int n, double k, double xi_prob, double xi_prec, int core, int overlap, int cm, int precision,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, int bc) {
+  MX_REQUIRE(bc == MX_BC_PEC || bc == MX_BC_IMPEDANCE, MX_EINVAL, "unknown boundary condition");
+  const bool imp = bc == MX_BC_IMPEDANCE;
   MX_REQUIRE(n >= 1 && n <= 256, MX_EINVAL, "n_cells must be in 1..256");
   MX_REQUIRE(core >= 1, MX_EINVAL, "core_cells must be >= 1");
   MX_REQUIRE(overlap >= 0 && overlap <= 6 * core, MX_EINVAL, "overlap_cells must be in 0..6*core_cells");
   MX_REQUIRE(k > 0 && std::isfinite(k), MX_EINVAL, "k must be > 0");
-  MX_REQUIRE(xi_prec != 0 && std::isfinite(xi_prec) && std::isfinite(xi_prob), MX_EINVAL,
-             "xi_prec must be nonzero and finite");
+  MX_REQUIRE((imp || xi_prec != 0) && std::isfinite(xi_prec) && std::isfinite(xi_prob), MX_EINVAL,
+             "xi_prec must be finite, and nonzero with PEC");
   MX_REQUIRE(precision == MX_MIXED || precision == MX_PLAIN_FP64, MX_EINVAL, "unknown precision");
   MX_REQUIRE(cm >= 0 && (cm == 0 || n % cm == 0), MX_EINVAL, "coarse n_cells must divide the fine n_cells");
   auto P = new Problem();
@@ -145,18 +147,19 @@ Problem* create_problem(int n, double k, double xi_prob, double xi_prec, int cor
     P->overlap = overlap;
     P->coarse_m = cm;
     P->precision = precision;
+    P->bc = bc;
     P->stream = stream;
     P->status.alloc(4);
     MX_CUDA(cudaMemsetAsync(P->status.p, 0, 16, P->stream));
     EventTimer t(P->stream);
-    build_mesh(P->fine, P->n, P->stream);
+    build_mesh(P->fine, P->n, P->stream, imp);
     MX_REQUIRE(P->fine.n_dof > 0, MX_EINVAL, "mesh has no interior edge");
-    assemble_KM(P->fine, P->A, P->stream);
+    assemble_KM(P->fine, P->A, P->stream, imp);
     build_subdomains(*P);
     if (cm) {
-      build_mesh(P->coarse, cm, P->stream);
+      build_mesh(P->coarse, cm, P->stream, imp);
       MX_REQUIRE(P->coarse.n_dof > 0, MX_EINVAL, "coarse mesh has no interior edge (use n_cells >= 2)");
-      assemble_KM(P->coarse, P->Ac, P->stream);
+      assemble_KM(P->coarse, P->Ac, P->stream, imp);
       build_coarse_restriction(*P);
       P->n_c = P->coarse.n_dof;
     }
@@ -203,7 +206,7 @@ int mx_build_problem(const mx_mesh_desc* mesh, double k, double xi_prob, double 
   return guard([&] {
     MX_REQUIRE(mesh && dd && out, MX_EINVAL, "null descriptor");
     Problem* P = create_problem(mesh->n_cells, k, xi_prob, xi_prec, dd->core_cells, dd->overlap_cells,
-                                coarse ? coarse->n_cells : 0, precision, nullptr);
+                                coarse ? coarse->n_cells : 0, precision, nullptr, mesh->boundary);
     *out = reinterpret_cast<mx_handle>(P);
   });
 }
@@ -298,7 +301,7 @@ int mx_set_coarse_solver(mx_handle h, int kind, const mx_dd_desc* dd, double tol
     MX_REQUIRE(prec_kind == MX_PREC_AS || dd->overlap_cells >= 1, MX_EINVAL,
                "RAS needs an overlap of at least one cell");
     std::unique_ptr<Problem> Q(create_problem(P.coarse_m, P.k, P.xi_prec, P.xi_prec, dd->core_cells,
-                                              dd->overlap_cells, 0, P.precision, P.stream));
+                                              dd->overlap_cells, 0, P.precision, P.stream, P.bc));
     Q->prec_kind = prec_kind;
     if (P.factored) factor_problem(*Q);
     delete P.coarse_inner;
@@ -454,6 +457,17 @@ int mx_get_csr(mx_handle h, int which, int32_t* rowptr, int32_t* col, double* K,
     if (col) MX_CUDA(cudaMemcpy(col, A.col.p, A.nnz * 4, cudaMemcpyDeviceToHost));
     if (K) MX_CUDA(cudaMemcpy(K, A.K.p, A.nnz * 8, cudaMemcpyDeviceToHost));
     if (M) MX_CUDA(cudaMemcpy(M, A.M.p, A.nnz * 8, cudaMemcpyDeviceToHost));
+  });
+}
+
+int mx_get_boundary_mass(mx_handle h, int which, double* B) {
+  return guard([&] {
+    MX_REQUIRE(h && B && (which == 0 || which == 1), MX_EINVAL, "bad arguments");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    MX_REQUIRE(which == 0 || P.coarse_m, MX_EINVAL, "no coarse space");
+    CsrKM& A = which == 0 ? P.A : P.Ac;
+    if (A.B.p) MX_CUDA(cudaMemcpy(B, A.B.p, A.nnz * 8, cudaMemcpyDeviceToHost));
+    else std::memset(B, 0, A.nnz * 8);
   });
 }
 

@@ -13,6 +13,14 @@
 // Rows are assembled by gathering over the tetrahedra around each edge in a fixed order
 // (no atomics), the integer parts are summed exactly and scaled once, so K and M are
 // deterministic and exact up to that single rounding.
+//
+// Impedance condition (Eq. imp): B_ij = int_{boundary} (w_j)_T . (w_i)_T over the boundary
+// triangles. On a triangle in a plane normal to axis a the tangential trace of w_pq is the
+// triangle's Whitney form with the surface gradients g_i / h with their a-components
+// dropped, int_F lam_i lam_j = |F| (1 + delta_ij) / 12 and |F| = h^2 / 2, so
+//   B_F[(pq),(rs)] = (1 / 24) [ same bracket as M_e with the projected g ],
+// independent of h. The same row gather restricted to a box (tetrahedra inside it,
+// triangles on its surface) gives the ImpRAS local matrices (Sec. 6.3).
 #include "problem.cuh"
 
 namespace mx {
@@ -67,14 +75,26 @@ __device__ inline int ledge_index(int a, int b) {
   return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
-// Tetrahedra containing the edge from vertex c (grid coords) with direction d, in a fixed
-// order (cubes in z, y, x order of their corner offsets, then permutations). Writes
-// tet ids and the local edge index of the edge in each. Returns the count (<= 6).
-__device__ inline int edge_tets(int n, const int* c, int d, int64_t* tets, int* loc) {
+// Boundary-mass integer of local edges ea, eb on a tetrahedron face normal to axis ax.
+__device__ inline int face_int(int p, int ea, int eb, int ax) {
+  int g[4][3];
+  kuhn_grads(p, g);
+  for (int i = 0; i < 4; ++i) g[i][ax] = 0;
+  const int P = a_ledge[ea][0], Q = a_ledge[ea][1], R = a_ledge[eb][0], S = a_ledge[eb][1];
+  return idot(g[Q], g[S]) * (1 + (P == R)) - idot(g[Q], g[R]) * (1 + (P == S)) -
+         idot(g[P], g[S]) * (1 + (Q == R)) + idot(g[P], g[R]) * (1 + (Q == S));
+}
+
+// Tetrahedra containing the edge from vertex c (grid coords) with direction d whose cube
+// lies in the box of vertices [blo, bhi], in a fixed order (cubes in z, y, x order of their
+// corner offsets, then permutations). Writes tet ids and the local edge index of the edge
+// in each. Returns the count (<= 6).
+__device__ inline int edge_tets(int n, const int* c, int d, int64_t* tets, int* loc, const int* blo,
+                                const int* bhi) {
   int lo[3], hi[3];
   for (int a = 0; a < 3; ++a) {
     if (a_dirs[d][a]) { lo[a] = c[a]; hi[a] = c[a]; }
-    else { lo[a] = max(c[a] - 1, 0); hi[a] = min(c[a], n - 1); }
+    else { lo[a] = max(c[a] - 1, blo[a]); hi[a] = min(c[a], bhi[a] - 1); }
   }
   int k = 0;
   for (int z = lo[2]; z <= hi[2]; ++z)
@@ -102,10 +122,75 @@ __device__ inline void key_to_coords(int32_t key, int n, int* c, int& d) {
   c[2] = (int)(v / ((int64_t)(n + 1) * (n + 1)));
 }
 
+// One row of the integer Galerkin parts: sorted column DOFs and the K, M, B integers.
+struct RowInts {
+  int m = 0;
+  int32_t cols[36];
+  int ik[36], im[36], ib[36];
+  __device__ void add(int32_t cd, int kk, int mm, int bb) {
+    // insert in column order, merging duplicates (integer sums are exact)
+    int j = 0;
+    while (j < m && cols[j] < cd) ++j;
+    if (j < m && cols[j] == cd) {
+      ik[j] += kk;
+      im[j] += mm;
+      ib[j] += bb;
+    } else {
+      for (int s = m; s > j; --s) { cols[s] = cols[s - 1]; ik[s] = ik[s - 1]; im[s] = im[s - 1]; ib[s] = ib[s - 1]; }
+      cols[j] = cd; ik[j] = kk; im[j] = mm; ib[j] = bb;
+      ++m;
+    }
+  }
+};
+
+// Row of the edge (c, d) over the tetrahedra inside the box [blo, bhi] and, with `faces`,
+// the triangles on the box surface (each met once: its other tetrahedron is outside).
+__device__ inline void row_ints(int n, const int* c, int d, const int* blo, const int* bhi, bool faces,
+                                const int32_t* tet2dof, RowInts& R) {
+  int64_t tets[6];
+  int loc[6];
+  const int nt = edge_tets(n, c, d, tets, loc, blo, bhi);
+  for (int t = 0; t < nt; ++t) {
+    const int p = (int)(tets[t] % 6);
+    for (int eb = 0; eb < 6; ++eb) {
+      const int32_t cd = tet2dof[tets[t] * 6 + eb];
+      if (cd < 0) continue;
+      int kk, mm;
+      elem_int(p, loc[t], eb, kk, mm);
+      R.add(cd, kk, mm, 0);
+    }
+    if (!faces) continue;
+    const int64_t cube = tets[t] / 6;
+    int V[4][3];
+    V[0][0] = (int)(cube % n);
+    V[0][1] = (int)((cube / n) % n);
+    V[0][2] = (int)(cube / ((int64_t)n * n));
+    for (int k = 0; k < 3; ++k) {
+      for (int a = 0; a < 3; ++a) V[k + 1][a] = V[k][a];
+      V[k + 1][a_perms[p][k]] += 1;
+    }
+    const int P = a_ledge[loc[t]][0], Q = a_ledge[loc[t]][1];
+    for (int S = 0; S < 4; ++S) {
+      if (S == P || S == Q) continue;
+      for (int ax = 0; ax < 3; ++ax) {
+        const int v = V[P][ax];
+        if (V[Q][ax] != v || V[S][ax] != v || (v != blo[ax] && v != bhi[ax])) continue;
+        // triangle {P, Q, S} on the box face normal to ax
+        const int fe[3] = {loc[t], ledge_index(min(P, S), max(P, S)), ledge_index(min(Q, S), max(Q, S))};
+        for (int f = 0; f < 3; ++f) {
+          const int32_t cd = tet2dof[tets[t] * 6 + fe[f]];
+          if (cd >= 0) R.add(cd, 0, 0, face_int(p, loc[t], fe[f], ax));
+        }
+      }
+    }
+  }
+}
+
 struct AsmArgs {
   int n;
   int64_t n_dof;
-  double sK, sM;
+  double sK, sM, sB;
+  int boundary;
   const int32_t* dof_key;
   const int32_t* tet2dof;
   int32_t* count;
@@ -113,56 +198,36 @@ struct AsmArgs {
   int32_t* col;
   double* K;
   double* M;
+  double* B;
 };
 
 template <bool FILL>
 __global__ void k_assemble(AsmArgs a) {
+  const int blo[3] = {0, 0, 0}, bhi[3] = {a.n, a.n, a.n};
   for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < a.n_dof;
        row += (int64_t)gridDim.x * blockDim.x) {
     int c[3], d;
     key_to_coords(a.dof_key[row], a.n, c, d);
-    int64_t tets[6];
-    int loc[6];
-    const int nt = edge_tets(a.n, c, d, tets, loc);
-    int cols[36], ik[36], im[36];
-    int m = 0;
-    for (int t = 0; t < nt; ++t) {
-      const int p = (int)(tets[t] % 6);
-      for (int eb = 0; eb < 6; ++eb) {
-        const int32_t cd = a.tet2dof[tets[t] * 6 + eb];
-        if (cd < 0) continue;
-        int kk, mm;
-        elem_int(p, loc[t], eb, kk, mm);
-        // insert in column order, merging duplicates (integer sums are exact)
-        int j = 0;
-        while (j < m && cols[j] < cd) ++j;
-        if (j < m && cols[j] == cd) {
-          ik[j] += kk;
-          im[j] += mm;
-        } else {
-          for (int s = m; s > j; --s) { cols[s] = cols[s - 1]; ik[s] = ik[s - 1]; im[s] = im[s - 1]; }
-          cols[j] = cd; ik[j] = kk; im[j] = mm;
-          ++m;
-        }
-      }
-    }
+    RowInts R;
+    row_ints(a.n, c, d, blo, bhi, a.boundary != 0, a.tet2dof, R);
     if (!FILL) {
-      a.count[row] = m;
+      a.count[row] = R.m;
     } else {
       const int32_t o = a.rowptr[row];
-      for (int j = 0; j < m; ++j) {
-        a.col[o + j] = cols[j];
-        a.K[o + j] = a.sK * (double)ik[j];
-        a.M[o + j] = a.sM * (double)im[j];
+      for (int j = 0; j < R.m; ++j) {
+        a.col[o + j] = R.cols[j];
+        a.K[o + j] = a.sK * (double)R.ik[j];
+        a.M[o + j] = a.sM * (double)R.im[j];
+        if (a.B) a.B[o + j] = a.sB * (double)R.ib[j];
       }
     }
   }
 }
 
-void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s) {
+void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s, bool boundary) {
   const double h = 1.0 / m.n;
-  AsmArgs a{m.n, m.n_dof, 2.0 / (3.0 * h), h / 120.0, m.dof_key.p, m.tet2dof.p,
-            nullptr, nullptr, nullptr, nullptr, nullptr};
+  AsmArgs a{m.n, m.n_dof, 2.0 / (3.0 * h), h / 120.0, 1.0 / 24.0, boundary ? 1 : 0, m.dof_key.p, m.tet2dof.p,
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   DevBuf<int32_t> cnt(std::max<int64_t>(m.n_dof, 1));
   A.rows = A.cols = m.n_dof;
   A.rowptr.alloc(m.n_dof + 1);
@@ -177,6 +242,12 @@ void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s) {
   a.col = A.col.p;
   a.K = A.K.p;
   a.M = A.M.p;
+  if (boundary) {
+    A.B.alloc(A.nnz);
+    a.B = A.B.p;
+  } else {
+    A.B.reset();
+  }
   MX_LAUNCH(k_assemble<true><<<grid_for(m.n_dof, 128), 128, 0, s>>>(a));
   MX_CHECK_LAUNCH();
   MX_CUDA(cudaStreamSynchronize(s));
@@ -310,7 +381,8 @@ __global__ void k_load_gather(int n, int64_t n_dof, int nrhs, const int32_t* dof
     key_to_coords(dof_key[i], n, c, d);
     int64_t tets[6];
     int loc[6];
-    const int nt = edge_tets(n, c, d, tets, loc);
+    const int blo[3] = {0, 0, 0}, bhi[3] = {n, n, n};
+    const int nt = edge_tets(n, c, d, tets, loc, blo, bhi);
     double2 s = make_double2(0, 0);
     for (int k = 0; k < nt; ++k) {
       const double2 v = contrib[(tets[k] * 6 + loc[k]) * nrhs + r];
@@ -496,6 +568,86 @@ __global__ void k_r0_rows(int n, int m, int64_t n_c, const int32_t* cdof_key, co
     if (!fill && threadIdx.x == 0) count[p] = running;
     __syncthreads();
   }
+}
+
+// ---- ImpRAS local matrices ----------------------------------------------------------
+struct ImpArgs {
+  int n, n_sub;
+  int64_t sum_local;
+  double sK, sM, sB, k2, xi, c;  // A = K - (k2 + i xi) M - i c B
+  const int32_t* box;            // [n_sub][6] vertex bounds
+  const int64_t* offsets;
+  const int32_t* lists;
+  const int32_t* dof_key;
+  const int32_t* tet2dof;
+  const int32_t* inv_ptr;
+  const int32_t* inv_pos;
+  const int32_t* band;
+  const int32_t* ld;
+  const int64_t* moff;
+  void* out;
+  int32_t* bad;  // entries outside the planned band or columns outside the box (none expected)
+};
+
+// One thread per (subdomain, local row): the row of the box's Galerkin matrix with the
+// impedance term on the box surface, written into the band storage at the local columns.
+template <typename T2>
+__global__ void k_extract_imp(ImpArgs a) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < a.sum_local;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = a.n_sub - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.offsets[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const int l = lo;
+    const int64_t o0 = a.offsets[l], o1 = a.offsets[l + 1];
+    const int i = (int)(q - o0);
+    const int blo[3] = {a.box[6 * l], a.box[6 * l + 1], a.box[6 * l + 2]};
+    const int bhi[3] = {a.box[6 * l + 3], a.box[6 * l + 4], a.box[6 * l + 5]};
+    int c[3], d;
+    key_to_coords(a.dof_key[a.lists[q]], a.n, c, d);
+    RowInts R;
+    row_ints(a.n, c, d, blo, bhi, true, a.tet2dof, R);
+    const int bw = a.band[l], ldl = a.ld[l];
+    const int64_t off = a.moff[l];
+    T2* A = reinterpret_cast<T2*>(a.out);
+    for (int e = 0; e < R.m; ++e) {
+      const int32_t cd = R.cols[e];
+      int j = -1;
+      for (int32_t t = a.inv_ptr[cd]; t < a.inv_ptr[cd + 1]; ++t) {
+        const int32_t p = a.inv_pos[t];
+        if (p >= o0 && p < o1) { j = (int)(p - o0); break; }
+      }
+      if (j < 0 || abs(i - j) > bw) {
+        atomicAdd(a.bad, 1);
+        continue;
+      }
+      const double K = a.sK * (double)R.ik[e], M = a.sM * (double)R.im[e], B = a.sB * (double)R.ib[e];
+      A[bidx(off, ldl, bw, i, j)] = conv<T2>(make_double2(K - a.k2 * M, -a.xi * M - a.c * B));
+    }
+  }
+}
+
+void extract_imp(Problem& P) {
+  cudaStream_t s = P.stream;
+  const double h = 1.0 / P.n;
+  DevBuf<int32_t> dbox(P.box.size()), bad(1);
+  MX_CUDA(cudaMemcpyAsync(dbox.p, P.box.data(), P.box.size() * 4, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaMemsetAsync(bad.p, 0, 4, s));
+  ImpArgs a{P.n, P.n_sub, P.sum_local, 2.0 / (3.0 * h), h / 120.0, 1.0 / 24.0, P.k * P.k, P.xi_prec,
+            imp_coef(P, P.xi_prec), dbox.p, P.offsets.p, P.lists.p, P.fine.dof_key.p, P.fine.tet2dof.p,
+            P.inv_ptr.p, P.inv_pos.p, P.band.p, P.ld.p, P.mat_off.p, P.factors.p, bad.p};
+  ProfScope ps(K_EXTRACT, s);
+  if (P.precision == MX_MIXED)
+    MX_LAUNCH(k_extract_imp<float2><<<grid_for(P.sum_local, 128), 128, 0, s>>>(a));
+  else
+    MX_LAUNCH(k_extract_imp<double2><<<grid_for(P.sum_local, 128), 128, 0, s>>>(a));
+  MX_CHECK_LAUNCH();
+  int32_t h_bad = 0;
+  MX_CUDA(cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  MX_REQUIRE(h_bad == 0, MX_EINVAL, "impedance local matrix entry outside its subdomain band");
 }
 
 void build_coarse_restriction(Problem& P) {

@@ -27,11 +27,13 @@ __global__ void k_csr_band(int64_t rows, const int32_t* rowptr, const int32_t* c
   atomicMax(out, bmax);
 }
 
+// A^0 = K_c - (sr + i si) M_c - i bc B_c in band storage (B_c: impedance term, or null)
 __global__ void k_coarse_fill(int64_t rows, const int32_t* rowptr, const int32_t* col, const double* K,
-                              const double* M, double sr, double si, int b, int ld, double2* A) {
+                              const double* M, double sr, double si, int b, int ld, double2* A, const double* B,
+                              double bc) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
     for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
-      A[bidx(0, ld, b, (int)i, col[e])] = make_double2(K[e] - sr * M[e], -si * M[e]);
+      A[bidx(0, ld, b, (int)i, col[e])] = make_double2(K[e] - sr * M[e], -si * M[e] - (B ? bc * B[e] : 0.0));
 }
 
 __global__ void k_to_c64(int64_t n, const double2* a, float2* b) {
@@ -56,7 +58,8 @@ void factor_coarse(Problem& P) {
   P.A0.alloc(P.ld_c * nc);
   MX_CUDA(cudaMemsetAsync(P.A0.p, 0, P.A0.bytes(), s));
   MX_LAUNCH(k_coarse_fill<<<grid_for(nc, 256), 256, 0, s>>>(nc, P.Ac.rowptr.p, P.Ac.col.p, P.Ac.K.p, P.Ac.M.p,
-                                                  P.k * P.k, P.xi_prec, b, (int)P.ld_c, P.A0.p));
+                                                  P.k * P.k, P.xi_prec, b, (int)P.ld_c, P.A0.p, P.Ac.B.p,
+                                                  imp_coef(P, P.xi_prec)));
   MX_CHECK_LAUNCH();
   const int32_t meta[3] = {(int32_t)nc, b, (int32_t)P.ld_c};
   const int64_t zero = 0;

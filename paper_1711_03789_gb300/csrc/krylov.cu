@@ -18,11 +18,12 @@
 namespace mx {
 
 // ---- SpMV ---------------------------------------------------------------------------
-// y[i][r] = sum_e (K_e - s M_e) x[col_e][r],  s = k^2 + i xi
+// y[i][r] = sum_e (K_e - s M_e - i bc B_e) x[col_e][r],  s = k^2 + i xi (B: impedance term,
+// absent with PEC)
 template <typename XT>
 __global__ void k_spmv(int64_t rows, int nrhs, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                        const double* __restrict__ K, const double* __restrict__ M, double sr, double si,
-                       const XT* __restrict__ x, double2* __restrict__ y) {
+                       const XT* __restrict__ x, double2* __restrict__ y, const double* __restrict__ B, double bc) {
   const int64_t work = rows * nrhs;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t % nrhs);
@@ -38,20 +39,34 @@ __global__ void k_spmv(int64_t rows, int nrhs, const int32_t* __restrict__ rowpt
       mx_.y = fma(m, xv.y, mx_.y);
     }
     // K x - (sr + i si) M x
-    y[t] = make_double2(kx.x - sr * mx_.x + si * mx_.y, kx.y - sr * mx_.y - si * mx_.x);
+    double2 out = make_double2(kx.x - sr * mx_.x + si * mx_.y, kx.y - sr * mx_.y - si * mx_.x);
+    if (B) {  // - i bc B x
+      double2 bx = make_double2(0, 0);
+      for (int32_t e = rowptr[i]; e < e1; ++e) {
+        const double b = B[e];
+        if (b == 0.0) continue;
+        const double2 xv = to_c128(x[(int64_t)col[e] * nrhs + r]);
+        bx.x = fma(b, xv.x, bx.x);
+        bx.y = fma(b, xv.y, bx.y);
+      }
+      out.x += bc * bx.y;
+      out.y -= bc * bx.x;
+    }
+    y[t] = out;
   }
 }
 
 static void spmv_km(const Problem& P, double sr, double si, const void* x, int xtype, double2* y, int nrhs,
-                    cudaStream_t s);
+                    cudaStream_t s, double bc = 0.0);
 
 void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int nrhs, cudaStream_t s) {
-  spmv_km(P, P.k * P.k, xi, x, xtype, y, nrhs, s);
+  spmv_km(P, P.k * P.k, xi, x, xtype, y, nrhs, s, imp_coef(P, xi));
 }
 
-// y = (K - (sr + i si) M) x
+// y = (K - (sr + i si) M - i bc B) x (bc = 0: no boundary term)
 static void spmv_km(const Problem& P, double sr, double si, const void* x, int xtype, double2* y, int nrhs,
-                    cudaStream_t s) {
+                    cudaStream_t s, double bc) {
+  const double* B = (bc != 0.0 && P.A.B.p) ? P.A.B.p : nullptr;
   const int64_t work = P.A.rows * nrhs;
   // K, M values and column indices once, x once, y once (algorithmic minimum)
   const double xb = xtype == 0 ? 16.0 : 8.0;
@@ -59,10 +74,10 @@ static void spmv_km(const Problem& P, double sr, double si, const void* x, int x
                8.0 * (double)P.A.nnz * nrhs);
   if (xtype == 0)
     MX_LAUNCH(k_spmv<double2><<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, P.A.K.p,
-                                                                    P.A.M.p, sr, si, (const double2*)x, y));
+                                                                    P.A.M.p, sr, si, (const double2*)x, y, B, bc));
   else
     MX_LAUNCH(k_spmv<float2><<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, P.A.K.p,
-                                                                   P.A.M.p, sr, si, (const float2*)x, y));
+                                                                   P.A.M.p, sr, si, (const float2*)x, y, B, bc));
   MX_CHECK_LAUNCH();
 }
 

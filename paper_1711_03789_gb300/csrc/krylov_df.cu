@@ -9,10 +9,13 @@
 
 namespace mx {
 
-// coef[e] = {a_hi, a_lo, b_hi, b_lo} with a + i b = K_e - (sr + i si) M_e
-__global__ void k_coef_df(int64_t nnz, const double* K, const double* M, double sr, double si, float4* coef) {
+// coef[e] = {a_hi, a_lo, b_hi, b_lo} with a + i b = K_e - (sr + i si) M_e - i bc B_e (B: the
+// impedance term, absent with PEC)
+__global__ void k_coef_df(int64_t nnz, const double* K, const double* M, double sr, double si, float4* coef,
+                          const double* B, double bc) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
-    const float2 a = df::split(K[e] - sr * M[e]), b = df::split(-si * M[e]);
+    const double im = -si * M[e] - (B ? bc * B[e] : 0.0);
+    const float2 a = df::split(K[e] - sr * M[e]), b = df::split(im);
     coef[e] = make_float4(a.x, a.y, b.x, b.y);
   }
 }
@@ -248,7 +251,7 @@ static const float4* coef_df(Problem& P, double xi, int slot, cudaStream_t s) {
   if (P.A_coef_df[slot].n != (size_t)P.A.nnz || P.A_coef_xi[slot] != xi) {
     P.A_coef_df[slot].alloc(P.A.nnz);
     MX_LAUNCH(k_coef_df<<<grid_for(P.A.nnz, 256), 256, 0, s>>>(P.A.nnz, P.A.K.p, P.A.M.p, P.k * P.k, xi,
-                                                              P.A_coef_df[slot].p));
+                                                              P.A_coef_df[slot].p, P.A.B.p, imp_coef(P, xi)));
     MX_CHECK_LAUNCH();
     P.A_coef_xi[slot] = xi;
   }
@@ -261,7 +264,7 @@ void dmul_df(Problem& P, const float4* w, float4* y, int nrhs, cudaStream_t s) {
     P.A_coef_df[2].alloc(P.A.nnz);
     // K - (sr + i si) M with sr = -k^2, si = 0
     MX_LAUNCH(k_coef_df<<<grid_for(P.A.nnz, 256), 256, 0, s>>>(P.A.nnz, P.A.K.p, P.A.M.p, -P.k * P.k, 0.0,
-                                                              P.A_coef_df[2].p));
+                                                              P.A_coef_df[2].p, nullptr, 0.0));
     MX_CHECK_LAUNCH();
   }
   const int64_t work = P.A.rows * nrhs;

@@ -367,7 +367,9 @@ void extract_minors(Problem& P) {
   a.ld = P.ld.p;
   a.moff = P.mat_off.p;
   a.out = P.factors.p;
-  if (P.precision == MX_MIXED)
+  if (P.bc == MX_BC_IMPEDANCE)
+    extract_imp(P);  // ImpRAS: Galerkin matrices of the closed boxes, not minors of A
+  else if (P.precision == MX_MIXED)
     MX_LAUNCH(k_extract<float2, true><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a));
   else
     MX_LAUNCH(k_extract<double2, true><<<grid_for(P.sum_local, 256), 256, 0, s>>>(a));

@@ -5,7 +5,8 @@
 // c, c + e_s0, c + e_s0 + e_s1, c + (1,1,1). Every mesh edge is (v, v + D_d) for one of
 // the 7 directions D (3 axes, 3 face diagonals, the body diagonal), oriented from the
 // lower to the higher vertex id. Edges on a boundary face carry no DOF (PEC, Eq. 1.4);
-// the others are numbered in increasing key 7 v + d.
+// the others are numbered in increasing key 7 v + d. With the impedance condition (Eq. imp)
+// every edge is a DOF, and the subdomains are closed boxes (ImpRAS, Sec. 6.3).
 #include "problem.cuh"
 
 namespace mx {
@@ -17,7 +18,7 @@ __constant__ int c_ledge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}
 // direction index of the 0/1 step vector encoded as dx + 2 dy + 4 dz
 __constant__ int c_dir_of_code[8] = {-1, 0, 1, 3, 2, 4, 5, 6};
 
-__global__ void k_edge_flags(int n, int32_t* flag) {
+__global__ void k_edge_flags(int n, int all_edges, int32_t* flag) {
   const int64_t total = (int64_t)(n + 1) * (n + 1) * (n + 1) * 7;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -28,7 +29,7 @@ __global__ void k_edge_flags(int n, int32_t* flag) {
     for (int a = 0; a < 3; ++a) {
       const int D = c_dirs[d][a];
       if (c[a] + D > n) ok = false;                   // edge leaves the grid
-      if (D == 0 && (c[a] == 0 || c[a] == n)) ok = false;  // lies on a boundary face
+      if (!all_edges && D == 0 && (c[a] == 0 || c[a] == n)) ok = false;  // lies on a boundary face
     }
     flag[t] = ok ? 1 : 0;
   }
@@ -70,12 +71,12 @@ __global__ void k_tet2dof(int n, const int32_t* edge_dof, int32_t* tet2dof) {
   }
 }
 
-void build_mesh(MeshDev& m, int n, cudaStream_t s) {
+void build_mesh(MeshDev& m, int n, cudaStream_t s, bool all_edges) {
   m.n = n;
   const int64_t total = (int64_t)(n + 1) * (n + 1) * (n + 1) * 7;
   MX_REQUIRE(total < (1LL << 31), MX_EINVAL, "mesh too large for 32-bit edge keys");
   DevBuf<int32_t> flag(total), pre(total + 1);
-  MX_LAUNCH(k_edge_flags<<<grid_for(total, 256), 256, 0, s>>>(n, flag.p));
+  MX_LAUNCH(k_edge_flags<<<grid_for(total, 256), 256, 0, s>>>(n, all_edges ? 1 : 0, flag.p));
   MX_CHECK_LAUNCH();
   m.n_dof = exclusive_scan_i32(flag.p, pre.p, total, s);
   m.edge_dof.alloc(total);
@@ -96,14 +97,22 @@ static inline void span(int n, int core, int overlap, int i, int& lo, int& hi) {
   hi = std::min(std::min(core * (i + 1), n) + overlap, n);
 }
 
-// Edges with both ends in the box [lo, hi] (vertex indices) that do not lie on a box face.
-static inline int64_t box_count(int a, int b, int c) {
+// Edges with both ends in the box [lo, hi] (vertex indices) that do not lie on a box face;
+// closed: all edges of the box, per direction D the product over axes of (len + 1 - D).
+static inline int64_t box_count(int a, int b, int c, bool closed) {
+  if (closed) {
+    static const int D[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+    int64_t t = 0;
+    for (int d = 0; d < 7; ++d) t += (int64_t)(a + 1 - D[d][0]) * (b + 1 - D[d][1]) * (c + 1 - D[d][2]);
+    return t;
+  }
   return (int64_t)a * (b - 1) * (c - 1) + (int64_t)b * (a - 1) * (c - 1) + (int64_t)c * (a - 1) * (b - 1) +
          (int64_t)a * b * (c - 1) + (int64_t)a * c * (b - 1) + (int64_t)b * c * (a - 1) + (int64_t)a * b * c;
 }
 
 struct BoxArgs {
   int n;
+  int closed;  // keep the edges on the box faces
   const int32_t* box;  // [n_sub][6]
   const int64_t* offsets;
   const int32_t* edge_dof;
@@ -134,7 +143,7 @@ __global__ void k_box_lists(BoxArgs a) {
       for (int ax = 0; ax < 3; ++ax) {
         const int D = c_dirs[d][ax];
         if (c[ax] + D > B[3 + ax]) ok = false;
-        if (D == 0 && (c[ax] == B[ax] || c[ax] == B[3 + ax])) ok = false;
+        if (!a.closed && D == 0 && (c[ax] == B[ax] || c[ax] == B[3 + ax])) ok = false;
       }
       if (ok) {
         const int64_t v = c[0] + (int64_t)(a.n + 1) * (c[1] + (int64_t)(a.n + 1) * c[2]);
@@ -160,7 +169,7 @@ __global__ void k_box_lists(BoxArgs a) {
 }
 
 struct InvArgs {
-  int n, core, overlap, N;
+  int n, core, overlap, N, closed;
   int64_t n_dof;
   const int32_t* dof_key;
   const int32_t* box;
@@ -173,14 +182,14 @@ struct InvArgs {
 };
 
 // Candidate boxes along one axis for an edge starting at coordinate c with step D.
-__device__ inline int axis_boxes(int c, int D, int n, int core, int overlap, int N, int* out) {
+__device__ inline int axis_boxes(int c, int D, int n, int core, int overlap, int N, int closed, int* out) {
   int k = 0;
   const int i0 = max(0, (c - overlap) / core - 1), i1 = min(N - 1, (c + overlap) / core + 1);
   for (int i = i0; i <= i1; ++i) {
     const int lo = max(core * i - overlap, 0);
     const int hi = min(min(core * (i + 1), n) + overlap, n);
     if (c < lo || c + D > hi) continue;
-    if (D == 0 && (c == lo || c == hi)) continue;
+    if (!closed && D == 0 && (c == lo || c == hi)) continue;
     out[k++] = i;
   }
   return k;
@@ -195,9 +204,9 @@ __global__ void k_inverse_map(InvArgs a) {
     const int64_t v = key / 7;
     const int c[3] = {(int)(v % (a.n + 1)), (int)((v / (a.n + 1)) % (a.n + 1)), (int)(v / ((int64_t)(a.n + 1) * (a.n + 1)))};
     int bx[16], by[16], bz[16];
-    const int nx = axis_boxes(c[0], c_dirs[d][0], a.n, a.core, a.overlap, a.N, bx);
-    const int ny = axis_boxes(c[1], c_dirs[d][1], a.n, a.core, a.overlap, a.N, by);
-    const int nz = axis_boxes(c[2], c_dirs[d][2], a.n, a.core, a.overlap, a.N, bz);
+    const int nx = axis_boxes(c[0], c_dirs[d][0], a.n, a.core, a.overlap, a.N, a.closed, bx);
+    const int ny = axis_boxes(c[1], c_dirs[d][1], a.n, a.core, a.overlap, a.N, a.closed, by);
+    const int nz = axis_boxes(c[2], c_dirs[d][2], a.n, a.core, a.overlap, a.N, a.closed, bz);
     if (!FILL) {
       a.count[i] = nx * ny * nz;
       continue;
@@ -267,6 +276,7 @@ void build_subdomains(Problem& P) {
   cudaStream_t s = P.stream;
   const int n = P.n;
   const int N = (n + P.core - 1) / P.core;
+  const bool closed = P.bc == MX_BC_IMPEDANCE;
   P.n_per_axis = N;
   P.n_sub = N * N * N;
   P.box.assign((size_t)P.n_sub * 6, 0);
@@ -281,7 +291,7 @@ void build_subdomains(Problem& P) {
         span(n, P.core, P.overlap, ix, B[0], B[3]);
         span(n, P.core, P.overlap, iy, B[1], B[4]);
         span(n, P.core, P.overlap, iz, B[2], B[5]);
-        const int64_t cnt = box_count(B[3] - B[0], B[4] - B[1], B[5] - B[2]);
+        const int64_t cnt = box_count(B[3] - B[0], B[4] - B[1], B[5] - B[2], closed);
         MX_REQUIRE(cnt > 0, MX_EINVAL, "a subdomain has no interior edge (core/overlap too small)");
         P.h_nl[l] = (int32_t)cnt;
         P.max_local = std::max<int>(P.max_local, (int)cnt);
@@ -295,14 +305,14 @@ void build_subdomains(Problem& P) {
   MX_CUDA(cudaMemcpyAsync(dbox.p, P.box.data(), P.box.size() * 4, cudaMemcpyHostToDevice, s));
   MX_CUDA(cudaMemcpyAsync(P.offsets.p, P.h_offsets.data(), (P.n_sub + 1) * 8, cudaMemcpyHostToDevice, s));
   MX_CUDA(cudaMemcpyAsync(P.nl.p, P.h_nl.data(), P.n_sub * 4, cudaMemcpyHostToDevice, s));
-  BoxArgs ba{n, dbox.p, P.offsets.p, P.fine.edge_dof.p, P.lists.p};
+  BoxArgs ba{n, closed ? 1 : 0, dbox.p, P.offsets.p, P.fine.edge_dof.p, P.lists.p};
   MX_LAUNCH(k_box_lists<<<P.n_sub, 256, 0, s>>>(ba));
   MX_CHECK_LAUNCH();
 
   const int64_t nd = P.fine.n_dof;
   DevBuf<int32_t> cnt(nd);
   P.inv_ptr.alloc(nd + 1);
-  InvArgs ia{n, P.core, P.overlap, N, nd, P.fine.dof_key.p, dbox.p, P.offsets.p, P.nl.p,
+  InvArgs ia{n, P.core, P.overlap, N, closed ? 1 : 0, nd, P.fine.dof_key.p, dbox.p, P.offsets.p, P.nl.p,
              P.lists.p, cnt.p, nullptr, nullptr};
   MX_LAUNCH(k_inverse_map<false><<<grid_for(nd, 256), 256, 0, s>>>(ia));
   MX_CHECK_LAUNCH();

@@ -16,11 +16,12 @@ struct MeshDev {
   DevBuf<int32_t> tet2dof;   // [6 n^3 * 6]
 };
 
-// Real CSR with the curl-curl (K) and mass (M) values on one pattern.
+// Real CSR with the curl-curl (K) and mass (M) values on one pattern, and the tangential
+// boundary mass (B) of the impedance condition (empty with PEC).
 struct CsrKM {
   int64_t rows = 0, cols = 0, nnz = 0;
   DevBuf<int32_t> rowptr, col;
-  DevBuf<double> K, M;
+  DevBuf<double> K, M, B;
 };
 
 // Plain CSR with one real value per entry (R^0 and its transpose).
@@ -56,6 +57,7 @@ __host__ __device__ inline int64_t bidx(int64_t off, int ld, int b, int i, int j
 struct Problem {
   // parameters
   int n = 0, core = 0, overlap = 0, coarse_m = 0, precision = MX_MIXED;
+  int bc = MX_BC_PEC;  // MX_BC_IMPEDANCE: all edges are DOFs, ImpRAS local problems
   double k = 0, xi_prob = 0, xi_prec = 0;
   cudaStream_t stream = nullptr;
 
@@ -149,7 +151,7 @@ struct Problem {
 // ---- api.cu -------------------------------------------------------------------------
 // validate, build mesh / assembly / subdomains / coarse space on `stream` (throws Error)
 Problem* create_problem(int n, double k, double xi_prob, double xi_prec, int core, int overlap, int coarse_m,
-                        int precision, cudaStream_t stream);
+                        int precision, cudaStream_t stream, int bc = MX_BC_PEC);
 // extract minors, batched local LU, coarse LU; checks pivots and waits (throws Error)
 void factor_problem(Problem& P);
 // device bytes of the local factors a factorisation will allocate (runs the band pass)
@@ -159,13 +161,23 @@ void transpose_to_internal(const double2* user, double2* in, int64_t n, int nrhs
 void transpose_to_user(const double2* in, double2* user, int64_t n, int nrhs, cudaStream_t s);
 
 // ---- mesh.cu ------------------------------------------------------------------------
-void build_mesh(MeshDev& m, int n, cudaStream_t s);
+// all_edges: every edge is a DOF (impedance condition), else the PEC-interior ones
+void build_mesh(MeshDev& m, int n, cudaStream_t s, bool all_edges = false);
 void build_subdomains(Problem& P);
 // owner positions of the partition of unity of the restricted variants (once)
 void build_owner(Problem& P);
 
 // ---- assemble.cu --------------------------------------------------------------------
-void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s);
+// boundary: also B, the tangential mass of the boundary triangles (impedance condition)
+void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s, bool boundary = false);
+// ImpRAS local matrices (Sec. 6.3): K - (k^2 + i xi_prec) M - i sign(xi_prec) k B of every
+// closed subdomain box (tetrahedra inside the box, triangles on its surface) into the
+// band storage of the local factors (element type of the precision)
+void extract_imp(Problem& P);
+// coefficient c of the impedance term -i c B of A_xi: sign(xi) k (sign(0) = +1), 0 for PEC
+inline double imp_coef(const Problem& P, double xi) {
+  return P.bc == MX_BC_IMPEDANCE ? (xi < 0 ? -P.k : P.k) : 0.0;
+}
 void load_vector(const Problem& P, int nrhs, int nbumps, const double* h_centres,
                  const double* h_pol, double width, double2* f /* [nrhs][n] device */);
 void build_coarse_restriction(Problem& P);

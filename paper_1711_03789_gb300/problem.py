@@ -7,10 +7,10 @@ class Problem:
     from A_{xi_prec} (Eq. 3.4); see include/mxas.h for the meaning of every argument."""
 
     def __init__(self, n_cells, k, xi_prob, xi_prec, core_cells=5, overlap_cells=1, coarse_cells=0,
-                 precision=L.MX_MIXED, stream=None, dense_local=False):
+                 precision=L.MX_MIXED, stream=None, dense_local=False, bc=L.MX_BC_PEC):
         self.n_cells = n_cells
         self.h = L.mx_build_problem(n_cells, k, xi_prob, xi_prec, core_cells, overlap_cells, coarse_cells,
-                                    precision)
+                                    precision, bc)
         if stream is not None:
             L.mx_set_stream(self.h, stream)
         if dense_local:
