@@ -50,7 +50,7 @@ static const char* k_names[K_COUNT] = {
     "mesh", "subdomains", "assemble", "coarse_r0", "load_vector", "extract_minors", "lu_diag", "lu_panel",
     "lu_update", "coarse_lu", "local_solve", "coarse_restrict", "coarse_sweep", "scatter", "spmv",
     "arnoldi_dots", "arnoldi_update", "arnoldi_small", "update_x", "residual", "layout", "coarse_inverse",
-    "coarse_gmres"};
+    "coarse_gmres", "arnoldi_dots_c64"};
 const char* kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? k_names[id] : ""; }
 
 struct Pending {

@@ -46,7 +46,7 @@ void note_launch();
 enum KernelId {
   K_MESH = 0, K_SUBDOMAINS, K_ASSEMBLE, K_COARSE_R0, K_LOAD, K_EXTRACT, K_LU_DIAG, K_LU_PANEL,
   K_LU_UPDATE, K_COARSE_LU, K_LOCAL_SOLVE, K_COARSE_RESTRICT, K_COARSE_SWEEP, K_SCATTER, K_SPMV,
-  K_DOTS, K_ORTH_UPDATE, K_ARNOLDI_SMALL, K_UPDATE_X, K_RESIDUAL, K_LAYOUT, K_COARSE_INV, K_COARSE_GMRES, K_COUNT
+  K_DOTS, K_ORTH_UPDATE, K_ARNOLDI_SMALL, K_UPDATE_X, K_RESIDUAL, K_LAYOUT, K_COARSE_INV, K_COARSE_GMRES, K_DOTS_C64, K_COUNT
 };
 const char* kernel_name(int id);
 bool prof_enabled();

@@ -140,6 +140,8 @@ struct Workspace {
   DevBuf<double2> w, b, x, r;     // [n][nrhs]
   DevBuf<double2> zc;             // [n][nrhs] current z_j promoted to c128 (unused by the solver)
   DevBuf<float4> hs;              // [m+2][nrhs] h of the current pass as double-floats (mixed)
+  DevBuf<float2> g2;              // [m+1][nrhs] pass-2 coefficients rounded to c64 (mixed)
+  DevBuf<float2> inv2;            // [nrhs] 1 / ||w''|| as a double-float (mixed)
   DevBuf<double2> pv;             // 3 [n][nrhs] work vectors of the hybrid preconditioners
   DevBuf<unsigned char> loc;      // [sum_local][nrhs] local solutions
   DevBuf<double2> yc;             // [n_c][nrhs]
@@ -188,7 +190,11 @@ static Workspace& workspace(Problem& P, int nrhs, int m) {
   W->b.alloc(nv);
   W->x.alloc(nv);
   W->r.alloc(nv);
-  if (P.precision == MX_MIXED) W->hs.alloc((size_t)(m + 2) * nrhs);
+  if (P.precision == MX_MIXED) {
+    W->hs.alloc((size_t)(m + 2) * nrhs);
+    W->g2.alloc((size_t)(m + 1) * nrhs);
+    W->inv2.alloc(nrhs);
+  }
   W->loc.alloc((size_t)P.sum_local * nrhs * zsz);
   if (P.coarse_m) W->yc.alloc((size_t)P.n_c * nrhs);
   W->H.alloc((size_t)m * (m + 1) * nrhs);
@@ -253,6 +259,9 @@ __global__ void k_sub_from(int64_t nv, const void* v, int vtype, double2* t) {
     if (vtype == 3) {
       const float4 d = reinterpret_cast<const float4*>(v)[i];
       a = make_double2((double)d.x + (double)d.z, (double)d.y + (double)d.w);
+    } else if (vtype == 1) {
+      const float2 d = reinterpret_cast<const float2*>(v)[i];
+      a = make_double2(d.x, d.y);
     } else {
       a = reinterpret_cast<const double2*>(v)[i];
     }
@@ -472,6 +481,44 @@ __global__ void k_arnoldi_finish_w(int nrhs, int j, int m, int stage, const doub
   }
 }
 
+// Two-pass classical Gram-Schmidt of the mixed form, per right-hand side. stage 0, after the
+// pass-1 inner products h (c64 accuracy): column j of H = h. stage 1, after the double-float
+// update (npart: ||w'||^2 partials) and the pass-2 inner products h: add h to the column,
+// ||w''||^2 = ||w'||^2 - |h|^2 (Pythagoras; the correction is small) into the subdiagonal,
+// g = h rounded to c64 and inv = 1 / ||w''|| as a double-float (0 for a zero norm or a
+// finished right-hand side) for the fused correction and normalisation.
+__global__ void k_cgs2_finish(int nblk, int nrhs, int j, int m, int stage, const double2* h, const double* npart,
+                              double2* H, const int32_t* active, float2* g, float2* inv) {
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  if (!active[r]) {
+    if (stage == 1) {
+      for (int i = 0; i <= j; ++i) g[i * nrhs + r] = make_float2(0.f, 0.f);
+      inv[r] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
+  double2* Hc = H + (int64_t)j * (m + 1) * nrhs;
+  if (stage == 0) {
+    for (int i = 0; i <= j; ++i) Hc[i * nrhs + r] = h[i * nrhs + r];
+    return;
+  }
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += npart[(int64_t)b * nrhs + r];
+  double c = 0;
+  for (int i = 0; i <= j; ++i) {
+    const double2 v = h[i * nrhs + r];
+    Hc[i * nrhs + r] = make_double2(Hc[i * nrhs + r].x + v.x, Hc[i * nrhs + r].y + v.y);
+    c += v.x * v.x + v.y * v.y;
+    g[i * nrhs + r] = make_float2((float)v.x, (float)v.y);
+  }
+  const double nw = sqrt(fmax(s - c, 0.0));
+  Hc[(j + 1) * nrhs + r] = make_double2(nw, 0.0);
+  const double iv = nw > 0 ? 1.0 / nw : 0.0;
+  const float hi = (float)iv;
+  inv[r] = make_float2(hi, (float)(iv - (double)hi));
+}
+
 // npart[blk][q] = partial sums of Re(conj(r) y) (y = D r): the D-norm of r squared
 __global__ void k_wnorm_partials(int64_t n, int nrhs, const double2* r, const double2* y, double* npart) {
   __shared__ double sh[256];
@@ -672,12 +719,16 @@ static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t 
   MX_CHECK_LAUNCH();
 }
 
+// planes of the mixed-form basis inside W.V: all c64 roundings first, then all remainders
+static float2* basis_hi(Workspace& W) { return reinterpret_cast<float2*>(W.V.p); }
+static float2* basis_lo(Workspace& W) { return reinterpret_cast<float2*>(W.V.p) + (int64_t)(W.m + 1) * W.n * W.nrhs; }
+
 // mixed form: double-float passes over the basis, FP64 reduction of the block partials
 static void dots_mixed(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s,
                        const double2* target = nullptr, const double2* extra = nullptr) {
   // one resident wave: the dots kernel holds 64 KB of accumulators per block (3 per SM)
   const int nb = std::min(W.nblk, 3 * sm_count());
-  dots_df(nb, n, W.nrhs, nvec, with_norm, reinterpret_cast<const float4*>(W.V.p),
+  dots_df(nb, n, W.nrhs, nvec, with_norm, basis_hi(W), basis_lo(W),
           reinterpret_cast<const float4*>(target ? target : W.w.p), W.active.p, W.hpart.p, s,
           reinterpret_cast<const float4*>(extra));
   const int total = nvec + with_norm;
@@ -783,7 +834,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
   }
   MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
   if (mixed) {
-    scale_v0_df(nv, nrhs, beta.p, W.active.p, W.r.p, reinterpret_cast<float4*>(W.V.p), s);
+    scale_v0_df(nv, nrhs, beta.p, W.active.p, W.r.p, basis_hi(W), basis_lo(W), s);
   } else {
     MX_LAUNCH(k_scale_v0<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p));
     MX_CHECK_LAUNCH();
@@ -796,8 +847,10 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     std::vector<int32_t> start_active = act;
     for (int j = 0; j < m; ++j) {
       unsigned char* zj = W.Z.p + (size_t)j * nv * zsz;
-      // z_j = B^{-1} v_j ; w = A z_j (mixed: v_j and w are double-floats, z_j is c64)
-      precond_apply(P, W.V.p + (int64_t)j * nv, zj, ztype, nrhs, 3, nullptr, mixed ? 3 : 0);
+      // z_j = B^{-1} v_j ; w = A z_j (mixed: the preconditioner reads the c64 plane of v_j,
+      // w is a double-float, z_j is c64)
+      if (mixed) precond_apply(P, basis_hi(W) + (int64_t)j * nv, zj, ztype, nrhs, 3, nullptr, 1);
+      else precond_apply(P, W.V.p + (int64_t)j * nv, zj, ztype, nrhs, 3, nullptr, 0);
       launches += 1 + (P.coarse_m ? 2 : 0) + 1;
       if (mixed) spmv_df(P, reinterpret_cast<const float2*>(zj), reinterpret_cast<float4*>(W.w.p), nrhs, s);
       else spmv(P, P.xi_prob, zj, ztype, W.w.p, nrhs, s);
@@ -814,7 +867,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
         };
         auto update = [&]() {
           if (mixed)
-            orth_update_df(W.nblk, n, nrhs, j + 1, reinterpret_cast<const float4*>(W.V.p), W.h2.p, W.hs.p,
+            orth_update_df(W.nblk, n, nrhs, j + 1, basis_hi(W), basis_lo(W), W.h2.p, W.hs.p,
                            W.active.p, reinterpret_cast<float4*>(W.w.p), W.npart.p, s);
           else
             orth_update(W, n, j + 1, s);
@@ -840,31 +893,52 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
         }
         launches += 8;
       }
+      if (mixed && !P.weighted) {
+        // classical Gram-Schmidt, two passes: c64 inner products, double-float update,
+        // double-float inner products, c64 correction fused with the normalisation
+        const int nb = std::min(W.nblk, 3 * sm_count());
+        float2* Vh = basis_hi(W);
+        dots_c64(nb, n, nrhs, j + 1, Vh, reinterpret_cast<const float4*>(W.w.p), W.active.p, W.hpart.p, s);
+        {
+          ProfScope ps(K_ARNOLDI_SMALL, s);
+          MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)(j + 1) * nrhs, 128), 128, 0, s>>>(nb, j + 1, nrhs, W.hpart.p,
+                                                                                           W.h2.p));
+          MX_LAUNCH(k_cgs2_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, 0, W.h2.p, W.npart.p, W.H.p, W.active.p,
+                                                  W.g2.p, W.inv2.p));
+          MX_CHECK_LAUNCH();
+        }
+        orth_update_df(W.nblk, n, nrhs, j + 1, Vh, basis_lo(W), W.h2.p, W.hs.p, W.active.p,
+                       reinterpret_cast<float4*>(W.w.p), W.npart.p, s);
+        dots_mixed(W, n, j + 1, 0, s);
+        {
+          ProfScope ps(K_ARNOLDI_SMALL, s);
+          MX_LAUNCH(k_cgs2_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, 1, W.h2.p, W.npart.p, W.H.p, W.active.p,
+                                                  W.g2.p, W.inv2.p));
+          MX_CHECK_LAUNCH();
+        }
+        update2_normalize(nv, nrhs, j + 1, Vh, W.g2.p, W.inv2.p, reinterpret_cast<const float4*>(W.w.p),
+                          Vh + (int64_t)(j + 1) * nv, basis_lo(W) + (int64_t)(j + 1) * nv, s);
+        launches += 9;
+      }
       // Arnoldi: classical Gram-Schmidt, second pass when needed
-      for (int pass = 0; pass < 2 && !P.weighted; ++pass) {
+      for (int pass = 0; pass < 2 && !P.weighted && !mixed; ++pass) {
         if (pass == 1) {
           MX_CUDA(cudaMemcpyAsync(W.h_flags, W.flags.p, 8, cudaMemcpyDeviceToHost, s));
           MX_CUDA(cudaStreamSynchronize(s));
           if (!W.h_flags[1]) break;
         }
-        if (mixed) {
-          dots_mixed(W, n, j + 1, pass == 0 ? 1 : 0, s);
-          orth_update_df(W.nblk, n, nrhs, j + 1, reinterpret_cast<const float4*>(W.V.p), W.h2.p, W.hs.p, W.active.p,
-                         reinterpret_cast<float4*>(W.w.p), W.npart.p, s);
-        } else {
-          dots(W, n, j + 1, pass == 0 ? 1 : 0, s);
-          orth_update(W, n, j + 1, s);
-        }
+        dots(W, n, j + 1, pass == 0 ? 1 : 0, s);
+        orth_update(W, n, j + 1, s);
         ProfScope ps(K_ARNOLDI_SMALL, s);
         MX_LAUNCH(k_arnoldi_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, pass, W.h2.p, W.npart.p, W.H.p, W.wnorm0.p,
                                           W.active.p, W.flags.p));
         MX_CHECK_LAUNCH();
         launches += 4;
       }
-      if (mixed) {
+      if (mixed && P.weighted) {
         normalize_df(nv, nrhs, j, m, W.H.p, W.active.p, reinterpret_cast<const float4*>(W.w.p),
-                     reinterpret_cast<float4*>(W.V.p + (int64_t)(j + 1) * nv), s);
-      } else {
+                     basis_hi(W) + (int64_t)(j + 1) * nv, basis_lo(W) + (int64_t)(j + 1) * nv, s);
+      } else if (!mixed) {
         ProfScope ps(K_ARNOLDI_SMALL, s, 1, 32.0 * (double)nv, 2.0 * (double)nv);
         MX_LAUNCH(k_normalize<<<gv, 256, 0, s>>>(nv, nrhs, j, m, W.H.p, W.active.p, W.w.p,
                                                  W.V.p + (int64_t)(j + 1) * nv));
@@ -925,7 +999,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     ++restarts;
     MX_CUDA(cudaMemcpyAsync(W.active.p, act.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
     if (mixed) {
-      scale_v0_df(nv, nrhs, beta.p, W.active.p, W.r.p, reinterpret_cast<float4*>(W.V.p), s);
+      scale_v0_df(nv, nrhs, beta.p, W.active.p, W.r.p, basis_hi(W), basis_lo(W), s);
     } else {
       MX_LAUNCH(k_scale_v0<<<gv, 256, 0, s>>>(nv, nrhs, beta.p, W.active.p, W.r.p, W.V.p));
       MX_CHECK_LAUNCH();

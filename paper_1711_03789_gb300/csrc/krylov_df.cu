@@ -1,9 +1,17 @@
 // Krylov kernels of the mixed form in double-float arithmetic (df64.cuh): the operator
 // w = A z_j on the stored c64 z_j, the classical Gram-Schmidt passes and the
-// normalisation, with the basis V and w stored as complex double-floats (float4
-// {re_hi, im_hi, re_lo, im_lo}, 16 bytes like c128). The small dense work (H, Givens,
-// least squares), the solution update and the true residual stay in FP64; inner products
-// leave the kernels as FP64 block partials.
+// normalisation. w is a complex double-float vector (float4 {re_hi, im_hi, re_lo, im_lo});
+// the basis V is stored as two c64 planes, Vh (the c64 rounding of each entry) and Vl (the
+// remainder), so that the passes that need only c64 accuracy read half the bytes. The
+// small dense work (H, Givens, least squares), the solution update and the true residual
+// stay in FP64; inner products leave the kernels as FP64 block partials.
+//
+// Arnoldi step (classical Gram-Schmidt, two passes, Sec. 6.1 leaves the orthogonalisation
+// open): pass 1 takes h1 = V^H w from the c64 planes (k_dots_c64; its error, about 1e-7 of
+// ||w||, is what pass 2 removes), w' = w - V h1 in double-float (k_orth_update_df), pass 2
+// h2 = V^H w' in double-float (k_dots_df), and v_{j+1} = (w' - V h2) / ||w''|| with the
+// correction V h2 -- of the size of the pass-1 error -- in c64 products on Vh, and
+// ||w''||^2 = ||w'||^2 - |h2|^2 (k_update2_normalize).
 #include "df64.cuh"
 #include "problem.cuh"
 
@@ -51,10 +59,10 @@ __global__ void k_spmv_df(int64_t rows, int nrhs, const int32_t* __restrict__ ro
 constexpr int DOTS_U = 8;
 constexpr int DOTS_IC = 32;
 template <int RP>
-__global__ void __launch_bounds__(256) k_dots_df(int64_t n, int nrhs, int nvec, int with_norm,
-                                                 const float4* __restrict__ V, const float4* __restrict__ w,
-                                                 const int32_t* __restrict__ active, double2* __restrict__ hpart,
-                                                 const float4* __restrict__ extra) {
+__global__ void __launch_bounds__(256, 3) k_dots_df(int64_t n, int nrhs, int nvec, int with_norm,
+                                                 const float2* __restrict__ Vh, const float2* __restrict__ Vl,
+                                                 const float4* __restrict__ w, const int32_t* __restrict__ active,
+                                                 double2* __restrict__ hpart, const float4* __restrict__ extra) {
   constexpr int XL = 32 / RP;
   extern __shared__ float4 acc_sm[];  // [8 warps][DOTS_IC][RP]: {re_s, re_e, im_s, im_e}
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -78,12 +86,23 @@ __global__ void __launch_bounds__(256) k_dots_df(int64_t n, int nrhs, int nvec, 
       }
       for (int k = 0; k < icn; ++k) {
         const int i = ic + k;
-        const float4* Vi = (i < nvec) ? V + (int64_t)i * nv : (extra ? extra : w);
+        const bool basis = i < nvec;
+        const float2* Hi = Vh + (int64_t)i * nv;
+        const float2* Lo = Vl + (int64_t)i * nv;
+        const float4* Ei = extra ? extra : w;
         df::Acc are, aim;
 #pragma unroll
         for (int u = 0; u < DOTS_U; ++u) {
           const int64_t x = xb + (int64_t)u * 8 * XL + xl;
-          const float4 a = (on && x < x1) ? Vi[x * nrhs + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+          float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (on && x < x1) {
+            if (basis) {
+              const float2 ah = Hi[x * nrhs + r], al = Lo[x * nrhs + r];
+              a = make_float4(ah.x, ah.y, al.x, al.y);
+            } else {
+              a = Ei[x * nrhs + r];
+            }
+          }
           // conj(a) c = (a.re c.re + a.im c.im) + i (a.re c.im - a.im c.re)
           df::add_prod2(are, a.x, a.z, c[u].x, c[u].z);
           df::add_prod2(are, a.y, a.w, c[u].y, c[u].w);
@@ -129,6 +148,124 @@ __global__ void __launch_bounds__(256) k_dots_df(int64_t n, int nrhs, int nvec, 
   }
 }
 
+// Paired form of k_dots_df for an even number of right-hand sides: a lane takes the pair
+// (r, r+1), so each plane is read with one 16-byte load per two entries (the c64 planes of
+// two neighbouring right-hand sides are adjacent) instead of two 8-byte loads per entry.
+// Lanes (xl, rp), rp = pair index fastest; XL2 = 32 / (RP / 2) rows per warp step.
+constexpr int DOTS_U2 = 4;
+
+// a += the accumulator of lane (lane ^ o), compensated
+__device__ __forceinline__ void fold_lanes(df::Acc& a, int o) {
+  float sm, e;
+  df::two_sum(a.s, __shfl_xor_sync(0xffffffffu, a.s, o), sm, e);
+  a.e = __fadd_rn(__fadd_rn(a.e, __shfl_xor_sync(0xffffffffu, a.e, o)), e);
+  a.s = sm;
+}
+template <int RP>
+__global__ void __launch_bounds__(256, 3) k_dots_df2(int64_t n, int nrhs, int nvec, int with_norm,
+                                                  const float2* __restrict__ Vh, const float2* __restrict__ Vl,
+                                                  const float4* __restrict__ w, const int32_t* __restrict__ active,
+                                                  double2* __restrict__ hpart, const float4* __restrict__ extra) {
+  constexpr int RP2 = RP / 2;
+  constexpr int XL = 32 / RP2;
+  extern __shared__ float4 acc_sm2[];  // [8 warps][DOTS_IC][RP]: {re_s, re_e, im_s, im_e}
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rp = lane % RP2, xl = lane / RP2;
+  const int r0 = 2 * rp;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t x0 = blockIdx.x * chunk, x1 = min(n, x0 + chunk);
+  const int total = nvec + with_norm;
+  const int64_t nv = n * nrhs;
+  const bool in = r0 < nrhs;  // nrhs even: r0 + 1 < nrhs too
+  const bool on0 = in && active[min(r0, nrhs - 1)], on1 = in && active[min(r0 + 1, nrhs - 1)];
+  float4* my = acc_sm2 + (size_t)warp * DOTS_IC * RP;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int ic = 0; ic < total; ic += DOTS_IC) {
+    const int icn = min(DOTS_IC, total - ic);
+    for (int t = lane; t < DOTS_IC * RP; t += 32) my[t] = zero;
+    __syncwarp();
+    for (int64_t xb = x0 + warp * XL; xb < x1; xb += (int64_t)8 * XL * DOTS_U2) {
+      float4 c0[DOTS_U2], c1[DOTS_U2];
+#pragma unroll
+      for (int u = 0; u < DOTS_U2; ++u) {
+        const int64_t x = xb + (int64_t)u * 8 * XL + xl;
+        const bool ok = in && x < x1;
+        c0[u] = (ok && on0) ? w[x * nrhs + r0] : zero;
+        c1[u] = (ok && on1) ? w[x * nrhs + r0 + 1] : zero;
+      }
+      for (int k = 0; k < icn; ++k) {
+        const int i = ic + k;
+        const bool basis = i < nvec;
+        const float4* Hi = reinterpret_cast<const float4*>(Vh + (int64_t)i * nv);
+        const float4* Lo = reinterpret_cast<const float4*>(Vl + (int64_t)i * nv);
+        const float4* Ei = extra ? extra : w;
+        df::Acc are0, aim0, are1, aim1;
+#pragma unroll
+        for (int u = 0; u < DOTS_U2; ++u) {
+          const int64_t x = xb + (int64_t)u * 8 * XL + xl;
+          float4 a0 = zero, a1 = zero;
+          if (in && x < x1) {
+            if (basis) {
+              const int64_t q = (x * nrhs + r0) >> 1;
+              const float4 h = Hi[q], l = Lo[q];
+              a0 = make_float4(h.x, h.y, l.x, l.y);
+              a1 = make_float4(h.z, h.w, l.z, l.w);
+            } else {
+              a0 = Ei[x * nrhs + r0];
+              a1 = Ei[x * nrhs + r0 + 1];
+            }
+          }
+          // conj(a) c = (a.re c.re + a.im c.im) + i (a.re c.im - a.im c.re)
+          df::add_prod2(are0, a0.x, a0.z, c0[u].x, c0[u].z);
+          df::add_prod2(are0, a0.y, a0.w, c0[u].y, c0[u].w);
+          df::add_prod2(aim0, a0.x, a0.z, c0[u].y, c0[u].w);
+          df::add_prod2(aim0, -a0.y, -a0.w, c0[u].x, c0[u].z);
+          df::add_prod2(are1, a1.x, a1.z, c1[u].x, c1[u].z);
+          df::add_prod2(are1, a1.y, a1.w, c1[u].y, c1[u].w);
+          df::add_prod2(aim1, a1.x, a1.z, c1[u].y, c1[u].w);
+          df::add_prod2(aim1, -a1.y, -a1.w, c1[u].x, c1[u].z);
+        }
+        // fold the row lanes (same pair) together, then into the warp's accumulators
+#pragma unroll
+        for (int o = RP2; o < 32; o <<= 1) {
+          fold_lanes(are0, o);
+          fold_lanes(aim0, o);
+          fold_lanes(are1, o);
+          fold_lanes(aim1, o);
+        }
+        if (xl == 0 && in) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const df::Acc& ar = q ? are1 : are0;
+            const df::Acc& ai = q ? aim1 : aim0;
+            float4 m = my[k * RP + r0 + q];
+            float sm, e;
+            df::two_sum(m.x, ar.s, sm, e);
+            m.y = __fadd_rn(m.y, __fadd_rn(ar.e, e));
+            m.x = sm;
+            df::two_sum(m.z, ai.s, sm, e);
+            m.w = __fadd_rn(m.w, __fadd_rn(ai.e, e));
+            m.z = sm;
+            my[k * RP + r0 + q] = m;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < icn * RP; t += blockDim.x) {
+      const int k = t / RP, rr = t % RP;
+      double sx = 0, sy = 0;
+      for (int wq = 0; wq < 8; ++wq) {
+        const float4 m = acc_sm2[((size_t)wq * DOTS_IC + k) * RP + rr];
+        sx += (double)m.x + (double)m.y;
+        sy += (double)m.z + (double)m.w;
+      }
+      if (rr < nrhs) hpart[((int64_t)blockIdx.x * total + ic + k) * nrhs + rr] = make_double2(sx, sy);
+    }
+    __syncthreads();
+  }
+}
+
 // hs[i][r] = h[i][r] as a complex double-float
 __global__ void k_split_h(int count, const double2* h, float4* hs) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) hs[t] = df::split_c(h[t]);
@@ -136,8 +273,8 @@ __global__ void k_split_h(int count, const double2* h, float4* hs) {
 
 // w[x][r] -= sum_{i < nvec} V_i[x][r] h_i[r]; npart[blk][r] = sum over the block of |w|^2
 template <int RP>
-__global__ void __launch_bounds__(256) k_orth_update_df(int64_t n, int nrhs, int nvec, const float4* __restrict__ V,
-                                                        const float4* __restrict__ hs,
+__global__ void __launch_bounds__(256) k_orth_update_df(int64_t n, int nrhs, int nvec, const float2* __restrict__ Vh,
+                                                        const float2* __restrict__ Vl, const float4* __restrict__ hs,
                                                         const int32_t* __restrict__ active, float4* __restrict__ w,
                                                         double* __restrict__ npart) {
   constexpr int XL = 32 / RP;
@@ -154,7 +291,8 @@ __global__ void __launch_bounds__(256) k_orth_update_df(int64_t n, int nrhs, int
       df::Acc sre, sim;
 #pragma unroll 8
       for (int i = 0; i < nvec; ++i) {
-        const float4 a = V[(int64_t)i * nv + x * nrhs + r];
+        const float2 ah = Vh[(int64_t)i * nv + x * nrhs + r], al = Vl[(int64_t)i * nv + x * nrhs + r];
+        const float4 a = make_float4(ah.x, ah.y, al.x, al.y);
         const float4 c = hs[i * nrhs + r];
         // a c = (a.re c.re - a.im c.im) + i (a.re c.im + a.im c.re)
         df::add_prod2(sre, a.x, a.z, c.x, c.z);
@@ -181,26 +319,127 @@ __global__ void __launch_bounds__(256) k_orth_update_df(int64_t n, int nrhs, int
   }
 }
 
-// v_{j+1} = w / h_{j+1,j}
+// v_{j+1} = w / h_{j+1,j} into the planes (vh, vl)
 __global__ void k_normalize_df(int64_t nv, int nrhs, int j, int m, const double2* H, const int32_t* active,
-                               const float4* w, float4* vnext) {
+                               const float4* w, float2* vh, float2* vl) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t % nrhs);
     const double hn = H[((int64_t)j * (m + 1) + j + 1) * nrhs + r].x;
     const float2 inv = df::split((hn > 0 && active[r]) ? 1.0 / hn : 0.0);
     const float4 a = w[t];
     const float2 u = df::mul(a.x, a.z, inv.x, inv.y), v = df::mul(a.y, a.w, inv.x, inv.y);
-    vnext[t] = make_float4(u.x, v.x, u.y, v.y);
+    vh[t] = make_float2(u.x, v.x);
+    vl[t] = make_float2(u.y, v.y);
   }
 }
 
-// v0 = r / beta (r FP64)
+// v0 = r / beta (r FP64) into the planes (vh, vl)
 __global__ void k_scale_v0_df(int64_t nv, int nrhs, const double* beta, const int32_t* active, const double2* r,
-                              float4* v0) {
+                              float2* vh, float2* vl) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(t % nrhs);
     const double inv = (active[q] && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
-    v0[t] = df::split_c(make_double2(r[t].x * inv, r[t].y * inv));
+    const float4 v = df::split_c(make_double2(r[t].x * inv, r[t].y * inv));
+    vh[t] = make_float2(v.x, v.y);
+    vl[t] = make_float2(v.z, v.w);
+  }
+}
+
+// hpart[blk][i][r] = sum over the block's rows of conj(Vh_i[x][r]) wh[x][r] with FP32
+// products and sums over a lane's DOTS_U rows, FP64 from the lane reduction on (the first
+// Gram-Schmidt pass). Same row split and lane layout as k_dots_df; per-warp FP64
+// accumulators in shared memory.
+template <int RP>
+__global__ void __launch_bounds__(256) k_dots_c64(int64_t n, int nrhs, int nvec, const float2* __restrict__ Vh,
+                                                  const float4* __restrict__ w, const int32_t* __restrict__ active,
+                                                  double2* __restrict__ hpart) {
+  constexpr int XL = 32 / RP;
+  extern __shared__ double2 acc_c[];  // [8 warps][DOTS_IC][RP]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = lane % RP, xl = lane / RP;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t x0 = blockIdx.x * chunk, x1 = min(n, x0 + chunk);
+  const int64_t nv = n * nrhs;
+  const bool on = r < nrhs && active[min(r, nrhs - 1)];
+  double2* my = acc_c + (size_t)warp * DOTS_IC * RP;
+  for (int ic = 0; ic < nvec; ic += DOTS_IC) {
+    const int icn = min(DOTS_IC, nvec - ic);
+    for (int t = lane; t < DOTS_IC * RP; t += 32) my[t] = make_double2(0.0, 0.0);
+    __syncwarp();
+    for (int64_t xb = x0 + warp * XL; xb < x1; xb += (int64_t)8 * XL * DOTS_U) {
+      float2 c[DOTS_U];
+#pragma unroll
+      for (int u = 0; u < DOTS_U; ++u) {
+        const int64_t x = xb + (int64_t)u * 8 * XL + xl;
+        if (on && x < x1) {
+          const float4 wv = w[x * nrhs + r];
+          c[u] = make_float2(wv.x, wv.y);
+        } else {
+          c[u] = make_float2(0.f, 0.f);
+        }
+      }
+      for (int k = 0; k < icn; ++k) {
+        const float2* Hi = Vh + (int64_t)(ic + k) * nv;
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int u = 0; u < DOTS_U; ++u) {
+          const int64_t x = xb + (int64_t)u * 8 * XL + xl;
+          const float2 a = (on && x < x1) ? Hi[x * nrhs + r] : make_float2(0.f, 0.f);
+          sr = fmaf(a.x, c[u].x, fmaf(a.y, c[u].y, sr));
+          si = fmaf(a.x, c[u].y, fmaf(-a.y, c[u].x, si));
+        }
+        double dr = sr, di = si;
+#pragma unroll
+        for (int o = RP; o < 32; o <<= 1) {
+          dr += __shfl_xor_sync(0xffffffffu, dr, o);
+          di += __shfl_xor_sync(0xffffffffu, di, o);
+        }
+        if (xl == 0) {
+          double2 m = my[k * RP + r];
+          m.x += dr;
+          m.y += di;
+          my[k * RP + r] = m;
+        }
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < icn * RP; t += blockDim.x) {
+      const int k = t / RP, rr = t % RP;
+      double sx = 0, sy = 0;
+      for (int wq = 0; wq < 8; ++wq) {
+        const double2 m = acc_c[((size_t)wq * DOTS_IC + k) * RP + rr];
+        sx += m.x;
+        sy += m.y;
+      }
+      if (rr < nrhs) hpart[((int64_t)blockIdx.x * nvec + ic + k) * nrhs + rr] = make_double2(sx, sy);
+    }
+    __syncthreads();
+  }
+}
+
+// v_{j+1}[t] = (w'[t] - sum_{i < nvec} Vh_i[t] g_i[r]) inv[r] into the planes (vh, vl): g the
+// c64 rounding of the pass-2 coefficients, inv = 1 / ||w''|| as a double-float (0 for a
+// finished right-hand side or a zero norm)
+__global__ void __launch_bounds__(256) k_update2_normalize(int64_t nv, int nrhs, int nvec,
+                                                           const float2* __restrict__ Vh,
+                                                           const float2* __restrict__ g, const float2* __restrict__ inv,
+                                                           const float4* __restrict__ w, float2* __restrict__ vh,
+                                                           float2* __restrict__ vl) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nrhs);
+    float cr = 0.f, ci = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < nvec; ++i) {
+      const float2 a = Vh[(int64_t)i * nv + t], b = g[i * nrhs + r];
+      cr = fmaf(a.x, b.x, fmaf(-a.y, b.y, cr));
+      ci = fmaf(a.x, b.y, fmaf(a.y, b.x, ci));
+    }
+    const float4 a = w[t];
+    const float2 s = inv[r];
+    const float2 u = df::sub(a.x, a.z, cr, 0.f), v = df::sub(a.y, a.w, ci, 0.f);
+    const float2 ur = df::mul(u.x, u.y, s.x, s.y), vr = df::mul(v.x, v.y, s.x, s.y);
+    vh[t] = make_float2(ur.x, vr.x);
+    vl[t] = make_float2(ur.y, vr.y);
   }
 }
 
@@ -298,60 +537,103 @@ void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s) {
 }
 
 template <int RP>
-static void dots_rp(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
-                    const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra) {
+static void dots_rp(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2* Vh, const float2* Vl,
+                    const float4* w, const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra) {
   const size_t smem = (size_t)8 * DOTS_IC * RP * sizeof(float4);
   static bool configured = false;
   if (!configured) {
     MX_CUDA(cudaFuncSetAttribute(k_dots_df<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = true;
   }
-  MX_LAUNCH(k_dots_df<RP><<<nblk, 256, smem, s>>>(n, nrhs, nvec, with_norm, V, w, active, hpart, extra));
+  if constexpr (RP >= 2) {
+    if (nrhs % 2 == 0) {
+      static bool configured2 = false;
+      if (!configured2) {
+        MX_CUDA(cudaFuncSetAttribute(k_dots_df2<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured2 = true;
+      }
+      MX_LAUNCH(k_dots_df2<RP><<<nblk, 256, smem, s>>>(n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, extra));
+      return;
+    }
+  }
+  MX_LAUNCH(k_dots_df<RP><<<nblk, 256, smem, s>>>(n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, extra));
 }
-void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
-             const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra) {
+void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2* Vh, const float2* Vl,
+             const float4* w, const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra) {
   ProfScope ps(K_DOTS, s, 1, 16.0 * (nvec + 1) * (double)n * nrhs, 8.0 * (nvec + with_norm) * (double)n * nrhs);
-  if (nrhs <= 1) dots_rp<1>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
-  else if (nrhs <= 2) dots_rp<2>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
-  else if (nrhs <= 4) dots_rp<4>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
-  else if (nrhs <= 8) dots_rp<8>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
-  else if (nrhs <= 16) dots_rp<16>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
-  else dots_rp<32>(nblk, n, nrhs, nvec, with_norm, V, w, active, hpart, s, extra);
+  if (nrhs <= 1) dots_rp<1>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
+  else if (nrhs <= 2) dots_rp<2>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
+  else if (nrhs <= 4) dots_rp<4>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
+  else if (nrhs <= 8) dots_rp<8>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
+  else if (nrhs <= 16) dots_rp<16>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
+  else dots_rp<32>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
   MX_CHECK_LAUNCH();
 }
 
 template <int RP>
-static void update_rp(int nblk, int64_t n, int nrhs, int nvec, const float4* V, const float4* hs, const int32_t* active,
-                      float4* w, double* npart, cudaStream_t s) {
-  MX_LAUNCH(k_orth_update_df<RP><<<nblk, 256, 0, s>>>(n, nrhs, nvec, V, hs, active, w, npart));
+static void dots_c64_rp(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float4* w,
+                        const int32_t* active, double2* hpart, cudaStream_t s) {
+  const size_t smem = (size_t)8 * DOTS_IC * RP * sizeof(double2);
+  static bool configured = false;
+  if (!configured) {
+    MX_CUDA(cudaFuncSetAttribute(k_dots_c64<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  MX_LAUNCH(k_dots_c64<RP><<<nblk, 256, smem, s>>>(n, nrhs, nvec, Vh, w, active, hpart));
 }
-void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float4* V, const double2* h, float4* hs,
-                    const int32_t* active, float4* w, double* npart, cudaStream_t s) {
+void dots_c64(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float4* w, const int32_t* active,
+              double2* hpart, cudaStream_t s) {
+  // Vh (8 B per entry) once per basis vector, w once
+  ProfScope ps(K_DOTS_C64, s, 1, (8.0 * nvec + 16.0) * (double)n * nrhs, 8.0 * nvec * (double)n * nrhs);
+  if (nrhs <= 1) dots_c64_rp<1>(nblk, n, nrhs, nvec, Vh, w, active, hpart, s);
+  else if (nrhs <= 2) dots_c64_rp<2>(nblk, n, nrhs, nvec, Vh, w, active, hpart, s);
+  else if (nrhs <= 4) dots_c64_rp<4>(nblk, n, nrhs, nvec, Vh, w, active, hpart, s);
+  else if (nrhs <= 8) dots_c64_rp<8>(nblk, n, nrhs, nvec, Vh, w, active, hpart, s);
+  else if (nrhs <= 16) dots_c64_rp<16>(nblk, n, nrhs, nvec, Vh, w, active, hpart, s);
+  else dots_c64_rp<32>(nblk, n, nrhs, nvec, Vh, w, active, hpart, s);
+  MX_CHECK_LAUNCH();
+}
+
+void update2_normalize(int64_t nv, int nrhs, int nvec, const float2* Vh, const float2* g, const float2* inv,
+                       const float4* w, float2* vh, float2* vl, cudaStream_t s) {
+  // Vh once per basis vector, w' once, v_{j+1} (both planes) written once
+  ProfScope ps(K_ORTH_UPDATE, s, 1, (8.0 * nvec + 32.0) * (double)nv, 8.0 * nvec * (double)nv);
+  MX_LAUNCH(k_update2_normalize<<<grid_for(nv, 256, 152LL * 16), 256, 0, s>>>(nv, nrhs, nvec, Vh, g, inv, w, vh, vl));
+  MX_CHECK_LAUNCH();
+}
+
+template <int RP>
+static void update_rp(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float2* Vl, const float4* hs,
+                      const int32_t* active, float4* w, double* npart, cudaStream_t s) {
+  MX_LAUNCH(k_orth_update_df<RP><<<nblk, 256, 0, s>>>(n, nrhs, nvec, Vh, Vl, hs, active, w, npart));
+}
+void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float2* Vl, const double2* h,
+                    float4* hs, const int32_t* active, float4* w, double* npart, cudaStream_t s) {
   {
     ProfScope ps(K_ARNOLDI_SMALL, s);
     MX_LAUNCH(k_split_h<<<grid_for((int64_t)nvec * nrhs, 128), 128, 0, s>>>(nvec * nrhs, h, hs));
     MX_CHECK_LAUNCH();
   }
   ProfScope ps(K_ORTH_UPDATE, s, 1, 16.0 * (nvec + 2) * (double)n * nrhs, 8.0 * (nvec + 0.25) * (double)n * nrhs);
-  if (nrhs <= 1) update_rp<1>(nblk, n, nrhs, nvec, V, hs, active, w, npart, s);
-  else if (nrhs <= 2) update_rp<2>(nblk, n, nrhs, nvec, V, hs, active, w, npart, s);
-  else if (nrhs <= 4) update_rp<4>(nblk, n, nrhs, nvec, V, hs, active, w, npart, s);
-  else if (nrhs <= 8) update_rp<8>(nblk, n, nrhs, nvec, V, hs, active, w, npart, s);
-  else if (nrhs <= 16) update_rp<16>(nblk, n, nrhs, nvec, V, hs, active, w, npart, s);
-  else update_rp<32>(nblk, n, nrhs, nvec, V, hs, active, w, npart, s);
+  if (nrhs <= 1) update_rp<1>(nblk, n, nrhs, nvec, Vh, Vl, hs, active, w, npart, s);
+  else if (nrhs <= 2) update_rp<2>(nblk, n, nrhs, nvec, Vh, Vl, hs, active, w, npart, s);
+  else if (nrhs <= 4) update_rp<4>(nblk, n, nrhs, nvec, Vh, Vl, hs, active, w, npart, s);
+  else if (nrhs <= 8) update_rp<8>(nblk, n, nrhs, nvec, Vh, Vl, hs, active, w, npart, s);
+  else if (nrhs <= 16) update_rp<16>(nblk, n, nrhs, nvec, Vh, Vl, hs, active, w, npart, s);
+  else update_rp<32>(nblk, n, nrhs, nvec, Vh, Vl, hs, active, w, npart, s);
   MX_CHECK_LAUNCH();
 }
 
 void normalize_df(int64_t nv, int nrhs, int j, int m, const double2* H, const int32_t* active, const float4* w,
-                  float4* vnext, cudaStream_t s) {
+                  float2* vh, float2* vl, cudaStream_t s) {
   ProfScope ps(K_ARNOLDI_SMALL, s, 1, 32.0 * (double)nv, 2.0 * (double)nv);
-  MX_LAUNCH(k_normalize_df<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, j, m, H, active, w, vnext));
+  MX_LAUNCH(k_normalize_df<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, j, m, H, active, w, vh, vl));
   MX_CHECK_LAUNCH();
 }
 
-void scale_v0_df(int64_t nv, int nrhs, const double* beta, const int32_t* active, const double2* r, float4* v0,
-                 cudaStream_t s) {
-  MX_LAUNCH(k_scale_v0_df<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, beta, active, r, v0));
+void scale_v0_df(int64_t nv, int nrhs, const double* beta, const int32_t* active, const double2* r, float2* vh,
+                 float2* vl, cudaStream_t s) {
+  MX_LAUNCH(k_scale_v0_df<<<grid_for(nv, 256), 256, 0, s>>>(nv, nrhs, beta, active, r, vh, vl));
   MX_CHECK_LAUNCH();
 }
 

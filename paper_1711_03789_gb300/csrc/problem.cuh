@@ -228,16 +228,24 @@ void free_workspace(Problem& P);
 void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s);
 // y = A_xi z, z c64, y c128 (double-float accumulation)
 void spmv_df_c128(Problem& P, double xi, const float2* z, double2* y, int nrhs, cudaStream_t s);
-void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float4* V, const float4* w,
-             const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra = nullptr);
+// The basis of the mixed form is two c64 planes: Vh [m+1][n][nrhs] (c64 rounding) and Vl
+// (remainder); vector i at offset i * n * nrhs of each.
+void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2* Vh, const float2* Vl,
+             const float4* w, const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra = nullptr);
+// first Gram-Schmidt pass: FP32 products of the c64 planes, FP64 partials
+void dots_c64(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float4* w, const int32_t* active,
+              double2* hpart, cudaStream_t s);
+// v_{j+1} = (w' - Vh g) inv into the planes (g: c64 pass-2 coefficients, inv: 1/||w''|| split)
+void update2_normalize(int64_t nv, int nrhs, int nvec, const float2* Vh, const float2* g, const float2* inv,
+                       const float4* w, float2* vh, float2* vl, cudaStream_t s);
 // y = D_k w, D_k = K + k^2 M, double-float vectors
 void dmul_df(Problem& P, const float4* w, float4* y, int nrhs, cudaStream_t s);
-void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float4* V, const double2* h, float4* hs,
-                    const int32_t* active, float4* w, double* npart, cudaStream_t s);
+void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float2* Vl, const double2* h,
+                    float4* hs, const int32_t* active, float4* w, double* npart, cudaStream_t s);
 void normalize_df(int64_t nv, int nrhs, int j, int m, const double2* H, const int32_t* active, const float4* w,
-                  float4* vnext, cudaStream_t s);
-void scale_v0_df(int64_t nv, int nrhs, const double* beta, const int32_t* active, const double2* r, float4* v0,
-                 cudaStream_t s);
+                  float2* vh, float2* vl, cudaStream_t s);
+void scale_v0_df(int64_t nv, int nrhs, const double* beta, const int32_t* active, const double2* r, float2* vh,
+                 float2* vl, cudaStream_t s);
 // h[i][r] = sum_x conj(V_i[x][r]) w[x][r], i < nvec; V [nvec][n][nrhs], w [n][nrhs] (device);
 // partials: nblk * nvec * nrhs entries of scratch; ones: nrhs flags equal to 1
 void batched_dots(const double2* V, const double2* w, int64_t n, int nrhs, int nvec, double2* h, double2* partials,
