@@ -142,6 +142,8 @@ def run_ours(args, W, rank, world):
                        bc=mx.MX_BC_IMPEDANCE if args.bc == "imp" else mx.MX_BC_PEC)
         if args.local_tensor is not None:
             mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, args.local_tensor)
+        if args.lu_tensor is not None:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_TENSOR, args.lu_tensor)
         if args.weighted:
             mx.mx_set_weighted_gmres(P.h, 1)
         if args.precond != "as":
@@ -411,6 +413,8 @@ def main():
     ap.add_argument("--coarse-tol", type=float, default=0.1)
     ap.add_argument("--coarse-max-it", type=int, default=100)
     ap.add_argument("--coarse-inner", default="ras", choices=["ras", "as"])
+    ap.add_argument("--lu-tensor", type=int, default=None, choices=[0, 1, 3],
+                    help="local LU trailing update: 0 CUDA cores, 1 TF32, 3 split 3 x TF32 tensor cores")
     ap.add_argument("--local-tensor", type=int, default=None, choices=[0, 1],
                     help="local solves on the tensor cores (1) or CUDA cores (0); default: library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -236,30 +236,51 @@ __global__ void __launch_bounds__(256, 2) k_coarse_dense(int n, int nrhs, int jc
 #pragma unroll
   for (int g = 0; g < CD_R; ++g) acc0[g] = acc1[g] = make_float2(0.f, 0.f);
   const bool vec = gn == CD_R && (nrhs % 2) == 0;
-#pragma unroll 2
-  for (int j = j0; j < j1; ++j) {
-    const float2* xr = X + (int64_t)j * n + i0;
-    const float2 a0 = xr[0];
-    const float2 a1 = two ? xr[1] : make_float2(0.f, 0.f);
-    const float2* r = rc + (int64_t)j * nrhs + g0;
-    if (vec) {
-      const float4* r4 = reinterpret_cast<const float4*>(r);
+  // the two columns as one 16-byte load when the row offset is even
+  const bool pair = two && (n % 2) == 0;
+  constexpr int JU = 8;  // rows of X in flight per thread
+  for (int jb = j0; jb < j1; jb += JU) {
+    float2 xa[JU], xb[JU];
 #pragma unroll
-      for (int g = 0; g < CD_R / 2; ++g) {
-        const float4 q = r4[g];
-        cfma(acc0[2 * g], a0, make_float2(q.x, q.y));
-        cfma(acc1[2 * g], a1, make_float2(q.x, q.y));
-        cfma(acc0[2 * g + 1], a0, make_float2(q.z, q.w));
-        cfma(acc1[2 * g + 1], a1, make_float2(q.z, q.w));
-      }
-    } else {
-#pragma unroll
-      for (int g = 0; g < CD_R; ++g)
-        if (g < gn) {
-          const float2 q = r[g];
-          cfma(acc0[g], a0, q);
-          cfma(acc1[g], a1, q);
+    for (int u = 0; u < JU; ++u) {
+      const int j = jb + u;
+      xa[u] = xb[u] = make_float2(0.f, 0.f);
+      if (j < j1) {
+        const float2* xr = X + (int64_t)j * n + i0;
+        if (pair) {
+          const float4 q = *reinterpret_cast<const float4*>(xr);
+          xa[u] = make_float2(q.x, q.y);
+          xb[u] = make_float2(q.z, q.w);
+        } else {
+          xa[u] = xr[0];
+          if (two) xb[u] = xr[1];
         }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < JU; ++u) {
+      const int j = jb + u;
+      if (j >= j1) break;
+      const float2* r = rc + (int64_t)j * nrhs + g0;
+      if (vec) {
+        const float4* r4 = reinterpret_cast<const float4*>(r);
+#pragma unroll
+        for (int g = 0; g < CD_R / 2; ++g) {
+          const float4 q = r4[g];
+          cfma(acc0[2 * g], xa[u], make_float2(q.x, q.y));
+          cfma(acc1[2 * g], xb[u], make_float2(q.x, q.y));
+          cfma(acc0[2 * g + 1], xa[u], make_float2(q.z, q.w));
+          cfma(acc1[2 * g + 1], xb[u], make_float2(q.z, q.w));
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < CD_R; ++g)
+          if (g < gn) {
+            const float2 q = r[g];
+            cfma(acc0[g], xa[u], q);
+            cfma(acc1[g], xb[u], q);
+          }
+      }
     }
   }
   float2* o = part + ((int64_t)blockIdx.y * n + i0) * nrhs + g0;
@@ -366,10 +387,11 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
     MX_CHECK_LAUNCH();
   }
   if (dense) {
-    // split the rows of X among ks chunks so that the grid fills about two blocks per SM
+    // split the rows of X among ks chunks so that the grid fits in one wave of two blocks
+    // per SM (a second, nearly empty wave would double the time)
     const int rows_blocks = (int)((nc + 511) / 512);
     const int zgroups = (nrhs + CD_R - 1) / CD_R;
-    const int ks = std::max(1, std::min(64, (2 * sm_count() + rows_blocks * zgroups - 1) / (rows_blocks * zgroups)));
+    const int ks = std::max(1, std::min(64, (2 * sm_count()) / (rows_blocks * zgroups)));
     const int jchunk = (int)((nc + ks - 1) / ks);
     P.c_part.ensure((size_t)ks * nc * nrhs);
     {

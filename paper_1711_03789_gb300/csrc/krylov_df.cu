@@ -319,6 +319,74 @@ __global__ void __launch_bounds__(256) k_orth_update_df(int64_t n, int nrhs, int
   }
 }
 
+// Paired form of k_orth_update_df for an even number of right-hand sides: a lane updates
+// the pair (r, r+1) of a row, reading each plane with one 16-byte load per basis vector.
+template <int RP>
+__global__ void __launch_bounds__(256, 4) k_orth_update_df2(int64_t n, int nrhs, int nvec, const float2* __restrict__ Vh,
+                                                         const float2* __restrict__ Vl, const float4* __restrict__ hs,
+                                                         const int32_t* __restrict__ active, float4* __restrict__ w,
+                                                         double* __restrict__ npart) {
+  constexpr int RP2 = RP / 2;
+  constexpr int XL = 32 / RP2;
+  __shared__ double sh[8][RP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rp = lane % RP2, xl = lane / RP2;
+  const int r0 = 2 * rp;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t x0 = blockIdx.x * chunk, x1 = min(n, x0 + chunk);
+  const int64_t nv = n * nrhs;
+  const bool in = r0 < nrhs;
+  const bool on0 = in && active[min(r0, nrhs - 1)], on1 = in && active[min(r0 + 1, nrhs - 1)];
+  df::Acc nrm0, nrm1;
+  if (on0 || on1)
+    for (int64_t x = x0 + warp * XL + xl; x < x1; x += 8 * XL) {
+      df::Acc sre0, sim0, sre1, sim1;
+      const int64_t q = (x * nrhs + r0) >> 1;
+#pragma unroll 4
+      for (int i = 0; i < nvec; ++i) {
+        const float4 h = reinterpret_cast<const float4*>(Vh + (int64_t)i * nv)[q];
+        const float4 l = reinterpret_cast<const float4*>(Vl + (int64_t)i * nv)[q];
+        const float4 c0 = hs[i * nrhs + r0], c1 = hs[i * nrhs + r0 + 1];
+        // a c = (a.re c.re - a.im c.im) + i (a.re c.im + a.im c.re)
+        df::add_prod2(sre0, h.x, l.x, c0.x, c0.z);
+        df::add_prod2(sre0, -h.y, -l.y, c0.y, c0.w);
+        df::add_prod2(sim0, h.x, l.x, c0.y, c0.w);
+        df::add_prod2(sim0, h.y, l.y, c0.x, c0.z);
+        df::add_prod2(sre1, h.z, l.z, c1.x, c1.z);
+        df::add_prod2(sre1, -h.w, -l.w, c1.y, c1.w);
+        df::add_prod2(sim1, h.z, l.z, c1.y, c1.w);
+        df::add_prod2(sim1, h.w, l.w, c1.x, c1.z);
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (!(k ? on1 : on0)) continue;
+        const float4 wv = w[x * nrhs + r0 + k];
+        const float2 s1 = df::value(k ? sre1 : sre0), s2 = df::value(k ? sim1 : sim0);
+        const float2 u = df::sub(wv.x, wv.z, s1.x, s1.y), v = df::sub(wv.y, wv.w, s2.x, s2.y);
+        w[x * nrhs + r0 + k] = make_float4(u.x, v.x, u.y, v.y);
+        df::Acc& nrm = k ? nrm1 : nrm0;
+        df::add_prod2(nrm, u.x, u.y, u.x, u.y);
+        df::add_prod2(nrm, v.x, v.y, v.x, v.y);
+      }
+    }
+  double nd0 = df::to_double(nrm0), nd1 = df::to_double(nrm1);
+#pragma unroll
+  for (int o = RP2; o < 32; o <<= 1) {
+    nd0 += __shfl_xor_sync(0xffffffffu, nd0, o);
+    nd1 += __shfl_xor_sync(0xffffffffu, nd1, o);
+  }
+  if (xl == 0 && in) {
+    sh[warp][r0] = nd0;
+    sh[warp][r0 + 1] = nd1;
+  }
+  __syncthreads();
+  if (threadIdx.x < RP && threadIdx.x < nrhs) {
+    double s = 0;
+    for (int wq = 0; wq < 8; ++wq) s += sh[wq][threadIdx.x];
+    npart[(int64_t)blockIdx.x * nrhs + threadIdx.x] = s;
+  }
+}
+
 // v_{j+1} = w / h_{j+1,j} into the planes (vh, vl)
 __global__ void k_normalize_df(int64_t nv, int nrhs, int j, int m, const double2* H, const int32_t* active,
                                const float4* w, float2* vh, float2* vl) {
@@ -594,17 +662,67 @@ void dots_c64(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const f
   MX_CHECK_LAUNCH();
 }
 
+// Paired form of k_update2_normalize (nrhs even): a thread takes the adjacent entries
+// (t, t + 1) of one row, so every plane access is one 16-byte load or store.
+__global__ void __launch_bounds__(256) k_update2_normalize2(int64_t nv, int nrhs, int nvec,
+                                                            const float2* __restrict__ Vh,
+                                                            const float2* __restrict__ g,
+                                                            const float2* __restrict__ inv,
+                                                            const float4* __restrict__ w, float2* __restrict__ vh,
+                                                            float2* __restrict__ vl) {
+  const int64_t np = nv >> 1;
+  for (int64_t tp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tp < np; tp += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = tp << 1;
+    const int r = (int)(t % nrhs);
+    float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < nvec; ++i) {
+      const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)i * nv)[tp];
+      const float4 b = *reinterpret_cast<const float4*>(g + i * nrhs + r);
+      cr0 = fmaf(a.x, b.x, fmaf(-a.y, b.y, cr0));
+      ci0 = fmaf(a.x, b.y, fmaf(a.y, b.x, ci0));
+      cr1 = fmaf(a.z, b.z, fmaf(-a.w, b.w, cr1));
+      ci1 = fmaf(a.z, b.w, fmaf(a.w, b.z, ci1));
+    }
+    float4 oh, ol;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float4 a = w[t + k];
+      const float2 sc = inv[r + k];
+      const float2 u = df::sub(a.x, a.z, k ? cr1 : cr0, 0.f), v = df::sub(a.y, a.w, k ? ci1 : ci0, 0.f);
+      const float2 ur = df::mul(u.x, u.y, sc.x, sc.y), vr = df::mul(v.x, v.y, sc.x, sc.y);
+      if (k == 0) {
+        oh.x = ur.x; oh.y = vr.x; ol.x = ur.y; ol.y = vr.y;
+      } else {
+        oh.z = ur.x; oh.w = vr.x; ol.z = ur.y; ol.w = vr.y;
+      }
+    }
+    reinterpret_cast<float4*>(vh)[tp] = oh;
+    reinterpret_cast<float4*>(vl)[tp] = ol;
+  }
+}
+
 void update2_normalize(int64_t nv, int nrhs, int nvec, const float2* Vh, const float2* g, const float2* inv,
                        const float4* w, float2* vh, float2* vl, cudaStream_t s) {
   // Vh once per basis vector, w' once, v_{j+1} (both planes) written once
   ProfScope ps(K_ORTH_UPDATE, s, 1, (8.0 * nvec + 32.0) * (double)nv, 8.0 * nvec * (double)nv);
-  MX_LAUNCH(k_update2_normalize<<<grid_for(nv, 256, 152LL * 16), 256, 0, s>>>(nv, nrhs, nvec, Vh, g, inv, w, vh, vl));
+  if (nrhs % 2 == 0)
+    MX_LAUNCH(k_update2_normalize2<<<grid_for(nv / 2, 256, 152LL * 16), 256, 0, s>>>(nv, nrhs, nvec, Vh, g, inv, w,
+                                                                                     vh, vl));
+  else
+    MX_LAUNCH(k_update2_normalize<<<grid_for(nv, 256, 152LL * 16), 256, 0, s>>>(nv, nrhs, nvec, Vh, g, inv, w, vh, vl));
   MX_CHECK_LAUNCH();
 }
 
 template <int RP>
 static void update_rp(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float2* Vl, const float4* hs,
                       const int32_t* active, float4* w, double* npart, cudaStream_t s) {
+  if constexpr (RP >= 2) {
+    if (nrhs % 2 == 0) {
+      MX_LAUNCH(k_orth_update_df2<RP><<<nblk, 256, 0, s>>>(n, nrhs, nvec, Vh, Vl, hs, active, w, npart));
+      return;
+    }
+  }
   MX_LAUNCH(k_orth_update_df<RP><<<nblk, 256, 0, s>>>(n, nrhs, nvec, Vh, Vl, hs, active, w, npart));
 }
 void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float2* Vl, const double2* h,
