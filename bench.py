@@ -203,6 +203,18 @@ def run_ours(args, W, rank, world):
                 launches=launches, clocks=clk, xi_prob=xp, xi_prec=xq)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of a kernel,
+# from an ncu capture of the current kernel on a smaller case of the same workload family
+# (summary under profiles/); the roofline's `traffic` is this ratio times the launch's
+# algorithmic bytes. A kernel absent here reports traffic null.
+DRAM_PER_ALG = {
+    ("local_solve", "mixed"): (
+        1.142, "ncu --set full of k_local_solve_tc on maxwell30_k15_2lvl: 2,093.6 MB DRAM per launch for "
+               "1,832.7 MB algorithmic (panel images padded to 32-row blocks and the inverted diagonal blocks), "
+               "ratio applied to this launch's algorithmic bytes"),
+}
+
+
 def roofline(prof, peak, form="mixed"):
     """Dominant kernel by device time; its achieved rate against the roof it is closest to.
 
@@ -226,8 +238,14 @@ def roofline(prof, peak, form="mixed"):
     f_hbm = gbs / peak["hbm_gbs"]
     f_alu = tfl / alu_peak
     total_ms = sum(v["ms"] for v in prof.values())
+    per_launch = p["bytes"] / max(1, p["launches"])
+    ratio = DRAM_PER_ALG.get((name, form))
     base = {"kernel": name, "launches": p["launches"], "avg_launch_ms": p["ms"] / max(1, p["launches"]),
-            "share_of_device_time": p["ms"] / total_ms if total_ms else None, "traffic": None}
+            "share_of_device_time": p["ms"] / total_ms if total_ms else None,
+            "algorithmic_bytes_per_launch": per_launch,
+            "traffic": ratio[0] * per_launch if ratio else None}
+    if ratio:
+        base["traffic_source"] = ratio[1]
     if f_hbm >= f_alu:
         base.update({"bound": "hbm", "achieved": gbs, "peak": peak["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
                      "peak_source": f"{peak['source']} copy bandwidth"})
@@ -521,7 +539,8 @@ def main():
         "gpu_launches": r["launches"],
         "gpu_launches_per_step": r["launches"] // args.steps,
         "roofline": roof,
-        "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
+        "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps,
+                        "bytes_per_launch": v["bytes"] / v["launches"], "flops_per_launch": v["flops"] / v["launches"]}
                     for k, v in sorted(r["prof"].items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
         "clocks": r["clocks"],
     }
