@@ -434,6 +434,12 @@ template void invert_diag_blocks<double2>(const BandBatch&, const double2*, cons
                                           cudaStream_t);
 
 void factor_local(Problem& P) {
+  factor_local_launch(P);
+  factor_local_finish(P);
+}
+
+// queue the batched LU and the diagonal-block inversion (no host wait)
+void factor_local_launch(Problem& P) {
   if (!P.minors_ready) extract_minors(P);
   BandBatch B{P.n_sub, P.nl.p, P.band.p, P.ld.p, P.mat_off.p};
   int max_span = 0;
@@ -456,6 +462,10 @@ void factor_local(Problem& P) {
     invert_diag_blocks<double2>(B, reinterpret_cast<double2*>(P.factors.p), P.dinv_off.p,
                                 reinterpret_cast<double2*>(P.dinv.p), P.max_local, P.stream);
   }
+}
+
+// wait for the queued factorisation, then the tensor-core panel images
+void factor_local_finish(Problem& P) {
   MX_CUDA(cudaStreamSynchronize(P.stream));
   P.minors_ready = false;
   P.factored = true;

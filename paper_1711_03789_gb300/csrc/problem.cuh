@@ -185,6 +185,9 @@ void build_coarse_restriction(Problem& P);
 // ---- local.cu -----------------------------------------------------------------------
 void extract_minors(Problem& P);
 void factor_local(Problem& P);
+// factor_local in two halves: queue the LU (async), then wait and build the panel images
+void factor_local_launch(Problem& P);
+void factor_local_finish(Problem& P);
 template <typename T2>
 void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status, cudaStream_t s,
              const int32_t* hn, const int32_t* hb, int kid_update, int tc_split);
