@@ -137,6 +137,8 @@ def run_ours(args, W, rank, world):
     nrhs = W["nrhs"]
     centres, pol = inputs.bump_batch(1 + 1000 * rank, nrhs)
 
+    pinned = {}
+
     def step(host):
         P = mx.Problem(W["n"], k, xp, xq, W["core"], W["overlap"], W["coarse"], prec, stream=stream.cuda_stream,
                        bc=mx.MX_BC_IMPEDANCE if args.bc == "imp" else mx.MX_BC_PEC)
@@ -156,8 +158,14 @@ def run_ours(args, W, rank, world):
         P.factor()
         n = P.n_dof
         if host:
-            f = P.load_vector(centres, pol, 0.1)
-            x = np.empty_like(f)
+            # pinned host buffers (allocated once): the load vector comes back to the host and
+            # goes out again with the solve, whose result returns to the host
+            if pinned.get("n") != n:
+                pinned["f"] = torch.empty((nrhs, n), dtype=torch.complex128, pin_memory=True)
+                pinned["x"] = torch.empty((nrhs, n), dtype=torch.complex128, pin_memory=True)
+                pinned["n"] = n
+            f, x = pinned["f"], pinned["x"]
+            P.load_vector(centres, pol, 0.1, out=f)
         else:
             f = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
             P.load_vector(centres, pol, 0.1, out=f)
