@@ -15,29 +15,6 @@ int64_t launch_count();
 Problem::~Problem() {
   free_workspace(*this);
   delete coarse_inner;
-  if (side) {
-    cudaStreamSynchronize(side);
-    cudaEventDestroy(side_fork);
-    cudaEventDestroy(side_done);
-    cudaStreamDestroy(side);
-  }
-}
-
-void side_fork(Problem& P) {
-  if (!P.side) {
-    int least = 0, greatest = 0;
-    MX_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    MX_CUDA(cudaStreamCreateWithPriority(&P.side, cudaStreamNonBlocking, greatest));
-    MX_CUDA(cudaEventCreateWithFlags(&P.side_fork, cudaEventDisableTiming));
-    MX_CUDA(cudaEventCreateWithFlags(&P.side_done, cudaEventDisableTiming));
-  }
-  MX_CUDA(cudaEventRecord(P.side_fork, P.stream));
-  MX_CUDA(cudaStreamWaitEvent(P.side, P.side_fork, 0));
-}
-
-void side_join(Problem& P) {
-  MX_CUDA(cudaEventRecord(P.side_done, P.side));
-  MX_CUDA(cudaStreamWaitEvent(P.stream, P.side_done, 0));
 }
 
 // ---- layout helpers -----------------------------------------------------------------

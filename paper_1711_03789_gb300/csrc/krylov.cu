@@ -332,18 +332,11 @@ void precond_apply(Problem& P, const void* v, void* z, int ztype, int nrhs, int 
     MX_CHECK_LAUNCH();
     return;
   }
+  // (running the coarse solve concurrently with the local solves gains under 1 % of the step:
+  // both read HBM, and the memory-bound local solves lose what the coarse solve saves)
+  if (levels & 1) local_solves(P, v, vtype, W.loc.p, nrhs);
   const bool coarse = (levels & 2) && P.coarse_m;
-  if ((levels & 1) && coarse) {
-    // the two levels read only v: the coarse solve runs on the side stream next to the
-    // local solves (which hold one CTA per SM and leave registers and a tail wave free)
-    side_fork(P);
-    local_solves(P, v, vtype, W.loc.p, nrhs);
-    on_side(P, [&] { coarse_solve(P, v, vtype, W.yc.p, nrhs); });
-    side_join(P);
-  } else {
-    if (levels & 1) local_solves(P, v, vtype, W.loc.p, nrhs);
-    if (coarse) coarse_solve(P, v, vtype, W.yc.p, nrhs);
-  }
+  if (coarse) coarse_solve(P, v, vtype, W.yc.p, nrhs);
   scatter(P, W, z, ztype, nrhs, (levels & 1) != 0, coarse, own, zc);
 }
 

@@ -144,10 +144,6 @@ struct Problem {
 
   Workspace* ws = nullptr;
   Timing timing;
-  // high-priority side stream for work that overlaps the handle's stream (the coarse solve
-  // of the additive preconditioners next to the local solves); created on first use
-  cudaStream_t side = nullptr;
-  cudaEvent_t side_fork = nullptr, side_done = nullptr;
 
   ~Problem();
 };
@@ -218,21 +214,6 @@ void local_solves_tc(Problem& P, const void* v, int vtype, void* loc, int nrhs, 
 void factor_coarse(Problem& P);
 // y = (A^0)^{-1} R^0 v: coarse_rhs [nrhs][n_c] c128 workspace
 void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs);
-// fork the side stream from P.stream (it waits for the work queued so far), run f with P.stream
-// pointing at it, and return; side_join makes P.stream wait for everything run there
-void side_fork(Problem& P);
-void side_join(Problem& P);
-template <typename F> void on_side(Problem& P, F&& f) {
-  cudaStream_t main = P.stream;
-  P.stream = P.side;
-  try {
-    f();
-  } catch (...) {
-    P.stream = main;
-    throw;
-  }
-  P.stream = main;
-}
 
 // ---- krylov.cu ----------------------------------------------------------------------
 // y = A_{xi} x; x c128 or c64 [nrhs][n] (xtype 0/1), y c128
