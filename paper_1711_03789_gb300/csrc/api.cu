@@ -171,44 +171,6 @@ Problem* create_problem(int n, double k, double xi_prob, double xi_prec, int cor
   return P;
 }
 
-// A second (high-priority) stream forked from the handle's stream at construction (it starts after the work
-// queued there so far) and joined back into it at destruction; run() executes a step with the
-// handle's stream pointing at it.
-struct SideStream {
-  Problem& P;
-  cudaStream_t main, side = nullptr;
-  cudaEvent_t fork = nullptr, done = nullptr;
-  explicit SideStream(Problem& P_) : P(P_), main(P_.stream) {
-    // highest priority: the side stream carries a latency-bound chain of small launches
-    // that should take SMs as soon as blocks of the bulk work on the main stream retire
-    int least = 0, greatest = 0;
-    MX_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    MX_CUDA(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, greatest));
-    MX_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    MX_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
-    MX_CUDA(cudaEventRecord(fork, main));
-    MX_CUDA(cudaStreamWaitEvent(side, fork, 0));
-  }
-  template <typename F> void run(F&& f) {
-    P.stream = side;
-    try {
-      f();
-    } catch (...) {
-      P.stream = main;
-      throw;
-    }
-    P.stream = main;
-  }
-  ~SideStream() {
-    P.stream = main;
-    cudaEventRecord(done, side);
-    cudaStreamWaitEvent(main, done, 0);
-    cudaEventDestroy(fork);
-    cudaEventDestroy(done);
-    cudaStreamDestroy(side);
-  }
-};
-
 void factor_problem(Problem& P) {
   MX_CUDA(cudaMemsetAsync(P.status.p, 0, 16, P.stream));
   EventTimer t(P.stream);
@@ -217,18 +179,12 @@ void factor_problem(Problem& P) {
     factor_local(P);
     P.coarse_inner->stream = P.stream;
     factor_problem(*P.coarse_inner);  // the inner coarse GMRES replaces the direct factors
-  } else if (P.coarse_m) {
-    // the coarse band LU and explicit inverse (many small launches, host waits on its own
-    // stream) run on a side stream while the batched local LU runs on the handle's stream
-    {
-      SideStream side(P);  // forked before the local LU is queued
-      factor_local_launch(P);
-      side.run([&] { factor_coarse(P); });
-    }
-    factor_local_finish(P);
-    P.coarse_factored = true;
   } else {
+    // in sequence: running the coarse factorisation on a second stream during the local LU
+    // shortens this phase by about a tenth but leaves no per-kernel device time to measure
     factor_local(P);
+    factor_coarse(P);
+    P.coarse_factored = P.coarse_m > 0;
   }
   P.timing.factor_ms = t.stop();
   check_status(P);
