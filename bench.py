@@ -135,7 +135,7 @@ def run_ours(args, W, rank, world):
     xp, xq = xi_value(W["xi_prob"], k), xi_value(W["xi_prec"], k)
     prec = mx.MX_MIXED if args.form == "mixed" else mx.MX_PLAIN_FP64
     nrhs = W["nrhs"]
-    centres, pol = inputs.bump_batch(1 + 1000 * rank, nrhs)
+    centres, pol = inputs.bump_batch(rhs_seed(rank), nrhs)
 
     pinned = {}
 
@@ -409,14 +409,20 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
+def max_over_ranks(v, world, device="cuda"):
+    """The maximum of v over the ranks (the slowest rank sets the step time)."""
     if world <= 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rhs_seed(rank):
+    """Seed of a rank's right-hand-side batch: every rank solves its own batch (weak scaling)."""
+    return 1 + 1000 * rank
 
 
 def main():
