@@ -334,12 +334,91 @@ def cpu_baseline(W, iterations, budget_s=20.0):
     t_arn = (time.perf_counter() - t0) * scale_dof * nrhs
     per_it = n_sub * t_sol + t_spmv + t_arn
     step = t_build_s * scale_dof + n_sub * t_fac + iterations * per_it
-    return {"value": step, "unit": "s", "cores": 1, "kind": "oracle",
+    return {"value": step, "unit": "s", "cores": 1, "kind": "oracle", "t_fac": t_fac, "t_sol": t_sol,
             "sample": (f"oracle build on {ns}^3 cells scaled by unknowns; splu factor+solve of the {done} largest of "
                        f"{n_sub} subdomain minors scaled to all, {nrhs} rhs; SpMV and one CGS Arnoldi step at "
                        f"j={jm} scaled by unknowns; x {iterations} iterations; "
                        f"{time.perf_counter() - t_start:.1f} s of CPU work"),
             "per_iteration_s": per_it}
+
+
+_SUB = {}
+
+
+def _oracle_sub_init(n, k, xq, core, overlap, ready):
+    """Process-pool initializer: the sample geometry's matrix and subdomain lists, once per
+    worker; returns when every worker has them (barrier), so no timed job overlaps a set-up."""
+    from oracle.mesh import KuhnMesh
+    from oracle import fem, dd
+    m = KuhnMesh(n)
+    K, M = fem.assemble_KM(m)
+    _SUB["A"] = fem.a_xi(K, M, k, xq)
+    _SUB["idx"] = [dd.local_dofs(m, lo, hi) for lo, hi in dd.subdomain_boxes(n, core, overlap)]
+    ready.wait(600)
+
+
+def _oracle_sub_job(job):
+    """One subdomain's oracle factor + multi-RHS solve (process-pool worker); returns its own
+    wall time."""
+    l, nrhs = job
+    import scipy.sparse.linalg as spla
+    t0 = time.perf_counter()
+    i = _SUB["idx"][l]
+    sub = _SUB["A"][i][:, i].tocsc()
+    lu = spla.splu(sub)
+    lu.solve(np.ones((sub.shape[0], nrhs), dtype=np.complex128))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_allcore(W, iterations, single, budget_s=12.0):
+    """The oracle's subdomain factor + solve (the part of a step that runs per subdomain) on a
+    process pool of all host cores (spawn), on the same 30^3 sample geometry as cpu_baseline;
+    the rest of the step (build, SpMV, Arnoldi) keeps its single-thread time."""
+    import multiprocessing as mpr
+    cores = os.cpu_count() or 1
+    n, k = W["n"], W["k"]
+    xq = xi_value(W["xi_prec"], k)
+    ns = min(n, 30)
+    N = -(-ns // W["core"])
+    from oracle.mesh import count_interior_edges
+    from oracle import dd
+    # largest subdomains first, as in the single-thread sample
+    sizes = [count_interior_edges(*(hi - lo).tolist()) for lo, hi in dd.subdomain_boxes(ns, W["core"], W["overlap"])]
+    jobs = [(l, W["nrhs"]) for l in sorted(range(N ** 3), key=lambda l: -sizes[l])]
+    ctx = mpr.get_context("spawn")
+    t_start = time.perf_counter()
+    ready = ctx.Barrier(cores)
+    threads = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({v: "1" for v in threads})  # one thread per worker process
+    try:
+        pool = ctx.Pool(cores, initializer=_oracle_sub_init, initargs=(ns, k, xq, W["core"], W["overlap"], ready))
+    finally:
+        for v, old in threads.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    with pool:
+        # every worker times its own jobs; with all cores busy the pool completes `cores` jobs per
+        # median job time
+        times = list(pool.imap_unordered(_oracle_sub_job, jobs[:cores], chunksize=1))  # waits for the set-up
+        t0 = time.perf_counter()
+        for chunk in range(cores, len(jobs), cores):
+            if time.perf_counter() - t0 > budget_s:
+                break
+            times += list(pool.imap_unordered(_oracle_sub_job, jobs[chunk:chunk + cores], chunksize=1))
+        done = len(times)
+        rate = cores / float(np.median(times))  # subdomains (factor + one solve) per second, all cores
+    n_sub = (-(-n // W["core"])) ** 3
+    # the single-thread split: per subdomain factor and solve; keep the non-subdomain work serial
+    per_sub_single = (single["t_fac"] + single["t_sol"])
+    serial = single["value"] - n_sub * single["t_fac"] - iterations * n_sub * single["t_sol"]
+    speed = rate * per_sub_single  # all-core speed-up of the subdomain work
+    value = serial + (n_sub * single["t_fac"] + iterations * n_sub * single["t_sol"]) / max(speed, 1e-9)
+    return {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": (f"subdomain factor + solve of {done} subdomains of the 30^3 geometry on a {cores}-process pool "
+                       f"({rate:.1f} per s, {speed:.1f} x one core); build, SpMV and Arnoldi single-threaded; "
+                       f"{time.perf_counter() - t_start:.1f} s wall")}
 
 
 def run_serving(args):
@@ -564,6 +643,7 @@ def main():
     }
     if world == 1 and not args.no_cpu_baseline and args.bc == "pec":
         line["cpu_baseline"] = cpu_baseline(W, iters)
+        line["cpu_baseline_allcore"] = cpu_baseline_allcore(W, iters, line["cpu_baseline"])
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
