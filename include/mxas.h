@@ -335,6 +335,8 @@ typedef struct {
   double width;
   double tol;              /* GMRES settings as in mx_solve */
   int restart, max_it;
+  int boundary;            /* MX_BC_PEC or MX_BC_IMPEDANCE (mx_mesh_desc) */
+  int prec_kind;           /* MX_PREC_AS, _RAS, _HRAS or _ADEF1 (mx_set_preconditioner) */
 } mx_request;
 
 typedef struct {

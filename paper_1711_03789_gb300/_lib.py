@@ -396,7 +396,7 @@ class MxRequest(C.Structure):
                 ("core_cells", C.c_int), ("overlap_cells", C.c_int), ("coarse_cells", C.c_int),
                 ("precision", C.c_int), ("nrhs", C.c_int), ("nbumps", C.c_int), ("centres", C.c_void_p),
                 ("pol", C.c_void_p), ("width", C.c_double), ("tol", C.c_double), ("restart", C.c_int),
-                ("max_it", C.c_int)]
+                ("max_it", C.c_int), ("boundary", C.c_int), ("prec_kind", C.c_int)]
 
 
 class RequestTiming(C.Structure):
@@ -429,13 +429,14 @@ def mx_server_create(budget_bytes, workers=2):
 
 
 def mx_server_submit(s, n_cells, k, xi_prob, xi_prec, centres, pol, width=0.1, core_cells=5, overlap_cells=1,
-                     coarse_cells=0, precision=MX_MIXED, tol=1e-6, restart=0, max_it=200):
+                     coarse_cells=0, precision=MX_MIXED, tol=1e-6, restart=0, max_it=200, bc=MX_BC_PEC,
+                     prec_kind=MX_PREC_AS):
     """Queue one request (centres [nrhs, nbumps, 3], pol [nrhs, nbumps, 3] complex); returns its ticket."""
     centres = np.ascontiguousarray(centres, dtype=np.float64)
     pol = np.ascontiguousarray(pol, dtype=np.complex128)
     q = MxRequest(n_cells, k, xi_prob, xi_prec, core_cells, overlap_cells, coarse_cells, precision,
                   centres.shape[0], centres.shape[1], centres.ctypes.data, pol.ctypes.data, width, tol, restart,
-                  max_it)
+                  max_it, int(bc), int(prec_kind))
     t = C.c_int64()
     _check(lib.mx_server_submit(s, C.byref(q), C.byref(t)))
     return t.value

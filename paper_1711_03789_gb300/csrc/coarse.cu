@@ -82,7 +82,9 @@ void factor_coarse(Problem& P) {
     P.c_dinvf.alloc(nq * 2 * CB * CB);
     invert_diag_blocks<float2>(B, P.A0f.p, P.c_off.p, P.c_dinvf.p, (int)nc, s);
     P.A0inv.reset();
-    if (P.tune_coarse_inverse) {
+    // the inverse's band solve keeps (b + CB) rows of 8 right-hand sides in shared memory
+    const bool fits = nc <= COARSE_INVERSE_MAX && (size_t)(b + CB) * 8 * sizeof(float2) <= 200 * 1024;
+    if (P.tune_coarse_inverse && fits) {
       MX_CUDA(cudaStreamSynchronize(s));
       P.A0inv.alloc((size_t)nc * nc);
       coarse_inverse(P, P.A0inv.p);

@@ -14,6 +14,8 @@ static alloc_fn g_alloc = nullptr;
 static free_fn g_free = nullptr;
 static void* g_ctx = nullptr;
 
+bool allocator_hooked() { return g_alloc != nullptr; }
+
 void set_allocator(alloc_fn a, free_fn f, void* ctx) {
   g_alloc = a;
   g_free = f;

@@ -333,8 +333,10 @@ int64_t local_factor_bytes(Problem& P) {
   for (int l = 0; l < P.n_sub; ++l) blocks += (P.h_nl[l] + NB - 1) / NB;
   const int64_t panels = P.tune_local_tc ? panel_bytes_planned(P) : 0;
   // the explicit coarse inverse of the mixed form (the band factors of A^0 are smaller)
-  const int64_t cinv = (P.coarse_m && P.precision == MX_MIXED && P.tune_coarse_inverse)
-                           ? (int64_t)sizeof(float2) * P.coarse.n_dof * P.coarse.n_dof : 0;
+  const int64_t cinv =
+      (P.coarse_m && P.precision == MX_MIXED && P.tune_coarse_inverse && P.coarse.n_dof <= COARSE_INVERSE_MAX)
+          ? (int64_t)sizeof(float2) * P.coarse.n_dof * P.coarse.n_dof
+          : 0;
   return esz * (P.h_mat_off[P.n_sub] + blocks * 2 * NB * NB) + panels + cinv;
 }
 

@@ -129,7 +129,7 @@ struct Problem {
   DevBuf<float2> c_dinvf; // c64 copy (mixed)
   // mixed form: the explicit c64 inverse of A^0 (row-major; A^0 is complex symmetric, so
   // is its inverse), applied as one dense product instead of the band sweeps
-  int tune_coarse_inverse = 1;
+  int tune_coarse_inverse = 1;     // used while n_c <= COARSE_INVERSE_MAX and the band fits the solve window
   DevBuf<float2> A0inv;
   DevBuf<float2> c_part;  // split-K partial products of the dense coarse apply
   DevBuf<int32_t> status; // [4] device error words: 0 local pivot, 1 coarse pivot, 2 timeout
@@ -147,6 +147,10 @@ struct Problem {
 
   ~Problem();
 };
+
+// the explicit c64 coarse inverse is formed for coarse problems up to this size (n_c^2 c64
+// entries: 2.1 GB); larger coarse problems keep the band sweeps
+constexpr int64_t COARSE_INVERSE_MAX = 16384;
 
 // ---- api.cu -------------------------------------------------------------------------
 // validate, build mesh / assembly / subdomains / coarse space on `stream` (throws Error)

@@ -31,16 +31,18 @@
 
 namespace mx {
 
+bool allocator_hooked();  // common.cu: a device-allocation hook is installed
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
 
 struct Key {
-  int n, core, overlap, coarse, precision;
+  int n, core, overlap, coarse, precision, bc, prec;
   double k, xi_prec;
   bool operator<(const Key& o) const {
-    return std::tie(n, core, overlap, coarse, precision, k, xi_prec) <
-           std::tie(o.n, o.core, o.overlap, o.coarse, o.precision, o.k, o.xi_prec);
+    return std::tie(n, core, overlap, coarse, precision, bc, prec, k, xi_prec) <
+           std::tie(o.n, o.core, o.overlap, o.coarse, o.precision, o.bc, o.prec, o.k, o.xi_prec);
   }
   bool operator==(const Key& o) const { return !(*this < o) && !(o < *this); }
 };
@@ -164,7 +166,8 @@ struct Server {
       try {
         if (create) {
           std::unique_ptr<Problem> P(create_problem(key.n, key.k, batch[0]->xi_prob, key.xi_prec, key.core,
-                                                    key.overlap, key.coarse, key.precision, s));
+                                                    key.overlap, key.coarse, key.precision, s, key.bc));
+          P->prec_kind = key.prec;
           const int m = batch[0]->restart > 0 ? std::min(batch[0]->restart, batch[0]->max_it) : batch[0]->max_it;
           const int64_t need = local_factor_bytes(*P) + workspace_bytes(key, P->fine.n_dof, nrhs, m);
           // admission: memory budget (after evictions) and the device's free memory
@@ -178,7 +181,9 @@ struct Server {
               if (admitted) cached_bytes += need;
             }
             size_t fr = 0, tot = 0;
-            if (admitted && cudaMemGetInfo(&fr, &tot) == cudaSuccess && (int64_t)fr < need) {
+            // the device's free memory says something only when the library allocates from the
+            // driver itself: a caching allocator keeps freed blocks, which it will hand out again
+            if (admitted && !allocator_hooked() && cudaMemGetInfo(&fr, &tot) == cudaSuccess && (int64_t)fr < need) {
               std::lock_guard<std::mutex> g(mu);
               cached_bytes -= need;
               admitted = false;
@@ -288,12 +293,19 @@ MX_API int mx_server_submit(mx_server sv, const mx_request* q, int64_t* ticket) 
     MX_REQUIRE(q->nrhs >= 1 && q->nrhs <= 32 && q->nbumps >= 1 && q->centres && q->pol && q->width > 0 && q->tol > 0 &&
                    q->max_it >= 1 && q->restart >= 0,
                MX_EINVAL, "bad request");
-    MX_REQUIRE(q->n_cells >= 1 && q->core_cells >= 1 && q->k > 0 && q->xi_prec != 0 &&
+    MX_REQUIRE(q->n_cells >= 1 && q->core_cells >= 1 && q->k > 0 &&
+                   (q->xi_prec != 0 || q->boundary == MX_BC_IMPEDANCE) &&
+                   (q->boundary == MX_BC_PEC || q->boundary == MX_BC_IMPEDANCE) &&
                    (q->coarse_cells == 0 || q->n_cells % q->coarse_cells == 0),
                MX_EINVAL, "bad operator in request");
+    MX_REQUIRE(q->prec_kind >= MX_PREC_AS && q->prec_kind <= MX_PREC_ADEF1 &&
+                   (q->prec_kind == MX_PREC_AS || q->overlap_cells >= 1) &&
+                   (q->prec_kind <= MX_PREC_RAS || q->coarse_cells > 0),
+               MX_EINVAL, "bad preconditioner in request");
     auto S = reinterpret_cast<Server*>(sv);
     auto r = std::make_unique<Req>();
-    r->key = Key{q->n_cells, q->core_cells, q->overlap_cells, q->coarse_cells, q->precision, q->k, q->xi_prec};
+    r->key = Key{q->n_cells, q->core_cells, q->overlap_cells, q->coarse_cells, q->precision,
+                 q->boundary, q->prec_kind, q->k, q->xi_prec};
     r->xi_prob = q->xi_prob;
     r->tol = q->tol;
     r->restart = q->restart;
