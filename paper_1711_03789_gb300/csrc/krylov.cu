@@ -971,11 +971,14 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     {
       int kmax = 0;
       for (int r = 0; r < nrhs; ++r) kmax = std::max(kmax, kcols[r]);
-      ProfScope ps(K_UPDATE_X, s, 2, ((double)zsz * kmax + 32.0) * (double)nv, 8.0 * kmax * (double)nv);
+      ProfScope ps(K_UPDATE_X, s, mixed ? 3 : 2, ((double)zsz * kmax + 32.0) * (double)nv, 8.0 * kmax * (double)nv);
     MX_LAUNCH(k_backsolve<<<1, 32, 0, s>>>(nrhs, m, dk.p, W.H.p, W.g.p, W.y.p));
-    if (mixed) MX_LAUNCH(k_update_x<float2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const float2*)W.Z.p, W.y.p, W.x.p));
-    else MX_LAUNCH(k_update_x<double2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const double2*)W.Z.p, W.y.p, W.x.p));
-    MX_CHECK_LAUNCH();
+    if (mixed) {
+      update_x_df(nv, nrhs, kmax, dk.p, (const float2*)W.Z.p, W.y.p, W.hs.p, W.x.p, s);
+    } else {
+      MX_LAUNCH(k_update_x<double2><<<gv, 256, 0, s>>>(n, nrhs, dk.p, (const double2*)W.Z.p, W.y.p, W.x.p));
+      MX_CHECK_LAUNCH();
+    }
     }
     true_residual(P, W, s);
     launches += 4;

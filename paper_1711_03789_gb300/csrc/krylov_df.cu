@@ -742,6 +742,39 @@ void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, c
   MX_CHECK_LAUNCH();
 }
 
+// x[t] += sum_{i < kcols[r]} z_i[t] y_i[r] (mixed form): z c64, y as double-float pairs (ys), the
+// sum in double-float, added to the FP64 x once -- FP32 units instead of four FP64 FMAs per term
+__global__ void __launch_bounds__(256) k_update_x_df(int64_t nv, int nrhs, const int32_t* __restrict__ kcols,
+                                                     const float2* __restrict__ Z, const float4* __restrict__ ys,
+                                                     double2* __restrict__ x) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nrhs);
+    const int k = kcols[r];
+    if (k == 0) continue;
+    df::Acc re, im;
+#pragma unroll 4
+    for (int i = 0; i < k; ++i) {
+      const float2 z = Z[(int64_t)i * nv + t];
+      const float4 c = ys[i * nrhs + r];  // {re_hi, im_hi, re_lo, im_lo}
+      df::add_prod(re, c.x, c.z, z.x);
+      df::add_prod(re, -c.y, -c.w, z.y);
+      df::add_prod(im, c.y, c.w, z.x);
+      df::add_prod(im, c.x, c.z, z.y);
+    }
+    const double2 a = x[t];
+    x[t] = make_double2(a.x + df::to_double(re), a.y + df::to_double(im));
+  }
+}
+
+void update_x_df(int64_t nv, int nrhs, int kmax, const int32_t* kcols, const float2* Z, const double2* y, float4* ys,
+                 double2* x, cudaStream_t s) {
+  if (kmax <= 0) return;
+  MX_LAUNCH(k_split_h<<<grid_for((int64_t)kmax * nrhs, 128), 128, 0, s>>>(kmax * nrhs, y, ys));
+  MX_CHECK_LAUNCH();
+  MX_LAUNCH(k_update_x_df<<<grid_for(nv, 256, 152LL * 16), 256, 0, s>>>(nv, nrhs, kcols, Z, ys, x));
+  MX_CHECK_LAUNCH();
+}
+
 void normalize_df(int64_t nv, int nrhs, int j, int m, const double2* H, const int32_t* active, const float4* w,
                   float2* vh, float2* vl, cudaStream_t s) {
   ProfScope ps(K_ARNOLDI_SMALL, s, 1, 32.0 * (double)nv, 2.0 * (double)nv);

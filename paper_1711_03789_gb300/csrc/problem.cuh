@@ -245,6 +245,9 @@ void dots_c64(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const f
 // v_{j+1} = (w' - Vh g) inv into the planes (g: c64 pass-2 coefficients, inv: 1/||w''|| split)
 void update2_normalize(int64_t nv, int nrhs, int nvec, const float2* Vh, const float2* g, const float2* inv,
                        const float4* w, float2* vh, float2* vl, cudaStream_t s);
+// x += Z y over the first kcols[r] columns (kmax the largest), Z c64, y FP64 (split into ys)
+void update_x_df(int64_t nv, int nrhs, int kmax, const int32_t* kcols, const float2* Z, const double2* y, float4* ys,
+                 double2* x, cudaStream_t s);
 // y = D_k w, D_k = K + k^2 M, double-float vectors
 void dmul_df(Problem& P, const float4* w, float4* y, int nrhs, cudaStream_t s);
 void orth_update_df(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float2* Vl, const double2* h,
