@@ -378,16 +378,24 @@ __global__ void __launch_bounds__(256) k_dots(int64_t n, int nrhs, int nvec, int
   }
 }
 
-// h[i][r] = sum_blk hpart[blk][i][r] in block order (deterministic)
+// h[i][r] = sum_blk hpart[blk][i][r]: one warp per output, lane l sums blocks l, l + 32, ...,
+// then a fixed shuffle tree (deterministic)
 __global__ void k_reduce_dots(int nblk, int total, int nrhs, const double2* hpart, double2* h) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total * nrhs; t += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total * nrhs; t += warps) {
     double ax = 0, ay = 0;
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = lane; b < nblk; b += 32) {
       const double2 v = hpart[(int64_t)b * total * nrhs + t];
       ax += v.x;
       ay += v.y;
     }
-    h[t] = make_double2(ax, ay);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) h[t] = make_double2(ax, ay);
   }
 }
 
@@ -717,7 +725,7 @@ static void dots(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t 
   }
   const int total = nvec + with_norm;
   ProfScope ps(K_ARNOLDI_SMALL, s);
-  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * nr, 128), 128, 0, s>>>(W.nblk, total, nr, W.hpart.p, W.h2.p));
+  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * nr * 32, 256), 256, 0, s>>>(W.nblk, total, nr, W.hpart.p, W.h2.p));
   MX_CHECK_LAUNCH();
 }
 
@@ -735,7 +743,7 @@ static void dots_mixed(Workspace& W, int64_t n, int nvec, int with_norm, cudaStr
           reinterpret_cast<const float4*>(extra));
   const int total = nvec + with_norm;
   ProfScope ps(K_ARNOLDI_SMALL, s);
-  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * W.nrhs, 128), 128, 0, s>>>(nb, total, W.nrhs, W.hpart.p,
+  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * W.nrhs * 32, 256), 256, 0, s>>>(nb, total, W.nrhs, W.hpart.p,
                                                                                    W.h2.p));
   MX_CHECK_LAUNCH();
 }
@@ -793,7 +801,7 @@ void batched_dots(const double2* V, const double2* w, int64_t n, int nrhs, int n
   else MX_DOTS(32);
 #undef MX_DOTS
   MX_CHECK_LAUNCH();
-  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)nvec * nrhs, 128), 128, 0, s>>>(nblk, nvec, nrhs, partials, h));
+  MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)nvec * nrhs * 32, 256), 256, 0, s>>>(nblk, nvec, nrhs, partials, h));
   MX_CHECK_LAUNCH();
 }
 
@@ -903,7 +911,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
         dots_c64(nb, n, nrhs, j + 1, Vh, reinterpret_cast<const float4*>(W.w.p), W.active.p, W.hpart.p, s);
         {
           ProfScope ps(K_ARNOLDI_SMALL, s);
-          MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)(j + 1) * nrhs, 128), 128, 0, s>>>(nb, j + 1, nrhs, W.hpart.p,
+          MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)(j + 1) * nrhs * 32, 256), 256, 0, s>>>(nb, j + 1, nrhs, W.hpart.p,
                                                                                            W.h2.p));
           MX_LAUNCH(k_cgs2_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, 0, W.h2.p, W.npart.p, W.H.p, W.active.p,
                                                   W.g2.p, W.inv2.p));
