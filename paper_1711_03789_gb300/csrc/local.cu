@@ -149,27 +149,42 @@ __global__ void k_lu_panel(BandBatch B, T2* A, int k0) {
   const bool rows = (int)blockIdx.y < chunks;
   const int idx = ((rows ? blockIdx.y : blockIdx.y - chunks) * blockDim.x) + threadIdx.x;
   if (idx >= span) return;
+  // loops fully unrolled over NB (entries k >= kb are zero and unused), so x stays in registers
   T2 x[NB];
   if (rows) {
     const int i = k1 + idx;
-    for (int k = 0; k < kb; ++k) x[k] = (i - (k0 + k) <= b) ? A[bidx(off, ld, b, i, k0 + k)] : czero<T2>();
-    for (int k = 0; k < kb; ++k) {  // x U11 = a
-      T2 v = x[k];
-      for (int j = 0; j < k; ++j) cfms(v, x[j], s[j][k]);
-      x[k] = cmul(v, crcp(s[k][k]));
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      x[k] = (k < kb && i - (k0 + k) <= b) ? A[bidx(off, ld, b, i, k0 + k)] : czero<T2>();
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {  // x U11 = a
+      if (k < kb) {
+        T2 v = x[k];
+#pragma unroll
+        for (int j = 0; j < k; ++j) cfms(v, x[j], s[j][k]);
+        x[k] = cmul(v, crcp(s[k][k]));
+      }
     }
-    for (int k = 0; k < kb; ++k)
-      if (i - (k0 + k) <= b) A[bidx(off, ld, b, i, k0 + k)] = x[k];
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      if (k < kb && i - (k0 + k) <= b) A[bidx(off, ld, b, i, k0 + k)] = x[k];
   } else {
     const int j = k1 + idx;
-    for (int k = 0; k < kb; ++k) x[k] = (j - (k0 + k) <= b) ? A[bidx(off, ld, b, k0 + k, j)] : czero<T2>();
-    for (int k = 0; k < kb; ++k) {  // L11 y = a (unit lower)
-      T2 v = x[k];
-      for (int j2 = 0; j2 < k; ++j2) cfms(v, s[k][j2], x[j2]);
-      x[k] = v;
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      x[k] = (k < kb && j - (k0 + k) <= b) ? A[bidx(off, ld, b, k0 + k, j)] : czero<T2>();
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {  // L11 y = a (unit lower)
+      if (k < kb) {
+        T2 v = x[k];
+#pragma unroll
+        for (int j2 = 0; j2 < k; ++j2) cfms(v, s[k][j2], x[j2]);
+        x[k] = v;
+      }
     }
-    for (int k = 0; k < kb; ++k)
-      if (j - (k0 + k) <= b) A[bidx(off, ld, b, k0 + k, j)] = x[k];
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      if (k < kb && j - (k0 + k) <= b) A[bidx(off, ld, b, k0 + k, j)] = x[k];
   }
 }
 
