@@ -693,15 +693,19 @@ __global__ void __launch_bounds__(256, (sizeof(T2) == 8 && G < 16 ? 3 : 2)) k_lo
     __syncthreads();
   }
 
-  // ---- backward sweep: U z = y, blocks from the bottom
+  // ---- backward sweep: U z = y, blocks from the bottom. Identity right-hand sides form a
+  // complex symmetric inverse: column j is needed only in rows >= j (the rest comes from
+  // the transpose), so the sweep stops at g0's block; the rows above keep the zeros written
+  // by the forward sweep until the caller mirrors the lower triangle.
   const int nblk = (n + NB - 1) / NB;
+  const int bstop = cstart / NB;
   const int top0 = max(0, n - win);
   for (int t = tid; t < (n - top0) * G; t += nt) {
     const int i = top0 + t / G, g = t % G;
     W[(i % win) * G + g] = (g < gn) ? out[(pos0 + i) * a.nrhs + g0 + g] : czero<T2>();
   }
   __syncthreads();
-  for (int blk = nblk - 1; blk >= 0; --blk) {
+  for (int blk = nblk - 1; blk >= bstop; --blk) {
     const int c0 = blk * NB, c1 = min(c0 + NB, n);
     // diagonal block: x_blk = U_qq^{-1} r_blk with the precomputed inverse
     diag_apply<T2, G, true>(Dinv + doff + (int64_t)(c0 / NB) * 2 * NB * NB + NB * NB, c0, c1 - c0, W, win, Ds);
@@ -734,6 +738,24 @@ static void launch_local_solve(const SolveArgs& a, int win, cudaStream_t s, int 
   ProfScope ps(kid, s, 1, a.alg_bytes, a.alg_flops);
   MX_LAUNCH(k_local_solve<T2, G><<<a.n_sub * groups, 256, smem, s>>>(a));
   MX_CHECK_LAUNCH();
+}
+
+// X[i][j] = X[j][i] for i < j (row-major n x n): fills the upper triangle of a complex
+// symmetric matrix from its lower triangle, 32 x 32 tiles staged in shared memory
+__global__ void k_mirror_lower(int n, float2* X) {
+  __shared__ float2 t[32][33];
+  const int ti = blockIdx.y, tj = blockIdx.x;  // target tile (rows ti, columns tj), ti <= tj
+  if (ti > tj) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {  // source tile (rows tj, columns ti), coalesced along ti
+    const int i = tj * 32 + r, j = ti * 32 + tx;
+    if (i < n && j < n) t[r][tx] = X[(int64_t)i * n + j];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = ti * 32 + r, j = tj * 32 + tx;
+    if (i < n && j < n && i < j) X[(int64_t)i * n + j] = t[tx][r];
+  }
 }
 
 __global__ void k_iota(int n, int32_t* p) {
@@ -777,9 +799,15 @@ void coarse_inverse(Problem& P, float2* X) {
   MX_REQUIRE((size_t)a.win * 8 * sizeof(float2) <= 200 * 1024, MX_EINVAL, "coarse bandwidth too large for the inverse");
   const double entries = (double)nc * (2.0 * b + 1.0) - (double)b * (b + 1.0);
   a.alg_bytes = 8.0 * entries + 8.0 * (double)nc * nc;
-  a.alg_flops = 8.0 * entries * nc;
+  a.alg_flops = 4.0 * entries * nc;  // each sweep covers about half of the columns' rows
   if ((size_t)a.win * 16 * sizeof(float2) <= 100 * 1024) launch_local_solve<float2, 16>(a, a.win, s, K_COARSE_INV);
   else launch_local_solve<float2, 8>(a, a.win, s, K_COARSE_INV);
+  {
+    ProfScope ps(K_COARSE_INV, s, 1, 16.0 * (double)nc * nc, 0.0);
+    const unsigned tl = (unsigned)((nc + 31) / 32);
+    MX_LAUNCH(k_mirror_lower<<<dim3(tl, tl), dim3(32, 8), 0, s>>>((int)nc, X));
+    MX_CHECK_LAUNCH();
+  }
   MX_CUDA(cudaStreamSynchronize(s));
 }
 
