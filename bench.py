@@ -126,6 +126,7 @@ def run_ours(args, W, rank, world):
     import torch
     import inputs
     import paper_1711_03789_gb300 as mx
+    from paper_1711_03789_gb300 import autotune
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
@@ -138,10 +139,13 @@ def run_ours(args, W, rank, world):
     centres, pol = inputs.bump_batch(rhs_seed(rank), nrhs)
 
     pinned = {}
+    tuned = {}
 
-    def step(host):
+    def make_problem():
         P = mx.Problem(W["n"], k, xp, xq, W["core"], W["overlap"], W["coarse"], prec, stream=stream.cuda_stream,
                        bc=mx.MX_BC_IMPEDANCE if args.bc == "imp" else mx.MX_BC_PEC)
+        if tuned:
+            autotune.apply(P, tuned)
         if args.local_tensor is not None:
             mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, args.local_tensor)
         if args.lu_tensor is not None:
@@ -155,6 +159,24 @@ def run_ours(args, W, rank, world):
             # inexact coarse solve (Sec. 6.4): inner GMRES with one-level Schwarz on the coarse mesh
             P.set_coarse_solver(mx.MX_COARSE_GMRES, args.coarse_gmres, 1, args.coarse_tol, args.coarse_max_it,
                                 mx.MX_PREC_RAS if args.coarse_inner == "ras" else mx.MX_PREC_AS)
+        return P
+
+    if args.autotune:
+        # knob search (or cache lookup) on one problem of the workload, before the clock
+        P = make_problem()
+        tag = (f"{args.workload}/{args.form}/{args.bc}/{args.precond}/w{int(args.weighted)}/"
+               f"cg{args.coarse_gmres}:{args.coarse_inner}:{args.coarse_tol}/k{k}/xp{xp}/xq{xq}")
+        res = autotune.tune(P, nrhs=nrhs, tol=W["tol"], restart=W["restart"], max_it=W["max_it"],
+                            cache_path=args.autotune, tag=tag)
+        P.close()
+        tuned.update(res["knobs"])
+        tuned_info = {"knobs": dict(tuned), "cached": res["cached"], "cost_ms": res["cost_ms"],
+                      "default_ms": res["default_ms"]}
+    else:
+        tuned_info = None
+
+    def step(host):
+        P = make_problem()
         P.factor()
         n = P.n_dof
         if host:
@@ -212,7 +234,7 @@ def run_ours(args, W, rank, world):
     e2e_ms = (time.perf_counter() - t0) * 1000 / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms, world)
     return dict(ms=ms, e2e_ms=e2e_ms, stats=stats, stats_host=stats_h, phases=phases, info=info, prof=prof,
-                launches=launches, clocks=clk, xi_prob=xp, xi_prec=xq)
+                launches=launches, clocks=clk, xi_prob=xp, xi_prec=xq, autotune=tuned_info)
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of a kernel,
@@ -546,6 +568,9 @@ def main():
                     help="local LU trailing update: 0 CUDA cores, 1 TF32, 3 split 3 x TF32 tensor cores")
     ap.add_argument("--local-tensor", type=int, default=None, choices=[0, 1],
                     help="local solves on the tensor cores (1) or CUDA cores (0); default: library default")
+    ap.add_argument("--autotune", default=None, metavar="CACHE.json",
+                    help="pick the tuning knobs by the autotuner (cached in CACHE.json) before the timed steps; "
+                         "--lu-tensor / --local-tensor still override")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the solve benchmark")
     ap.add_argument("--requests", type=int, default=48)
@@ -655,6 +680,8 @@ def main():
                     for k, v in sorted(r["prof"].items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
         "clocks": r["clocks"],
     }
+    if r["autotune"] is not None:
+        line["autotune"] = r["autotune"]
     if world == 1 and not args.no_cpu_baseline and args.bc == "pec":
         line["cpu_baseline"] = cpu_baseline(W, iters)
         line["cpu_baseline_allcore"] = cpu_baseline_allcore(W, iters, line["cpu_baseline"])

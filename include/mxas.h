@@ -120,7 +120,8 @@ MX_API int mx_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*rele
  * effect at the next mx_factor. For comparison runs. */
 MX_API int mx_set_dense_local(mx_handle h, int dense);
 
-/* Tuning knobs (used by the autotuner); value 0 restores the default.
+/* Tuning knobs (the Python binding's autotune module searches them per problem shape);
+ * value 0 restores the default.
  *   MX_TUNE_LOCAL_RHS_GROUP: most right-hand sides one local-solve block handles
  *   (power of two, 1..16; default 16). Smaller groups run more blocks per subdomain. */
 #define MX_TUNE_LOCAL_RHS_GROUP 1

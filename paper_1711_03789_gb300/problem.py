@@ -36,6 +36,9 @@ class Problem:
     def set_weighted_gmres(self, weighted=True):
         L.mx_set_weighted_gmres(self.h, weighted)
 
+    def set_tuning(self, key, value):
+        L.mx_set_tuning(self.h, key, value)
+
     def set_coarse_solver(self, kind, core_cells=1, overlap_cells=1, tol=0.1, max_it=100, prec_kind=L.MX_PREC_RAS):
         L.mx_set_coarse_solver(self.h, kind, core_cells, overlap_cells, tol, max_it, prec_kind)
 
