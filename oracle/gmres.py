@@ -40,11 +40,14 @@ def givens(a, b):
 
 
 def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=None, weight=None,
-          flexible=False):
+          flexible=False, arnoldi=None):
     """Solve A x = b with right preconditioner B^{-1}.
 
     matvec(v) = A v, precond(v) = B^{-1} v for 1-D complex vectors; weight(v) = D v for
     weighted GMRES (None: the Euclidean inner product); flexible: keep Z_m (FGMRES).
+    arnoldi: a list that receives, per restart cycle, a dict of copies of the basis V_{k+1},
+    the preconditioned vectors Z_k and the Hessenberg matrix before the rotations (H-bar_k),
+    for checking the Arnoldi relation A Z_k = V_{k+1} H-bar_k.
     Returns (x, iterations, final relative true residual, converged)."""
     b = np.asarray(b, dtype=np.complex128)
     n = b.shape[0]
@@ -74,12 +77,13 @@ def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=
         g = np.zeros(m + 1, dtype=np.complex128)
         g[0] = beta
         V[0] = r / beta
-        Z = np.zeros((m, n), dtype=np.complex128) if flexible else None
+        Z = np.zeros((m, n), dtype=np.complex128) if (flexible or arnoldi is not None) else None
+        Hbar = np.zeros((m + 1, m), dtype=np.complex128) if arnoldi is not None else None
         j_done = 0
         converged = False
         for j in range(m):
             z = precond(V[j])
-            if flexible:
+            if Z is not None:
                 Z[j] = z
             w = matvec(z)
             for i in range(j + 1):  # modified Gram-Schmidt
@@ -88,6 +92,8 @@ def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=
             H[j + 1, j] = norm(w)
             if H[j + 1, j] != 0:
                 V[j + 1] = w / H[j + 1, j]
+            if Hbar is not None:
+                Hbar[:j + 2, j] = H[:j + 2, j]
             for i in range(j):  # previous rotations on the new column
                 hi, hi1 = H[i, j], H[i + 1, j]
                 H[i, j] = cs[i] * hi + sn[i] * hi1
@@ -105,6 +111,8 @@ def gmres(matvec, precond, b, tol=1e-6, restart=0, max_it=200, x0=None, history=
                 converged = abs(g[j + 1]) / bnorm <= tol
                 break
         k = j_done
+        if arnoldi is not None:
+            arnoldi.append({"V": V[:k + 1].copy(), "Z": Z[:k].copy(), "Hbar": Hbar[:k + 1, :k].copy()})
         y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])  # upper-triangular back substitution
         x = x + (Z[:k].T @ y if flexible else precond(V[:k].T @ y))
         r = b - matvec(x)

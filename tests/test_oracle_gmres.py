@@ -104,3 +104,99 @@ def test_weighted_gmres_on_the_maxwell_system():
     xd = np.linalg.solve(P.A.toarray(), f)
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
     assert np.all(np.diff(np.array(hist[0])) <= 1e-14)
+
+
+def _maxwell(n=6, k=4.0, xi=4.0, coarse_m=3):
+    P = Problem(n, k, xi, xi, 3, 1, coarse_m=coarse_m)
+    P.factor()
+    c, p = inputs.bump_batch(5, 1)
+    return P, P.load_vector(c, p, 0.1)[:, 0]
+
+
+def _orthogonality_loss(V, D=None):
+    """max |I - V_j^H D V_j| over the leading j vectors, for j = 1 .. len(V)."""
+    DV = V if D is None else np.stack([D @ v for v in V])
+    G = V.conj() @ DV.T
+    E = np.abs(G - np.eye(len(V)))
+    return np.array([E[:j, :j].max() for j in range(1, len(V) + 1)])
+
+
+def _check_mgs_loss(loss, hist):
+    """Modified Gram-Schmidt keeps the basis orthonormal to rounding while the residual is
+    large and loses orthogonality only as the residual falls, the loss staying of the order of
+    the unit roundoff divided by the relative residual (Paige, Rozloznik and Strakos, SIAM
+    J. Matrix Anal. Appl. 28 (2006), on MGS-GMRES). A wrong conjugation, index or sign in
+    the Gram-Schmidt loop breaks orthogonality at once, at residuals near 1."""
+    assert loss[0] <= 1e-15
+    for j in range(2, len(loss) + 1):
+        rho = hist[j - 2]  # relative residual after j - 1 steps
+        assert loss[j - 1] * rho <= 1e-14, (j, loss[j - 1], rho)
+        if rho >= 1e-3:
+            assert loss[j - 1] <= 1e-12, (j, loss[j - 1], rho)
+
+
+@pytest.mark.parametrize("restart", [0, 6])
+def test_arnoldi_relation_and_orthonormal_basis(restart):
+    """Arnoldi invariants of the right-preconditioned process (Sec. 5.2, Sec. 6.1): for every
+    cycle A Z_k = V_{k+1} H-bar_k with Z_k = B^{-1} V_k, V orthonormal up to the MGS loss,
+    and H-bar upper Hessenberg with a real positive subdiagonal."""
+    P, f = _maxwell()
+    rec, hist = [], []
+    x, its, rel, ok = gmres(lambda v: P.A @ v, lambda v: P.dd.apply(v, kind=P.kind), f, 1e-10, restart, 300,
+                            arnoldi=rec, history=hist)
+    assert ok and len(rec) >= (2 if restart else 1)
+    assert sum(c["Z"].shape[0] for c in rec) == its == len(hist)
+    start = 0
+    for c in rec:
+        V, Z, Hb = c["V"], c["Z"], c["Hbar"]
+        k = Z.shape[0]
+        assert V.shape[0] == k + 1 and Hb.shape == (k + 1, k)
+        AZ = np.stack([P.A @ z for z in Z], axis=1)
+        assert np.abs(AZ - V.T @ Hb).max() <= 1e-12 * np.abs(AZ).max()
+        # a restart cycle starts from the true residual: measure its loss against the
+        # residual reduction within the cycle
+        h = np.array(hist[start:start + k]) / (hist[start - 1] if start else 1.0)
+        _check_mgs_loss(_orthogonality_loss(V), h)
+        start += k
+        BV = np.stack([P.dd.apply(v, kind=P.kind) for v in V[:k]], axis=0)
+        assert np.abs(BV - Z).max() == 0.0
+        assert np.all(np.tril(Hb, -2) == 0)
+        sub = np.diag(Hb, -1)
+        assert np.all(sub.imag == 0) and np.all(sub.real > 0)
+    # the first basis vector of the first cycle is b / ||b|| (x0 = 0)
+    assert np.allclose(rec[0]["V"][0], f / np.linalg.norm(f), rtol=0, atol=1e-15)
+
+
+def test_weighted_arnoldi_basis_is_d_orthonormal():
+    """Weighted GMRES (Sec. 5.2): the basis is orthonormal in <u, v>_D = v^H D u with
+    D = K + k^2 M, and the Arnoldi relation is unchanged."""
+    P, f = _maxwell()
+    D = (P.K + P.k ** 2 * P.M).tocsr()
+    rec, hist = [], []
+    x, its, rel, ok = gmres(lambda v: P.A @ v, lambda v: P.dd.apply(v, kind=P.kind), f, 1e-8, 0, 300,
+                            weight=lambda v: D @ v, arnoldi=rec, history=hist)
+    V, Z, Hb = rec[0]["V"], rec[0]["Z"], rec[0]["Hbar"]
+    _check_mgs_loss(_orthogonality_loss(V, D), hist)
+    # the Euclidean Gram matrix is far from the identity: the weight matters
+    assert _orthogonality_loss(V[:3])[-1] > 1e-2
+    AZ = np.stack([P.A @ z for z in Z], axis=1)
+    assert np.abs(AZ - V.T @ Hb).max() <= 1e-12 * np.abs(AZ).max()
+
+
+def test_flexible_arnoldi_relation_with_a_changing_preconditioner():
+    """FGMRES: with B_j^{-1} changing at every call, A Z_k = V_{k+1} H-bar_k still holds for
+    the stored z_j, while Z_k is no longer B^{-1} V_k for any one B."""
+    P, f = _maxwell()
+    calls = [0]
+
+    def varying(v):
+        calls[0] += 1
+        return P.dd.apply(v, kind=P.kind) * (1.0 + 0.3 * np.sin(calls[0]))
+
+    rec = []
+    x, its, rel, ok = gmres(lambda v: P.A @ v, varying, f, 1e-10, 0, 300, flexible=True, arnoldi=rec)
+    assert ok
+    V, Z, Hb = rec[0]["V"], rec[0]["Z"], rec[0]["Hbar"]
+    AZ = np.stack([P.A @ z for z in Z], axis=1)
+    assert np.abs(AZ - V.T @ Hb).max() <= 1e-12 * np.abs(AZ).max()
+    assert np.linalg.norm(f - P.A @ x) <= 1.0001e-10 * np.linalg.norm(f)
