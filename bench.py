@@ -75,6 +75,7 @@ def peaks():
 # 152 SMs x 2 FP64 FMA / clock x 2 flops x 2.07 GHz; 152 x 128 FP32 FMA x 2 x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth, for context beside the measured copy rate
 
 
 class ClockSampler:
@@ -282,13 +283,30 @@ def roofline(prof, peak, form="mixed"):
         base["traffic_source"] = ratio[1]
     if f_hbm >= f_alu:
         base.update({"bound": "hbm", "achieved": gbs, "peak": peak["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
-                     "peak_source": f"{peak['source']} copy bandwidth"})
+                     "peak_source": f"{peak['source']} copy bandwidth", "frac_of_nominal": gbs / HBM_NOMINAL_GBS})
     else:
         base.update({"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": f_alu,
                      "peak_source": "FP64 unit count x max clock" if alu_peak == FP64_PEAK_TFLOPS
                      else ("measured bf16 GEMM x TF32/BF16 nominal ratio" if alu_peak == tf32_peak
                            else "FP32 unit count x max clock"), "hbm_frac": f_hbm})
     return base
+
+
+def kernel_table(prof, peak, steps):
+    """Per-kernel device time per step, launches, algorithmic bytes and flops per launch, and
+    the achieved HBM rate against the measured copy bandwidth and the nominal HBM3e figure."""
+    out = {}
+    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        if not v["launches"]:
+            continue
+        sec = v["ms"] / 1e3
+        gbs = v["bytes"] / sec / 1e9 if sec > 0 else None
+        out[k] = {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] // steps,
+                  "bytes_per_launch": v["bytes"] / v["launches"], "flops_per_launch": v["flops"] / v["launches"],
+                  "gbs": gbs, "tflops": v["flops"] / sec / 1e12 if sec > 0 else None,
+                  "hbm_frac": gbs / peak["hbm_gbs"] if gbs is not None else None,
+                  "hbm_frac_of_nominal": gbs / HBM_NOMINAL_GBS if gbs is not None else None}
+    return out
 
 
 def cpu_baseline(W, iterations, budget_s=20.0):
@@ -675,9 +693,7 @@ def main():
         "gpu_launches": r["launches"],
         "gpu_launches_per_step": r["launches"] // args.steps,
         "roofline": roof,
-        "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps,
-                        "bytes_per_launch": v["bytes"] / v["launches"], "flops_per_launch": v["flops"] / v["launches"]}
-                    for k, v in sorted(r["prof"].items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
+        "kernels": kernel_table(r["prof"], pk, args.steps),
         "clocks": r["clocks"],
     }
     if r["autotune"] is not None:

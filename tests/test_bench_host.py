@@ -25,6 +25,7 @@ def test_dominant_kernel_hbm_roof_and_traffic():
     ratio = bench.DRAM_PER_ALG[("local_solve", "mixed")][0]
     assert r["traffic"] == pytest.approx(ratio * 16.0e9)
     assert r["share_of_device_time"] == pytest.approx(100.0 / 130.0)
+    assert r["frac_of_nominal"] == pytest.approx(1600.0 / bench.HBM_NOMINAL_GBS)
 
 
 def test_alu_roof_and_no_traffic_without_a_capture():
@@ -40,3 +41,19 @@ def test_alu_roof_and_no_traffic_without_a_capture():
 def test_rank_seeds_are_distinct():
     assert len({bench.rhs_seed(r) for r in range(8)}) == 8
     assert bench.max_over_ranks(3.5, 1) == 3.5
+
+
+def test_kernel_table_rates_per_step():
+    prof = {
+        "spmv": _prof(20.0, 10, 10 * 2.0e9, 10 * 1.0e8),   # 2e10 B in 20 ms: 1,000 GB/s
+        "local_solve": _prof(60.0, 10, 10 * 30.0e9, 0.0),  # 3e11 B in 60 ms: 5,000 GB/s
+        "idle": _prof(0.0, 0, 0.0, 0.0),
+    }
+    t = bench.kernel_table(prof, PEAK, steps=5)
+    assert list(t) == ["local_solve", "spmv"]  # by device time, launched kernels only
+    s = t["spmv"]
+    assert s["ms_per_step"] == pytest.approx(4.0) and s["launches_per_step"] == 2
+    assert s["bytes_per_launch"] == pytest.approx(2.0e9) and s["flops_per_launch"] == pytest.approx(1.0e8)
+    assert s["gbs"] == pytest.approx(1000.0) and s["tflops"] == pytest.approx(1.0e9 / 0.02 / 1e12)
+    assert s["hbm_frac"] == pytest.approx(1000.0 / 6797.2)
+    assert t["local_solve"]["hbm_frac_of_nominal"] == pytest.approx(5000.0 / bench.HBM_NOMINAL_GBS)
