@@ -470,8 +470,10 @@ def run_serving(args):
     the one-level additive preconditioner does not reach 1e-6 within 200 iterations for
     these xi (the oracle at 20^3, k = 10, xi_prob = xi_prec = k: 1.2e-4 after 200), while
     ADEF1-ImpRAS takes 30 iterations there with xi_prob = 0 (oracle, 4^3 coarse cells). A closed-loop run
-    (everything submitted at once) measures capacity; a Poisson run at 0.8 x that capacity
-    measures latency under load. Reports p50 / p99 latency and solves per second."""
+    (everything submitted at once) measures capacity; Poisson runs at the offered loads of
+    --loads (fractions of that capacity; default 0.8) measure latency under load. --budget-gb
+    caps the server's factor cache below the mix's working set to exercise admission and
+    eviction. Reports p50 / p99 latency and solves per second."""
     import torch
     import inputs
     import paper_1711_03789_gb300 as mx
@@ -489,8 +491,13 @@ def run_serving(args):
         c, p = inputs.bump_batch(10_000 + i, nrhs)
         return dict(n=int(2 * k), k=k, xp=xp, nrhs=nrhs, c=c, p=p)
 
+    budget = int(args.budget_gb * 2 ** 30) if args.budget_gb else int(0.8 * free)
+    loads = [float(v) for v in args.loads.split(",") if v.strip()]
+    if not loads or any(v <= 0 for v in loads):
+        raise SystemExit("--loads: comma-separated positive fractions of the closed-loop capacity")
+
     def run(reqs, rate):
-        s = mx.mx_server_create(int(0.8 * free), workers=args.workers)
+        s = mx.mx_server_create(budget, workers=args.workers)
         try:
             return serve(s, reqs, rate)
         finally:
@@ -524,15 +531,21 @@ def run_serving(args):
 
     reqs = [draw(i) for i in range(nreq)]
     closed = run(reqs, 0.0)
-    torch.cuda.empty_cache()  # the first server's blocks back to the device before the second starts
-    poisson = run(reqs, 0.8 * closed["requests_per_s"])
-    line = {"metric": METRIC, "value": poisson["p99_ms"] / 1e3, "unit": "s (p99 latency)", "n_gpus": 1,
+    runs = {}
+    for load in loads:
+        torch.cuda.empty_cache()  # the previous server's blocks back to the device before the next starts
+        runs[load] = run(reqs, load * closed["requests_per_s"])
+    head = runs[0.8] if 0.8 in runs else runs[loads[0]]
+    line = {"metric": METRIC, "value": head["p99_ms"] / 1e3, "unit": "s (p99 latency)", "n_gpus": 1,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c64 factors / f64 Krylov",
             "data": "synthetic (seeded request mix and Gaussian-bump right-hand sides)",
             "config": {"workload": "serving_mix", "requests": nreq, "workers": args.workers,
                        "max_it": args.serve_max_it, "restart": 100, "tol": 1e-6, "boundary": "impedance",
-                       "preconditioner": "ADEF1-ImpRAS", "coarse_cells": "n / 5"},
-            "closed_loop": closed, "poisson_0.8x": poisson}
+                       "preconditioner": "ADEF1-ImpRAS", "coarse_cells": "n / 5", "budget_bytes": budget,
+                       "loads": loads},
+            "closed_loop": closed}
+    for load, res in runs.items():
+        line[f"poisson_{load:g}x"] = res
     print(json.dumps(line))
 
 
@@ -594,6 +607,10 @@ def main():
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--workers", type=int, default=3)
     ap.add_argument("--serve-max-it", type=int, default=200)
+    ap.add_argument("--loads", default="0.8",
+                    help="serving: offered loads of the Poisson runs as fractions of the closed-loop capacity")
+    ap.add_argument("--budget-gb", type=float, default=None,
+                    help="serving: factor-cache budget in GiB (default 0.8 x free device memory)")
     args = ap.parse_args()
     if args.serving:
         run_serving(args)
