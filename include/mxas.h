@@ -77,7 +77,7 @@ typedef enum { MX_PLAIN_FP64 = 0, MX_MIXED = 1 } mx_precision;
 typedef struct mx_problem* mx_handle;
 
 typedef struct {
-  int64_t n_dof;        /* PEC-interior edges of the fine mesh */
+  int64_t n_dof;        /* DOFs of the fine mesh: PEC-interior edges, or all edges (impedance) */
   int64_t nnz;          /* nonzeros of A (CSR) */
   int32_t n_sub;        /* number of subdomains N */
   int32_t max_local;    /* largest subdomain size n_l */
@@ -218,7 +218,9 @@ MX_API int mx_set_stream(mx_handle h, void* stream);
 /* Factor the preconditioner (Eq. 3.3-3.4): extract every local minor
  * A^l = R^l A_{xi_prec} (R^l)^T and LU-factor all of them in one batch without
  * pivoting (coercivity, Lemma 2.2, keeps every pivot nonzero), c64 in MX_MIXED and c128
- * in MX_PLAIN_FP64; LU-factor the coarse matrix A^0 in FP64 (band-limited).
+ * in MX_PLAIN_FP64; LU-factor the coarse matrix A^0 (band-limited; FP64 in MX_PLAIN_FP64,
+ * c64 in MX_MIXED, which also forms the explicit inverse unless MX_TUNE_COARSE_INVERSE
+ * is 0), or, with MX_COARSE_GMRES, factor the inner problem's subdomains instead.
  * Returns MX_ESINGULAR when a pivot modulus falls below 1e-30 times the matrix scale. */
 MX_API int mx_factor(mx_handle h);
 
@@ -240,7 +242,7 @@ MX_API int mx_load_vector(mx_handle h, int nrhs, int nbumps, const double* centr
 MX_API int mx_solve(mx_handle h, const void* rhs, int nrhs, double tol, int restart, int max_it,
              void* x, mx_rhs_stats* stats);
 
-/* Number of unknowns (PEC-interior edges). */
+/* Number of unknowns (PEC-interior edges, or all edges with the impedance condition). */
 MX_API int64_t mx_num_dofs(mx_handle h);
 
 /* Sizes of the assembled problem. */
@@ -319,7 +321,8 @@ MX_API int mx_dots_noalloc(const void* V, const void* w, int64_t n, int nrhs, in
  * together with every pending request of the same operator and solver settings (continuous
  * batching, at most 32 right-hand sides per batch); batches of different operators run
  * concurrently. Factorisations stay resident in HBM, cached by the preconditioner key
- * (n_cells, k, xi_prec, subdomains, coarse mesh, precision; xi_prob does not enter it, since
+ * (n_cells, k, xi_prec, subdomains, coarse mesh, precision, boundary condition,
+ * preconditioner variant; xi_prob does not enter it, since
  * B^{-1} is built from A_{xi_prec} only, Sec. 6.2). A new factorisation is admitted when its
  * planned factor bytes plus the batch's Krylov workspace fit the budget after evicting idle
  * cached factorisations (least recently used first) and fit the device's free memory;
