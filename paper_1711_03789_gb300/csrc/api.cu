@@ -513,12 +513,16 @@ int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels) {
     DevView in(v, bytes, true, P.stream);
     DevView out(z, bytes, false, P.stream);
     DevBuf<double2> a((size_t)n * nrhs), b((size_t)n * nrhs);
+    MX_CUDA(cudaMemsetAsync(P.status.p + 2, 0, sizeof(int32_t), P.stream));  // timed-out waits, as in mx_solve
     MX_LAUNCH(k_to_internal<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, (const double2*)in.p, a.p));
     precond_apply(P, a.p, b.p, 0, nrhs, levels);
     MX_LAUNCH(k_to_user<<<grid_for(n * nrhs, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, b.p, (double2*)out.p));
     MX_CHECK_LAUNCH();
     out.copy_out(bytes, P.stream);
+    int32_t timeouts = 0;
+    MX_CUDA(cudaMemcpyAsync(&timeouts, P.status.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, P.stream));
     MX_CUDA(cudaStreamSynchronize(P.stream));
+    MX_REQUIRE(timeouts == 0, MX_ETIMEOUT, std::to_string(timeouts) + " tensor-core waits ran out in the local solves");
   });
 }
 

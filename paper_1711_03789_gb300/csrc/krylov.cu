@@ -811,6 +811,9 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
   MX_REQUIRE(nrhs >= 1 && nrhs <= 32, MX_EINVAL, "nrhs must be in 1..32 per batch");
   MX_REQUIRE(max_it >= 1, MX_EINVAL, "max_it must be >= 1");
   cudaStream_t s = P.stream;
+  // status[2] counts bounded tensor-core waits that ran out; the local solves of this
+  // solve report into it, read back with the solution below
+  MX_CUDA(cudaMemsetAsync(P.status.p + 2, 0, sizeof(int32_t), s));
   const int m = restart > 0 ? std::min(restart, max_it) : max_it;
   Workspace& W = workspace(P, nrhs, m);
   const int64_t n = P.fine.n_dof, nv = n * nrhs;
@@ -1020,7 +1023,10 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
     ++launches;
   }
   MX_CUDA(cudaMemcpyAsync(x, W.x.p, nv * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  int32_t timeouts = 0;
+  MX_CUDA(cudaMemcpyAsync(&timeouts, P.status.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   MX_CUDA(cudaStreamSynchronize(s));
+  MX_REQUIRE(timeouts == 0, MX_ETIMEOUT, std::to_string(timeouts) + " tensor-core waits ran out in the local solves");
   int rc = MX_OK;
   int maxits = 0;
   for (int r = 0; r < nrhs; ++r) {
