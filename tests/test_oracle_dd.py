@@ -186,6 +186,39 @@ def test_partition_of_unity_sums_to_identity():
         assert np.array_equal(total, np.ones(m.n_dof))
 
 
+@pytest.mark.parametrize("n,core", [(6, 3), (7, 3), (10, 5), (11, 4)])
+def test_each_dof_is_owned_by_the_core_box_holding_its_midpoint(n, core):
+    """The reading behind D^l (Sec. 6.3): the owner of a DOF is the subdomain whose core box
+    [core i, core (i + 1)) per axis (the last box closed at n) contains the edge midpoint.
+    Checked as an inequality on the midpoint's coordinates, with a ragged last box for n = 7, 11."""
+    m = KuhnMesh(n)
+    K, M = fem.assemble_KM(m)
+    S = dd.Schwarz(m, fem.a_xi(K, M, 1.0, 1.0), core, 1)
+    N = -(-n // core)
+    own = S.owner()
+    mid = 0.5 * (m.coords(m.dof_edges[:, 0]) + m.coords(m.dof_edges[:, 1]))  # unit-cube coordinates
+    box = np.stack([own % N, (own // N) % N, own // (N * N)], axis=1)
+    lo = box * core / n
+    hi = np.minimum((box + 1) * core, n) / n
+    last = box == N - 1
+    eps = 1e-12
+    assert np.all(mid >= lo - eps)
+    assert np.all((mid < hi - eps) | (last & (mid <= hi + eps)))
+
+
+def test_preconditioner_is_built_from_xi_prec():
+    """Sec. 6.2: B^{-1} comes from A_{xi_prec}, the operator is A_{xi_prob}. With one subdomain
+    covering the cube B^{-1} = A_{xi_prec}^{-1} exactly, also when xi_prob differs."""
+    from oracle.problem import Problem
+    for bc in ("pec", "imp"):
+        P = Problem(4, 3.0, 0.5, 6.0, 4, 0, bc=bc)
+        P.factor()
+        A_prec = fem.a_xi(P.K, P.M, 3.0, 6.0, P.B)
+        x = np.arange(P.n_dof) * (1 - 0.25j) + 1.0
+        assert np.abs(P.dd.apply(A_prec @ x) - x).max() < 1e-10 * np.abs(x).max(), bc
+        assert np.abs(P.dd.apply(P.A @ x) - x).max() > 1e-3 * np.abs(x).max(), bc
+
+
 def test_ras_single_subdomain_is_the_inverse():
     """One subdomain covering the cube: D = I and RAS = AS = A^{-1}."""
     m = KuhnMesh(4)

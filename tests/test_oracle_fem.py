@@ -296,3 +296,19 @@ def test_discrete_solution_is_close_to_the_edge_interpolant(field):
     # from n = 4 to 8, 1.83 from 8 to 12): above first order at once, near 2 on the finer pair
     rm = _rates(mid, ns)
     assert all(1.55 < r < 2.3 for r in rm) and rm[-1] > 1.75, (field, l2, mid)
+
+
+def test_load_vector_of_a_gaussian_bump_against_its_integral():
+    """Bump field F(x) = p exp(-|x - c|^2 / w^2) (the right-hand sides' definition): for a
+    constant direction e, the edge interpolant of e has the DOFs g_i = e . (x_high - x_low) and
+    reproduces e exactly, so sum_i f_i g_i = int F . e dx = (p . e) (pi w^2)^(3/2), up to the
+    Gaussian's tail outside the cube (exp(-22) here) and the quadrature error."""
+    m = KuhnMesh(10)
+    c = np.array([[[0.5, 0.47, 0.52]]])
+    p = np.array([[[1.0, 2.0j, -0.5]]])
+    w = 0.1
+    f = fem.load_vector(m, fem.bump_field(c, p, w))[:, 0]
+    t = m.coords(m.dof_edges[:, 1]) - m.coords(m.dof_edges[:, 0])
+    for e in np.eye(3):
+        exact = (p[0, 0] @ e) * (math.pi * w * w) ** 1.5
+        assert abs(f @ (t @ e) - exact) <= 5e-6 * abs(exact), e

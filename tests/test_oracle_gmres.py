@@ -10,12 +10,15 @@ import inputs
 
 def test_givens():
     rng = np.random.default_rng(0)
-    for _ in range(20):
-        a, b = complex(*rng.standard_normal(2)), abs(rng.standard_normal())
+    for trial in range(40):
+        a = complex(*rng.standard_normal(2))
+        # real b (as GMRES produces: the subdiagonal is a norm) and general complex b
+        b = abs(rng.standard_normal()) if trial < 20 else complex(*rng.standard_normal(2))
         c, s = givens(a, b)
         G = np.array([[c, s], [-np.conj(s), c]])
         r = G @ np.array([a, b])
         assert abs(r[1]) < 1e-14 and np.allclose(G @ G.conj().T, np.eye(2))
+        assert abs(abs(r[0]) - np.hypot(abs(a), abs(b))) < 1e-14
 
 
 def test_unpreconditioned_dense():

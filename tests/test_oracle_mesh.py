@@ -84,3 +84,23 @@ def test_tet_paths_monotone():
     ijk0 = vertex_ijk(m.tets[:, 0], 3)
     ijk3 = vertex_ijk(m.tets[:, 3], 3)
     assert np.all(ijk3 - ijk0 == 1)
+
+
+def test_numbering_conventions_by_hand():
+    """The documented numbering, checked on hand-computed cases. DOFs are sorted by the key
+    7 v_low + d, with d indexing the directions (1,0,0), (0,1,0), (0,0,1), (1,1,0), (1,0,1),
+    (0,1,1), (1,1,1). On the single cube with all edges (n = 1, impedance), vertex 0 = (0,0,0)
+    starts one edge in every direction, to the vertices 1, 2, 4, 3, 5, 6, 7 (vertex id
+    i + 2 (j + 2 l)). Columns of tet2dof follow the local edges 01, 02, 03, 12, 13, 23."""
+    m = KuhnMesh(1, "imp")
+    assert m.n_dof == 19
+    first = [tuple(e) for e in m.dof_edges[:7].tolist()]
+    assert first == [(0, 1), (0, 2), (0, 4), (0, 3), (0, 5), (0, 6), (0, 7)]
+    assert m.dof_key[:7].tolist() == list(range(7))
+    # the tetrahedron of permutation (0, 1, 2): path 0 -> 1 -> 3 -> 7
+    assert m.tets[0].tolist() == [0, 1, 3, 7]
+    d = {tuple(e): i for i, e in enumerate(m.dof_edges.tolist())}
+    assert m.tet2dof[0].tolist() == [d[(0, 1)], d[(0, 3)], d[(0, 7)], d[(1, 3)], d[(1, 7)], d[(3, 7)]]
+    for t in (m, KuhnMesh(3)):
+        for k, (p, q) in enumerate([(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]):
+            assert np.array_equal(t.tet2dof[:, k], t.dof_of_pairs(t.tets[:, p], t.tets[:, q]))
