@@ -65,6 +65,10 @@ MUTANTS = [
  ("problem", "flexible off", "        self.flexible = inner_coarse is not None", "        self.flexible = False"),
  ("mesh", "dir table swap", "DIRS = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [1, 0, 1], [0, 1, 1], [1, 1, 1]],", "DIRS = np.array([[0, 1, 0], [1, 0, 0], [0, 0, 1], [1, 1, 0], [1, 0, 1], [0, 1, 1], [1, 1, 1]],"),
  ("mesh", "tet2dof local edge", "LOCAL_EDGES = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]", "LOCAL_EDGES = [(0, 1), (0, 2), (0, 3), (1, 2), (2, 3), (1, 3)]"),
+ ("problem", "weight k instead of k^2", "        Dk = (self.K + self.k ** 2 * self.M).tocsr() if weighted else None", "        Dk = (self.K + self.k * self.M).tocsr() if weighted else None"),
+ ("dd", "inner overlap", "        self.inner = Schwarz(self.coarse_mesh, self.A0, core, overlap, k=self.k, xi_prec=self.xi_prec)", "        self.inner = Schwarz(self.coarse_mesh, self.A0, core, overlap + 1, k=self.k, xi_prec=self.xi_prec)"),
+ ("dd", "coarse without impedance", "            self.A0 = fem.a_xi(Kc, Mc, k, xi_prec, fem.assemble_B(cm) if self.imp else None)", "            self.A0 = fem.a_xi(Kc, Mc, k, xi_prec, None)"),
+ ("dd", "box faces of the cube only", "        faces = boundary_faces(tets, mesh.n, tuple(lo), tuple(hi))", "        faces = boundary_faces(tets, mesh.n)"),
 ]
 
 PINS = ["tests/test_oracle_mesh.py", "tests/test_oracle_fem.py", "tests/test_oracle_dd.py", "tests/test_oracle_gmres.py",

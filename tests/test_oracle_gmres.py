@@ -109,6 +109,30 @@ def test_weighted_gmres_on_the_maxwell_system():
     assert np.all(np.diff(np.array(hist[0])) <= 1e-14)
 
 
+def test_weighted_solve_reports_the_curl_k_norm_residual():
+    """Sec. 5.2 with the weight of Eq. 2.3 / 5.1: the weighted solve's reported residual is
+    ||b - A x||_D / ||b||_D with D = K + k^2 M, the matrix of the (.,.)_{curl,k} inner
+    product. Checked on the impedance space, where the interpolant g of a constant field c
+    has g^T K g = 0 and g^T M g = |c|^2 (volume 1), so ||g||_D^2 = k^2 |c|^2."""
+    k = 3.0
+    P = Problem(4, k, 3.0, 3.0, 2, 1, bc="imp")
+    D = (P.K + k * k * P.M).tocsr()
+    t = P.mesh.coords(P.mesh.dof_edges[:, 1]) - P.mesh.coords(P.mesh.dof_edges[:, 0])
+    c = np.array([0.3, -1.2, 0.7])
+    g = t @ c
+    assert abs(g @ (D @ g) - k * k * (c @ c)) <= 1e-12 * k * k * (c @ c)
+    P.factor()
+    b = inputs.random_complex(8, P.n_dof)
+    x, st = P.solve(b, tol=1e-6, weighted=True)
+    its, rel, ok = st[0]
+    r = b - P.A @ x
+    rel_d = np.sqrt(np.vdot(r, D @ r).real / np.vdot(b, D @ b).real)
+    rel_e = np.linalg.norm(r) / np.linalg.norm(b)
+    assert ok and rel_d <= 1e-6
+    assert abs(rel - rel_d) <= 1e-9 * rel_d
+    assert abs(rel_e - rel_d) > 1e-2 * rel_d  # the weight matters for this residual
+
+
 def _maxwell(n=6, k=4.0, xi=4.0, coarse_m=3):
     P = Problem(n, k, xi, xi, 3, 1, coarse_m=coarse_m)
     P.factor()

@@ -106,6 +106,22 @@ def test_single_inner_subdomain_is_exact():
     assert np.linalg.norm(y - y_direct) <= 1e-10 * np.linalg.norm(y_direct)
 
 
+@pytest.mark.parametrize("core,overlap", [(2, 1), (3, 0), (2, 2)])
+def test_inner_schwarz_is_built_on_the_requested_coarse_boxes(core, overlap):
+    """Sec. 6.4: the inner preconditioner is one-level Schwarz on boxes of the coarse mesh of
+    `core` coarse cells widened by `overlap` (the fine-mesh rules applied to the coarse mesh),
+    built from A^0 itself."""
+    A, S, b = _system(n=12, k=6.0, xi_prec=36.0, core=4, coarse_m=6)
+    S.set_inner_coarse(core=core, overlap=overlap, tol=0.1, max_it=20, kind="ras")
+    want = dd.subdomain_boxes(6, core, overlap)
+    assert len(S.inner.boxes) == len(want)
+    for (lo, hi), (wl, wh) in zip(S.inner.boxes, want):
+        assert np.array_equal(lo, wl) and np.array_equal(hi, wh)
+    assert abs(S.inner.A_prec - S.A0).max() == 0
+    sizes = [len(i) for i in S.inner.idx]
+    assert sizes == [len(dd.local_dofs(S.coarse_mesh, lo, hi)) for lo, hi in want]
+
+
 @pytest.mark.parametrize("kind", ["as", "adef1"])
 def test_outer_fgmres_converges_with_rough_coarse_solves(kind):
     inner = dict(core=2, overlap=1, tol=0.1, max_it=50, kind="ras")
