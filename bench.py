@@ -313,9 +313,10 @@ def cpu_baseline(W, iterations, budget_s=20.0):
     """The oracle on a bounded sample of the workload, scaled to one step.
 
     Times (single-threaded SciPy): the oracle's mesh + assembly + subdomain lists on a
-    30^3-cell mesh (scaled by unknowns); the factorisation and one multi-RHS solve of the
-    largest 5^3+overlap subdomain minors, as many as fit in about half the budget (scaled to
-    all subdomains); SpMV (median of 3) and one CGS Arnoldi step at the mean Krylov index,
+    30^3-cell mesh (scaled by unknowns); the factorisation and one multi-RHS solve of
+    subdomain minors of every box shape of that mesh, round-robin for about half the budget,
+    each shape's mean weighted by its count in the full geometry (the 30^3 sample has every
+    box shape of the 60^3 one); SpMV (median of 3) and one CGS Arnoldi step at the mean Krylov index,
     per right-hand side (scaled by unknowns). Step time = build + factor + iterations x
     per-iteration cost. The whole sample takes about `budget_s` seconds of CPU time."""
     from oracle.mesh import KuhnMesh, count_interior_edges
@@ -337,25 +338,44 @@ def cpu_baseline(W, iterations, budget_s=20.0):
     scale_dof = count_interior_edges(n) / m.n_dof
     A_prec = fem.a_xi(K, M, k, xq)
     A = fem.a_xi(K, M, k, xp)
-    # subdomain sample: the largest boxes, until about half the budget is spent
-    order = np.argsort([-len(i) for i in idx])
-    t_fac_sum = t_sol_sum = 0.0
+    # subdomain sample: every box shape (cells per axis) of the sample geometry, largest first,
+    # round-robin until about half the budget is spent; each shape's mean factor and solve times
+    # are weighted by that shape's count in the full geometry
+    shape_of = lambda lo, hi: tuple((hi - lo).tolist())
+    by_shape = {}
+    for l, (lo, hi) in enumerate(boxes):
+        by_shape.setdefault(shape_of(lo, hi), []).append(l)
+    shapes = sorted(by_shape, key=lambda sh: -len(idx[by_shape[sh][0]]))
+    t_f = {sh: [] for sh in shapes}
+    t_s = {sh: [] for sh in shapes}
     done = 0
-    for l in order:
-        sub = A_prec[idx[l]][:, idx[l]].tocsc()
-        t0 = time.perf_counter()
-        lu = spla.splu(sub)
-        t1 = time.perf_counter()
-        lu.solve(np.ones((sub.shape[0], nrhs), dtype=np.complex128))
-        t2 = time.perf_counter()
-        t_fac_sum += t1 - t0
-        t_sol_sum += t2 - t1
-        done += 1
-        if done >= 4 and time.perf_counter() - t_start > 0.5 * budget_s:
+    while True:
+        for sh in shapes:
+            l = by_shape[sh][len(t_f[sh]) % len(by_shape[sh])]
+            sub = A_prec[idx[l]][:, idx[l]].tocsc()
+            t0 = time.perf_counter()
+            lu = spla.splu(sub)
+            t1 = time.perf_counter()
+            lu.solve(np.ones((sub.shape[0], nrhs), dtype=np.complex128))
+            t2 = time.perf_counter()
+            t_f[sh].append(t1 - t0)
+            t_s[sh].append(t2 - t1)
+            done += 1
+        if time.perf_counter() - t_start > 0.5 * budget_s:
             break
-    t_fac, t_sol = t_fac_sum / done, t_sol_sum / done
-    N = -(-n // W["core"])
-    n_sub = N ** 3
+    full = {}
+    for lo, hi in dd.subdomain_boxes(n, W["core"], W["overlap"]):
+        full[shape_of(lo, hi)] = full.get(shape_of(lo, hi), 0) + 1
+    n_sub = sum(full.values())
+
+    def nearest(sh):  # a full-geometry shape the sample lacks: the sample shape nearest in cells
+        return sh if sh in t_f else min(shapes, key=lambda q: abs(np.prod(q) - np.prod(sh)))
+
+    fac_total = sum(c * float(np.mean(t_f[nearest(sh)])) for sh, c in full.items())
+    sol_total = sum(c * float(np.mean(t_s[nearest(sh)])) for sh, c in full.items())
+    t_fac, t_sol = fac_total / n_sub, sol_total / n_sub  # per subdomain, weighted over the shapes
+    big = shapes[0]
+    t_fac_big, t_sol_big = float(np.mean(t_f[big])), float(np.mean(t_s[big]))
     v = np.ones((m.n_dof, nrhs), dtype=np.complex128)
     ts = []
     for _ in range(3):
@@ -375,8 +395,10 @@ def cpu_baseline(W, iterations, budget_s=20.0):
     per_it = n_sub * t_sol + t_spmv + t_arn
     step = t_build_s * scale_dof + n_sub * t_fac + iterations * per_it
     return {"value": step, "unit": "s", "cores": 1, "kind": "oracle", "t_fac": t_fac, "t_sol": t_sol,
-            "sample": (f"oracle build on {ns}^3 cells scaled by unknowns; splu factor+solve of the {done} largest of "
-                       f"{n_sub} subdomain minors scaled to all, {nrhs} rhs; SpMV and one CGS Arnoldi step at "
+            "t_fac_largest": t_fac_big, "t_sol_largest": t_sol_big,
+            "sample": (f"oracle build on {ns}^3 cells scaled by unknowns; splu factor+solve of {done} subdomain minors "
+                       f"covering its {len(shapes)} box shapes, weighted by their counts among the {n_sub} "
+                       f"subdomains, {nrhs} rhs; SpMV and one CGS Arnoldi step at "
                        f"j={jm} scaled by unknowns; x {iterations} iterations; "
                        f"{time.perf_counter() - t_start:.1f} s of CPU work"),
             "per_iteration_s": per_it}
@@ -410,10 +432,39 @@ def _oracle_sub_job(job):
     return time.perf_counter() - t0
 
 
+def _pool_job_times(ctx, procs, init_args, jobs, budget_s):
+    """Times of the subdomain jobs (factor + solve) on a spawn-started pool of `procs` worker
+    processes with one BLAS thread each; rounds of `procs` jobs until `budget_s` has passed."""
+    ready = ctx.Barrier(procs)
+    threads = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({v: "1" for v in threads})  # one thread per worker process
+    try:
+        pool = ctx.Pool(procs, initializer=_oracle_sub_init, initargs=(*init_args, ready))
+    finally:
+        for v, old in threads.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    with pool:
+        times = list(pool.imap_unordered(_oracle_sub_job, jobs[:procs], chunksize=1))  # waits for the set-up
+        t0 = time.perf_counter()
+        for chunk in range(procs, len(jobs), procs):
+            if time.perf_counter() - t0 > budget_s:
+                break
+            times += list(pool.imap_unordered(_oracle_sub_job, jobs[chunk:chunk + procs], chunksize=1))
+    return times
+
+
 def cpu_baseline_allcore(W, iterations, single, budget_s=12.0):
     """The oracle's subdomain factor + solve (the part of a step that runs per subdomain) on a
     process pool of all host cores (spawn), on the same 30^3 sample geometry as cpu_baseline;
-    the rest of the step (build, SpMV, Arnoldi) keeps its single-thread time."""
+    the rest of the step (build, SpMV, Arnoldi) keeps its single-thread time.
+
+    The speed-up of the subdomain work is measured pool against pool: the same jobs (the
+    largest subdomains, cycled) timed on a one-process pool and on the all-core pool, in
+    worker processes set up alike, so no difference between the bench process and a fresh
+    worker enters the ratio. The single-thread sample's subdomain total is divided by it."""
     import multiprocessing as mpr
     cores = os.cpu_count() or 1
     n, k = W["n"], W["k"]
@@ -422,46 +473,26 @@ def cpu_baseline_allcore(W, iterations, single, budget_s=12.0):
     N = -(-ns // W["core"])
     from oracle.mesh import count_interior_edges
     from oracle import dd
-    # the largest subdomains only, cycled: the size class the single-thread sample times, so
-    # that the two per-subdomain times compare like for like
     sizes = [count_interior_edges(*(hi - lo).tolist()) for lo, hi in dd.subdomain_boxes(ns, W["core"], W["overlap"])]
     big = [l for l in range(N ** 3) if sizes[l] == max(sizes)]
     jobs = [(big[j % len(big)], W["nrhs"]) for j in range(max(len(big), 8 * cores))]
     ctx = mpr.get_context("spawn")
+    init_args = (ns, k, xq, W["core"], W["overlap"])
     t_start = time.perf_counter()
-    ready = ctx.Barrier(cores)
-    threads = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    os.environ.update({v: "1" for v in threads})  # one thread per worker process
-    try:
-        pool = ctx.Pool(cores, initializer=_oracle_sub_init, initargs=(ns, k, xq, W["core"], W["overlap"], ready))
-    finally:
-        for v, old in threads.items():
-            if old is None:
-                os.environ.pop(v, None)
-            else:
-                os.environ[v] = old
-    with pool:
-        # every worker times its own jobs; with all cores busy the pool completes `cores` jobs per
-        # mean job time
-        times = list(pool.imap_unordered(_oracle_sub_job, jobs[:cores], chunksize=1))  # waits for the set-up
-        t0 = time.perf_counter()
-        for chunk in range(cores, len(jobs), cores):
-            if time.perf_counter() - t0 > budget_s:
-                break
-            times += list(pool.imap_unordered(_oracle_sub_job, jobs[chunk:chunk + cores], chunksize=1))
-        done = len(times)
-        rate = cores / float(np.mean(times))  # subdomains (factor + one solve) per second, all cores
-    n_sub = (-(-n // W["core"])) ** 3
-    # the single-thread split: per subdomain factor and solve; keep the non-subdomain work serial
-    per_sub_single = (single["t_fac"] + single["t_sol"])
-    serial = single["value"] - n_sub * single["t_fac"] - iterations * n_sub * single["t_sol"]
-    speed = rate * per_sub_single  # all-core speed-up of the subdomain work
-    value = serial + (n_sub * single["t_fac"] + iterations * n_sub * single["t_sol"]) / max(speed, 1e-9)
+    one = _pool_job_times(ctx, 1, init_args, jobs[:3 * cores], 0.25 * budget_s)
+    many = _pool_job_times(ctx, cores, init_args, jobs, budget_s)
+    rate_one = 1.0 / float(np.mean(one))       # subdomains per second, one process
+    rate = cores / float(np.mean(many))        # subdomains per second, all cores busy
+    speed = rate / rate_one                    # all-core speed-up of the subdomain work
+    n_sub = sum(1 for _ in dd.subdomain_boxes(n, W["core"], W["overlap"]))
+    sub_single = n_sub * single["t_fac"] + iterations * n_sub * single["t_sol"]
+    serial = single["value"] - sub_single
+    value = serial + sub_single / max(speed, 1e-9)
     return {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": (f"subdomain factor + solve of {done} of the largest subdomains of the 30^3 geometry on a "
-                       f"{cores}-process pool ({rate:.1f} per s, {speed:.1f} x one core, the same size class and "
-                       f"timed region as the single-thread sample); build, SpMV and Arnoldi single-threaded; "
-                       f"{time.perf_counter() - t_start:.1f} s wall")}
+            "sample": (f"subdomain factor + solve of the largest subdomains of the 30^3 geometry: {len(one)} on a "
+                       f"1-process pool ({rate_one:.1f} per s), {len(many)} on a {cores}-process pool ({rate:.1f} per s): "
+                       f"{speed:.1f} x; the single-thread sample's subdomain work divided by that, its build, SpMV "
+                       f"and Arnoldi kept; {time.perf_counter() - t_start:.1f} s wall")}
 
 
 def run_serving(args):
