@@ -310,6 +310,26 @@ def kernel_table(prof, peak, steps):
 
 
 def cpu_baseline(W, iterations, budget_s=20.0):
+    """The oracle on a bounded sample of the workload, scaled to one step (see
+    _cpu_baseline_sample), run in a spawn-started worker process limited to one BLAS / OpenMP
+    thread, so that the reported `cores` (1) is the number of threads it used."""
+    import multiprocessing as mpr
+    ctx = mpr.get_context("spawn")
+    threads = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({v: "1" for v in threads})
+    try:
+        pool = ctx.Pool(1)
+    finally:
+        for v, old in threads.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    with pool:
+        return pool.apply(_cpu_baseline_sample, (W, iterations, budget_s))
+
+
+def _cpu_baseline_sample(W, iterations, budget_s=20.0):
     """The oracle on a bounded sample of the workload, scaled to one step.
 
     Times (single-threaded SciPy): the oracle's mesh + assembly + subdomain lists on a
