@@ -770,8 +770,13 @@ def main():
     if r["autotune"] is not None:
         line["autotune"] = r["autotune"]
     if world == 1 and not args.no_cpu_baseline and args.bc == "pec":
-        line["cpu_baseline"] = cpu_baseline(W, iters)
-        line["cpu_baseline_allcore"] = cpu_baseline_allcore(W, iters, line["cpu_baseline"])
+        # a failure of the CPU baselines is recorded in their keys, not allowed to drop the line
+        try:
+            line["cpu_baseline"] = cpu_baseline(W, iters)
+            line["cpu_baseline_allcore"] = cpu_baseline_allcore(W, iters, line["cpu_baseline"])
+        except Exception as e:  # noqa: BLE001
+            line.setdefault("cpu_baseline", {"error": f"{type(e).__name__}: {e}"})
+            line["cpu_baseline_allcore"] = {"error": f"{type(e).__name__}: {e}"}
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -57,3 +57,15 @@ def test_kernel_table_rates_per_step():
     assert s["gbs"] == pytest.approx(1000.0) and s["tflops"] == pytest.approx(1.0e9 / 0.02 / 1e12)
     assert s["hbm_frac"] == pytest.approx(1000.0 / 6797.2)
     assert t["local_solve"]["hbm_frac_of_nominal"] == pytest.approx(5000.0 / bench.HBM_NOMINAL_GBS)
+
+
+def test_oracle_baselines_on_a_tiny_workload():
+    """The single-thread sample (one-thread spawned worker) and the pool-against-pool all-core
+    estimate run end to end: 10^3 cells, 2^3 subdomains, every box shape sampled."""
+    W = dict(bench.WORKLOADS["maxwell60_k30_2lvl"], n=10, coarse=0, nrhs=2)
+    s = bench.cpu_baseline(W, 10, budget_s=2.0)
+    assert s["cores"] == 1 and s["value"] > 0 and s["t_fac"] > 0 and s["t_fac_largest"] >= s["t_fac"] * 0.5
+    assert "8 subdomains" in s["sample"]
+    a = bench.cpu_baseline_allcore(W, 10, s, budget_s=1.0)
+    assert a["cores"] >= 1 and a["value"] > 0
+    assert "1-process pool" in a["sample"]
