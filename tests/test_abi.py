@@ -80,3 +80,17 @@ def test_c_client_compiles_links_and_matches_the_binding():
     for name, (size, fields) in want.items():
         assert sizes[name] == size, name
         assert offsets[name] == fields, name
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define MX_* and enum value of include/mxas.h has a constant of the same
+    name and value in the Python binding."""
+    import paper_1711_03789_gb300 as mx
+    src = open(os.path.join(ROOT, "include", "mxas.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (MX_\w+)\s+\(?(-?\d+)\)?", src, re.M)}
+    for body in re.findall(r"typedef enum \{([^}]*)\}", src):
+        for name, val in re.findall(r"(MX_\w+)\s*=\s*(-?\d+)", body):
+            consts[name] = int(val)
+    assert len(consts) >= 24
+    for name, val in consts.items():
+        assert getattr(mx, name, None) == val, name
