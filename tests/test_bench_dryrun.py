@@ -1,7 +1,8 @@
 """bench.py's main paths on CPU with stand-ins for the library and for CUDA: the default
 solve benchmark (JSON contract keys, roofline, per-kernel table, e2e byte counts, launch
 count), the autotuner path (search, then a cache hit) and the serving mix with an offered-load
-sweep. Nothing here measures anything; it checks that the host code runs end to end and
+sweep, and the oracle arm (rank 0 prints, other ranks exit). Nothing here measures anything; it
+checks that the host code runs end to end and
 emits the line the contract asks for."""
 import contextlib
 import io
@@ -167,3 +168,19 @@ def test_serving_line_with_a_load_sweep(fakes, monkeypatch):
     for key in ("closed_loop", "poisson_0.5x", "poisson_0.8x", "poisson_1.2x"):
         assert line[key]["converged_rhs"] == line[key]["rhs"], key
     assert line["value"] == pytest.approx(line["poisson_0.8x"]["p99_ms"] / 1e3)
+
+
+def test_reference_arm_line_and_other_ranks(monkeypatch):
+    """The oracle arm on the small 10^3 workload: rank 0 prints the contract line, any other
+    rank exits without work."""
+    line = _run(monkeypatch, ["--impl", "reference", "--workload", "maxwell10_k6_1lvl", "--steps", "1",
+                              "--warmup", "1"])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "maxwell10_k6_1lvl"])
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.main()
+    assert buf.getvalue().strip() == ""
