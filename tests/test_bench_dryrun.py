@@ -1,9 +1,8 @@
 """bench.py's main paths on CPU with stand-ins for the library and for CUDA: the default
 solve benchmark (JSON contract keys, roofline, per-kernel table, e2e byte counts, launch
 count), the autotuner path (search, then a cache hit) and the serving mix with an offered-load
-sweep, and the oracle arm (rank 0 prints, other ranks exit). Nothing here measures anything; it
-checks that the host code runs end to end and
-emits the line the contract asks for."""
+sweep, and the oracle arm (rank 0 prints, other ranks exit). Nothing here measures anything;
+it checks that the host code runs end to end and emits the line the contract asks for."""
 import contextlib
 import io
 import json
