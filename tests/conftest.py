@@ -1,11 +1,31 @@
+import importlib.util
 import os
+import shutil
 import sys
+import warnings
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def _ensure_library():
+    """Build libmxas.so in-tree (or bring it up to date) before the tests import the package,
+    with the same build script as __graft_entry__.build(); a no-op when nothing changed. The
+    package itself still refuses to import without the library."""
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        return
+    spec = importlib.util.spec_from_file_location(
+        "_mxas_build", os.path.join(ROOT, "paper_1711_03789_gb300", "build.py"))
+    b = importlib.util.module_from_spec(spec)
+    try:
+        spec.loader.exec_module(b)
+        b.build()
+    except Exception as e:  # the library tests then fail on import with this cause
+        warnings.warn(f"building libmxas.so failed: {e}")
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long CPU test")
+    _ensure_library()
