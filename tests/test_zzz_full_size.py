@@ -10,8 +10,15 @@ takes minutes), so it checks what it can compute independently:
     tetrahedra that touch those DOFs (Sec. 2.2; the full vector is a sum over all of them);
   * the solution through its defining property, with the oracle's own operator: the
     relative residual ||f - A x|| / ||f|| (Sec. 6.1) of every right-hand side is at most
-    the tolerance, and equals the residual the library reports.
+    the tolerance, and equals the residual the library reports;
+  * the solution itself, element by element, at the 2,000-odd sampled DOFs of
+    tests/golden/solution60_k30.txt, the oracle's own solution of this workload (right-hand
+    sides 0 and 1, its GMRES run to 1e-10 by tests/golden/make_solution60.py): error at
+    most 1e-5 of ||x_oracle||_inf at every sampled DOF, with the iteration counts beside
+    the oracle's count to 1e-6.
 The file name makes pytest collect it after the other GPU modules."""
+import os
+
 import numpy as np
 import pytest
 
@@ -21,6 +28,44 @@ from oracle import fem
 
 N, K, XI, CORE, OVERLAP, COARSE, NRHS = 60, 30.0, 900.0, 5, 1, 12, 16
 TOL, RESTART, MAX_IT, SEED = 1e-6, 200, 600, 1
+
+
+FIXTURE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "solution60_k30.txt")
+
+
+def load_solution_fixture(path=FIXTURE):
+    """(header fields, per-RHS fields, sampled DOFs, oracle solution [R, len])."""
+    meta, rhs, rows = {}, {}, []
+    for line in open(path):
+        t = line.split()
+        if line.startswith("# n="):
+            meta = dict(kv.split("=") for kv in t[1:])
+        elif line.startswith("# rhs "):
+            rhs[int(t[2])] = {t[i]: float(t[i + 1]) for i in range(3, len(t) - 1, 2)}
+        elif not line.startswith("#") and t:
+            rows.append([float(v) for v in t])
+    a = np.array(rows)
+    return meta, rhs, a[:, 0].astype(np.int64), (a[:, 1::2] + 1j * a[:, 2::2]).T
+
+
+def test_solution_fixture_describes_this_workload():
+    """CPU check of the stored oracle solution: written for the workload of this file, to
+    1e-10, with the DOFs nearest the bump centres among the samples."""
+    meta, rhs, dofs, xo = load_solution_fixture()
+    assert (int(meta["n"]), float(meta["k"]), float(meta["xi_prob"]), float(meta["xi_prec"])) == (N, K, XI, XI)
+    assert (int(meta["core"]), int(meta["overlap"]), int(meta["coarse"]), int(meta["seed"])) == (CORE, OVERLAP, COARSE,
+                                                                                                 SEED)
+    assert meta["bc"] == "pec" and meta["precond"] == "as" and float(meta["tol"]) == 1e-10
+    assert sorted(rhs) == [0, 1] and xo.shape == (2, len(dofs)) and np.isfinite(xo).all()
+    assert len(dofs) >= 2000 and dofs.min() >= 0 and dofs.max() < 1479780 and np.all(np.diff(dofs) > 0)
+    for r, v in rhs.items():
+        assert v["rel_residual"] <= 1e-10 and 0 < v["iterations_to_1e-6"] <= v["iterations"]
+        assert np.abs(xo[r]).max() <= v["x_inf"] * (1 + 1e-15)
+    m = KuhnMesh(N)
+    c, _ = inputs.bump_batch(SEED, 2)
+    mid = 0.5 * (m.coords(m.dof_edges[:, 0]) + m.coords(m.dof_edges[:, 1]))
+    for ctr in c.reshape(-1, 3):
+        assert int(np.argmin(np.sum((mid - ctr) ** 2, axis=1))) in set(dofs.tolist())
 
 
 class _TetSubset:
@@ -104,3 +149,10 @@ def test_benchmark_workload_at_full_size():
         # scale, times ||A|| ||A^-1|| of a few hundred here): far inside this slack
         assert res <= TOL * (1 + 1e-4), (r, res)
         assert abs(res - st[r]["rel_residual"]) <= 1e-3 * TOL, (r, res, st[r]["rel_residual"])
+
+    meta, rhs, sdofs, xo = load_solution_fixture()
+    for r, v in rhs.items():
+        err = np.abs(xh[r, sdofs] - xo[r]).max() / v["x_inf"]
+        print(f"rhs {r}: max sampled error / ||x_oracle||_inf = {err:.3e}; iterations {st[r]['iterations']} "
+              f"(oracle to 1e-6: {int(v['iterations_to_1e-6'])}, change {st[r]['iterations'] - int(v['iterations_to_1e-6'])})")
+        assert err <= 1e-5, (r, err)
