@@ -11,6 +11,7 @@ import inputs
 from oracle.mesh import KuhnMesh
 from oracle import fem, dd
 from oracle.problem import Problem as OracleProblem
+from parity import assert_close, MIXED_APPLY_TOL, TF32_SOLVE_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -143,9 +144,8 @@ def test_preconditioner_apply(prec, levels, nrhs):
         mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, 0)  # FP32 CUDA-core local solves
         P.factor()
         z = P.precond(v, levels=levels)
-    tol = 1e-11 if prec == mx.MX_PLAIN_FP64 else 1e-4
-    err = np.linalg.norm(z - ze) / np.linalg.norm(ze)
-    assert err <= tol, err
+    tol = 1e-11 if prec == mx.MX_PLAIN_FP64 else MIXED_APPLY_TOL
+    assert_close(z, ze, tol, what=f"apply levels={levels}")
 
 
 @pytest.mark.parametrize("prec,cm,nrhs", [(mx.MX_PLAIN_FP64, 0, 1), (mx.MX_PLAIN_FP64, 5, 2),
@@ -163,10 +163,9 @@ def test_gmres_matches_oracle(prec, cm, nrhs):
         f = P.load_vector(c, p, 0.1)
         x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
     assert rc == mx.MX_OK
+    assert_close(x, xo.T, 1e-8, what="GMRES solution")
     for r in range(nrhs):
         assert st[r]["converged"]
-        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
-        assert err <= 1e-8, (r, err)
         res = np.linalg.norm(fo[:, r] - O.A @ x[r]) / np.linalg.norm(fo[:, r])
         assert res <= 1.05e-10, res
         if prec == mx.MX_PLAIN_FP64:
@@ -184,8 +183,8 @@ def test_restarted_gmres():
         P.factor()
         x, st, rc = P.solve(fo.T.copy(), tol=1e-9, restart=20, max_it=400)
     assert rc == mx.MX_OK
+    assert_close(x, xo.T, 1e-7, what="restarted GMRES solution")
     for r in range(2):
-        assert np.linalg.norm(x[r] - xo[:, r]) <= 1e-7 * np.linalg.norm(xo[:, r])
         assert abs(st[r]["iterations"] - ost[r][0]) <= 2
 
 
@@ -269,7 +268,7 @@ def test_local_solves_tensor_cores(n, nrhs, after):
     nrhs = 20 leaves a ragged group of 32. `after` switches the mode after factor (panel
     images built at the first solve). Bound: the factors enter rounded to TF32 (unit
     roundoff u = 2^-12 relative), so the solves carry a perturbation of a few u; the test
-    allows 8 u per right-hand side."""
+    allows 4 u per right-hand side, element-wise too (measured: under 2 u)."""
     k, xi = 10.0, 100.0
     O = OracleProblem(n, k, 0.0, xi, 5, 1)
     O.factor()
@@ -284,12 +283,8 @@ def test_local_solves_tensor_cores(n, nrhs, after):
         z = P.precond(v, levels=1)
         mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, 0)
         zc = P.precond(v, levels=1)
-    err = np.linalg.norm(z - ze) / np.linalg.norm(ze)
-    err_c = np.linalg.norm(zc - ze) / np.linalg.norm(ze)
-    print("tensor", err, "cuda cores", err_c)
-    per_rhs = np.linalg.norm(z - ze, axis=1) / np.linalg.norm(ze, axis=1)
-    assert np.isfinite(z).all()
-    assert per_rhs.max() <= 8 * 2.0**-12, (per_rhs.max(), err_c)
+    assert_close(z, ze, TF32_SOLVE_TOL, what="tensor-core local solves")
+    assert_close(zc, ze, MIXED_APPLY_TOL, what="CUDA-core c64 local solves")
 
 
 def test_gmres_tensor_core_local_solves():
@@ -308,11 +303,38 @@ def test_gmres_tensor_core_local_solves():
         f = P.load_vector(c, p, 0.1)
         x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
     assert rc == mx.MX_OK
+    assert_close(x, xo.T, 1e-8, what="GMRES solution, tensor-core local solves")
     for r in range(nrhs):
         assert st[r]["converged"]
-        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
-        assert err <= 1e-8, (r, err)
         assert st[r]["iterations"] <= 1.25 * ost[r][0], (st[r], ost[r])
+
+
+def test_mixed_gmres_16_rhs_matches_oracle():
+    """The benchmark's launch configuration on a 20^3 mesh (64 subdomains, a 4^3 coarse mesh,
+    k = 10, xi_prob = xi_prec = k^2): 16 right-hand sides in one batched mixed-form solve --
+    tensor-core local solves in one 16-wide group, the RHS-paired double-float Gram-Schmidt,
+    normalisation and update kernels, the c64 coarse inverse -- against the oracle's FP64
+    one-at-a-time solves, both to a 1e-10 relative residual: every solution element by
+    element, and iteration counts within 10 % (FGMRES absorbs the c64 / TF32 preconditioner
+    with at most a few more iterations)."""
+    n, k, nrhs, cm = 20, 10.0, 16, 4
+    xi = k * k
+    c, p = inputs.bump_batch(1, nrhs)
+    O = OracleProblem(n, k, xi, xi, 5, 1, coarse_m=cm)
+    O.factor()
+    fo = O.load_vector(c, p, 0.1)
+    xo, ost = O.solve(fo, tol=1e-10, restart=0, max_it=300)
+    with _handle(n, k, xi, xi, 5, 1, cm=cm, prec=mx.MX_MIXED) as P:
+        P.factor()
+        f = P.load_vector(c, p, 0.1)
+        x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
+    assert rc == mx.MX_OK
+    assert_close(x, xo.T, 1e-8, what="mixed GMRES, 16 right-hand sides")
+    for r in range(nrhs):
+        assert st[r]["converged"]
+        res = np.linalg.norm(fo[:, r] - O.A @ x[r]) / np.linalg.norm(fo[:, r])
+        assert res <= 1.05e-10, (r, res)
+        assert abs(st[r]["iterations"] - ost[r][0]) <= max(2, 0.1 * ost[r][0]), (r, st[r], ost[r])
 
 
 def test_mixed_gmres_tight_tolerance():
@@ -334,8 +356,7 @@ def test_mixed_gmres_tight_tolerance():
         assert st[r]["converged"] and st[r]["rel_residual"] <= 1e-12
         res = np.linalg.norm(fo[:, r] - O.A @ x[r]) / np.linalg.norm(fo[:, r])
         assert res <= 1.05e-12, res
-        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
-        assert err <= 1e-9, err
+    assert_close(x, xo.T, 1e-9, what="mixed GMRES at 1e-12")
 
 
 @pytest.mark.parametrize("n,cm,nrhs", [(10, 5, 3), (20, 10, 16), (20, 4, 20)])
@@ -343,7 +364,7 @@ def test_coarse_inverse_apply(n, cm, nrhs):
     """Mixed-form coarse solve with the explicit c64 inverse of A^0 against the oracle's
     pivoted sparse coarse solve (levels = 2: coarse correction only), and against the band
     sweeps of the same c64 factors. The inverse carries the rounding of the c64 factors and
-    an FP32 dense product: bound 1e-4 relative, as for the other c64 preconditioner parts."""
+    an FP32 dense product: the bound of the other c64 preconditioner parts (MIXED_APPLY_TOL)."""
     k, xi = 6.0, 36.0
     O = OracleProblem(n, k, 0.0, xi, 5, 1, coarse_m=cm)
     O.factor()
@@ -356,9 +377,8 @@ def test_coarse_inverse_apply(n, cm, nrhs):
             P.factor()
             out[mode] = P.precond(v, levels=2)
     for mode in (1, 0):
-        err = np.linalg.norm(out[mode] - ze) / np.linalg.norm(ze)
-        assert err <= 1e-4, (mode, err)
-    assert np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]) <= 1e-4
+        assert_close(out[mode], ze, MIXED_APPLY_TOL, what=f"coarse apply, inverse={mode}")
+    assert_close(out[1], out[0], MIXED_APPLY_TOL, what="inverse against band sweeps")
 
 
 @pytest.mark.parametrize("prec", [mx.MX_PLAIN_FP64, mx.MX_MIXED])
@@ -379,12 +399,12 @@ def test_restricted_and_hybrid_preconditioners(prec, kind, name):
         mx.mx_set_preconditioner(P.h, kind)
         z = P.precond(v, levels=3)
         z1 = P.precond(v, levels=1) if kind == mx.MX_PREC_RAS else None
-    tol = 1e-11 if prec == mx.MX_PLAIN_FP64 else 1e-4
+    tol = 1e-11 if prec == mx.MX_PLAIN_FP64 else MIXED_APPLY_TOL
     ze = O.dd.apply(v.T, levels=(1, 0), kind=name).T
-    assert np.linalg.norm(z - ze) / np.linalg.norm(ze) <= tol
+    assert_close(z, ze, tol, what=f"{name} apply")
     if z1 is not None:
         z1e = O.dd.apply(v.T, levels=(1,), kind="ras").T
-        assert np.linalg.norm(z1 - z1e) / np.linalg.norm(z1e) <= tol
+        assert_close(z1, z1e, tol, what="one-level RAS apply")
 
 
 @pytest.mark.parametrize("kind,name", [(mx.MX_PREC_RAS, "ras"), (mx.MX_PREC_HRAS, "hras"),
@@ -404,10 +424,9 @@ def test_gmres_with_restricted_and_hybrid_preconditioners(kind, name):
         f = P.load_vector(c, p, 0.1)
         x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
     assert rc == mx.MX_OK
+    assert_close(x, xo.T, 1e-8, what=f"GMRES solution, {name}")
     for r in range(nrhs):
         assert st[r]["converged"]
-        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
-        assert err <= 1e-8, (r, err)
         assert abs(st[r]["iterations"] - ost[r][0]) <= 1, (st[r], ost[r])
 
 
@@ -429,10 +448,9 @@ def test_weighted_gmres_matches_oracle(prec):
         f = P.load_vector(c, p, 0.1)
         x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
     assert rc == mx.MX_OK
+    assert_close(x, xo.T, 1e-8, what="weighted GMRES solution")
     for r in range(nrhs):
         assert st[r]["converged"]
-        err = np.linalg.norm(x[r] - xo[:, r]) / np.linalg.norm(xo[:, r])
-        assert err <= 1e-8, (r, err)
         res = fo[:, r] - O.A @ x[r]
         rel = np.sqrt(abs(np.vdot(res, Dk @ res))) / np.sqrt(abs(np.vdot(fo[:, r], Dk @ fo[:, r])))
         assert rel <= 1.05e-10 and abs(rel - st[r]["rel_residual"]) <= 1e-12, (rel, st[r])
@@ -453,4 +471,4 @@ def test_weighted_gmres_restarted():
         mx.mx_set_weighted_gmres(P.h, 1)
         x, st, rc = P.solve(fo.T.copy(), tol=1e-9, restart=8, max_it=400)
     assert rc == mx.MX_OK and st[0]["converged"]
-    assert np.linalg.norm(x[0] - xd) / np.linalg.norm(xd) <= 1e-7
+    assert_close(x[0], xd, 1e-7, what="restarted weighted GMRES solution")
