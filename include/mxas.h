@@ -70,8 +70,19 @@ typedef struct { int core_cells; int overlap_cells; } mx_dd_desc;
  * fine n_cells (nested meshes). n_cells = 0 gives the one-level preconditioner. */
 typedef struct { int n_cells; } mx_coarse_desc;
 
-/* Precision of the local factors and local solves. FP64 is always used for the
- * outer residual, the Arnoldi process, Givens rotations and the coarse factorisation. */
+/* Precision of the preconditioner and of the Krylov process.
+ *   MX_PLAIN_FP64: FP64 throughout (c128 local and coarse factors, FP64 Krylov kernels).
+ *   MX_MIXED: c64 local factors (local solves on tcgen05 TF32 with the right-hand-side block
+ *     as a TF32 hi + lo pair, or FP32 CUDA cores); c64 coarse band LU and its explicit c64
+ *     inverse; FP32 scatter. The Krylov basis V, the products A z_j and both classical
+ *     Gram-Schmidt passes use double-float arithmetic (pairs of FP32 values, about 48
+ *     significant bits; the first pass forms its products from the c64 rounding of V).
+ *     FP64 is kept for H, the Givens rotations, the least-squares solve, the solution x
+ *     and the true residual b - A x at every restart and at the end, which the stopping
+ *     test uses. GMRES is flexible (the stored z_j enter x), so the c64 preconditioner
+ *     changes the iteration count, not the FP64 residual the solve stops at.
+ *   The mixed form departs from an FP64 Arnoldi process and an FP64 coarse factorisation
+ *   because FP64 runs at about 1/64 of the FP32 rate on GB300. */
 typedef enum { MX_PLAIN_FP64 = 0, MX_MIXED = 1 } mx_precision;
 
 typedef struct mx_problem* mx_handle;
@@ -87,6 +98,8 @@ typedef struct {
   int64_t factor_bytes; /* device bytes held by local + coarse factors */
   int32_t coarse_band;  /* half-bandwidth of the coarse matrix */
   int32_t precision;
+  int32_t growth_subdomain; /* subdomain with the largest pivot growth (-1 before mx_factor) */
+  double max_growth;    /* largest max|U_ij| / max|A^l_ij| over the local LUs of the last mx_factor */
 } mx_problem_info;
 
 typedef struct {
@@ -221,8 +234,19 @@ MX_API int mx_set_stream(mx_handle h, void* stream);
  * in MX_PLAIN_FP64; LU-factor the coarse matrix A^0 (band-limited; FP64 in MX_PLAIN_FP64,
  * c64 in MX_MIXED, which also forms the explicit inverse unless MX_TUNE_COARSE_INVERSE
  * is 0), or, with MX_COARSE_GMRES, factor the inner problem's subdomains instead.
- * Returns MX_ESINGULAR when a pivot modulus falls below 1e-30 times the matrix scale. */
+ * Returns MX_ESINGULAR when a local or coarse pivot is zero or not finite, or when the
+ * pivot growth of a local LU, max|U_ij| / max|A^l_ij|, exceeds the growth limit
+ * (mx_set_growth_limit). Coercivity bounds the pivots away from zero but not the growth;
+ * the factors carry relative errors of about the unit roundoff times the growth. The
+ * largest growth is reported by mx_info. After MX_ESINGULAR or MX_ETIMEOUT the handle is
+ * left unfactored: mx_solve and mx_precond return MX_ENOTFACTORED until an mx_factor
+ * succeeds. */
 MX_API int mx_factor(mx_handle h);
+
+/* Pivot-growth limit of the local LU checked by mx_factor; limit <= 0 restores the default
+ * (1e6 for the c64 factors of MX_MIXED, 1e12 for MX_PLAIN_FP64). Takes effect at the next
+ * mx_factor. MX_EINVAL for a NaN limit. */
+MX_API int mx_set_growth_limit(mx_handle h, double limit);
 
 /* Load vectors f_i = int F . w_i (Sec. 2.2) for nrhs right-hand sides with
  * F(x) = sum_b pol_b exp(-|x - c_b|^2 / width^2):
@@ -303,17 +327,31 @@ MX_API int mx_get_local(mx_handle h, int l, double* out);
 MX_API int mx_dots(const void* V, const void* w, int64_t n, int nrhs, int nvec, void* h, void* stream);
 
 /* mx_dots for callers that cannot allocate device memory: a host framework that owns all
- * device memory through its own pool, or code recording CUDA graphs that must not allocate
- * between recordings. The paper has no counterpart; it is a deployment variant.
- * Same arguments, layouts and results as mx_dots, but the block partial sums live in a
- * fixed 4 MiB array inside the library's device image (held on every GPU that loads the
- * library until the process exits), so the call allocates nothing. Limit: nvec * nrhs <=
- * 16384, else MX_EINVAL with a message. The first call on a device looks the array's
- * device address up (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. All calls on one device share the array: calls that overlap
- * on the GPU (unordered streams or threads) race on it. Every word a call reads from the
- * array is written earlier in the same call, so no clearing is needed between calls. */
+ * device memory through its own pool and forbids side allocations (a cudaMalloc there
+ * would bypass its accounting or fail under its fixed budget), or an embedding that has
+ * no allocator to hand the library. The paper has no counterpart; it is a deployment
+ * variant. Same arguments and layouts as mx_dots and the same results to rounding: the
+ * block partial sums live in a fixed 4 MiB array inside the library's device image (held
+ * on every GPU that loads the library until the process exits), so the call allocates
+ * nothing; when nvec * nrhs is above about 860 the array holds fewer than 2 x SM-count
+ * partial-sum blocks, so the summation order, and with it the last bits, depends on
+ * nvec * nrhs. Limit: nvec * nrhs <= 16384, else MX_EINVAL with a message. The first call
+ * on a device looks the array's device address up (cudaGetSymbolAddress, with that device
+ * current) and keeps it for the life of the process, which assumes the device is not
+ * reset (cudaDeviceReset) in between; make that first call before any stream capture.
+ * Like mx_dots, the call synchronises `stream` before it returns. All calls on one device
+ * share the array: calls that overlap on the GPU (unordered streams or threads) race on
+ * it. Every word a call reads from the array is written earlier in the same call, so no
+ * clearing is needed between calls. */
 MX_API int mx_dots_noalloc(const void* V, const void* w, int64_t n, int nrhs, int nvec, void* h, void* stream);
+
+/* Failure-path check (no counterpart in the paper): launches `blocks` blocks (1..1024) whose
+ * first thread waits, with the same bounded mbarrier wait as the tensor-core kernels and a
+ * limit of `limit` polls (1..2^20), on an mbarrier that nothing arrives on. Every wait runs
+ * out, is counted in the handle's device error word and read back as the solves read it:
+ * returns MX_ETIMEOUT, after which the handle and the CUDA context remain usable. The
+ * probe holds no tensor memory and starts no copies. */
+MX_API int mx_test_bounded_wait(mx_handle h, int limit, int blocks);
 
 /* ---- Serving --------------------------------------------------------------------------
  * A request loop for many solves with different operators and right-hand-side counts on

@@ -20,6 +20,7 @@ from ._lib import (  # noqa: F401
     mx_launch_count, mx_profile, mx_profile_read, mx_profile_name, mx_dots, mx_dots_noalloc,
     mx_set_preconditioner, mx_set_weighted_gmres, MX_PREC_AS, MX_PREC_RAS, MX_PREC_HRAS, MX_PREC_ADEF1,
     mx_set_coarse_solver, MX_COARSE_DIRECT, MX_COARSE_GMRES, mx_get_boundary_mass, MX_BC_PEC, MX_BC_IMPEDANCE,
+    mx_set_growth_limit, mx_test_bounded_wait,
     mx_set_tuning, MX_TUNE_LOCAL_RHS_GROUP, MX_TUNE_LU_TENSOR, MX_TUNE_COARSE_BLOCKS, MX_TUNE_LOCAL_TENSOR, MX_TUNE_COARSE_INVERSE,
     mx_server_create, mx_server_submit, mx_server_poll, mx_server_stats, mx_server_destroy, MX_PENDING,
 )

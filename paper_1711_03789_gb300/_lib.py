@@ -39,7 +39,8 @@ class CoarseDesc(C.Structure):
 class ProblemInfo(C.Structure):
     _fields_ = [("n_dof", C.c_int64), ("nnz", C.c_int64), ("n_sub", C.c_int32), ("max_local", C.c_int32),
                 ("sum_local", C.c_int64), ("n_coarse", C.c_int64), ("nnz_r0", C.c_int64),
-                ("factor_bytes", C.c_int64), ("coarse_band", C.c_int32), ("precision", C.c_int32)]
+                ("factor_bytes", C.c_int64), ("coarse_band", C.c_int32), ("precision", C.c_int32),
+                ("growth_subdomain", C.c_int32), ("max_growth", C.c_double)]
 
 
 class RhsStats(C.Structure):
@@ -62,6 +63,8 @@ _sig = {
     "mx_last_error": (C.c_char_p, []),
     "mx_set_allocator": (C.c_int, [_ALLOC, _FREE, C.c_void_p]),
     "mx_set_dense_local": (C.c_int, [H, C.c_int]),
+    "mx_set_growth_limit": (C.c_int, [H, C.c_double]),
+    "mx_test_bounded_wait": (C.c_int, [H, C.c_int, C.c_int]),
     "mx_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
     "mx_set_preconditioner": (C.c_int, [H, C.c_int]),
     "mx_set_weighted_gmres": (C.c_int, [H, C.c_int]),
@@ -168,6 +171,17 @@ MX_TUNE_COARSE_INVERSE = 5
 
 def mx_set_tuning(h, key, value):
     _check(lib.mx_set_tuning(h, int(key), int(value)))
+
+
+def mx_set_growth_limit(h, limit):
+    """Pivot-growth limit checked by mx_factor (<= 0: the default for the precision)."""
+    _check(lib.mx_set_growth_limit(h, float(limit)))
+
+
+def mx_test_bounded_wait(h, limit=1024, blocks=4):
+    """Failure-path probe: bounded waits on an mbarrier nothing arrives on; returns the
+    library's code (MX_ETIMEOUT expected) without raising."""
+    return lib.mx_test_bounded_wait(h, int(limit), int(blocks))
 
 
 MX_PREC_AS, MX_PREC_RAS, MX_PREC_HRAS, MX_PREC_ADEF1 = 0, 1, 2, 3

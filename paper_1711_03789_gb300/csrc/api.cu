@@ -106,6 +106,39 @@ static int guard(F&& f) {
   }
 }
 
+// Pivot growth of the no-pivot local LU (Sec. 3.3 and Lemma 2.2 keep the pivots away from
+// zero, not the growth bounded): for every subdomain max|U_ij| / max|A^l_ij| from the maxima
+// the extraction and the factorisation kernels recorded; the largest is kept for mx_info, and
+// a value above the limit returns MX_ESINGULAR (the factors would carry relative errors of
+// the unit roundoff times the growth).
+double growth_limit_of(const Problem& P) {
+  return P.growth_limit > 0 ? P.growth_limit : (P.precision == MX_MIXED ? 1e6 : 1e12);
+}
+
+static void check_growth(Problem& P) {
+  P.max_growth = 0;
+  P.growth_worst = -1;
+  if (!P.n_sub || P.amax.n != (size_t)P.n_sub || P.umax.n != (size_t)P.n_sub) return;
+  std::vector<uint32_t> a(P.n_sub), u(P.n_sub);
+  MX_CUDA(cudaMemcpyAsync(a.data(), P.amax.p, 4 * P.n_sub, cudaMemcpyDeviceToHost, P.stream));
+  MX_CUDA(cudaMemcpyAsync(u.data(), P.umax.p, 4 * P.n_sub, cudaMemcpyDeviceToHost, P.stream));
+  MX_CUDA(cudaStreamSynchronize(P.stream));
+  for (int l = 0; l < P.n_sub; ++l) {
+    float fa, fu;
+    std::memcpy(&fa, &a[l], 4);
+    std::memcpy(&fu, &u[l], 4);
+    const double g = fa > 0 ? (double)fu / fa : (fu > 0 ? INFINITY : 0.0);
+    if (!(g <= P.max_growth)) {  // also takes a NaN
+      P.max_growth = g;
+      P.growth_worst = l;
+    }
+  }
+  const double lim = growth_limit_of(P);
+  MX_REQUIRE(P.max_growth <= lim, MX_ESINGULAR,
+             "pivot growth max|U| / max|A^l| = " + std::to_string(P.max_growth) + " in subdomain " +
+                 std::to_string(P.growth_worst) + " exceeds the limit " + std::to_string(lim));
+}
+
 static void check_status(Problem& P) {
   int32_t st[4] = {0, 0, 0, 0};
   MX_CUDA(cudaMemcpyAsync(st, P.status.p, 16, cudaMemcpyDeviceToHost, P.stream));
@@ -113,6 +146,7 @@ static void check_status(Problem& P) {
   MX_REQUIRE(st[0] == 0, MX_ESINGULAR, std::to_string(st[0]) + " zero or non-finite local pivots");
   MX_REQUIRE(st[1] == 0, MX_ESINGULAR, std::to_string(st[1]) + " zero or non-finite coarse pivots");
   MX_REQUIRE(st[2] == 0, MX_ETIMEOUT, std::to_string(st[2]) + " tensor-core waits ran out in the factorisation");
+  check_growth(P);
 }
 
 void transpose_to_internal(const double2* user, double2* in, int64_t n, int nrhs, cudaStream_t s) {
@@ -187,7 +221,15 @@ void factor_problem(Problem& P) {
     P.coarse_factored = P.coarse_m > 0;
   }
   P.timing.factor_ms = t.stop();
-  check_status(P);
+  try {
+    check_status(P);
+  } catch (...) {
+    // a singular, over-grown or timed-out factorisation is not used: the handle needs a
+    // successful mx_factor before the next solve
+    P.factored = false;
+    P.coarse_factored = false;
+    throw;
+  }
 }
 
 }  // namespace mx
@@ -237,6 +279,25 @@ int mx_set_dense_local(mx_handle h, int dense) {
     P.dense_local = dense != 0;
     P.minors_ready = false;
     P.factored = false;
+  });
+}
+
+int mx_set_growth_limit(mx_handle h, double limit) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    MX_REQUIRE(!std::isnan(limit), MX_EINVAL, "growth limit is NaN");
+    reinterpret_cast<Problem*>(h)->growth_limit = limit > 0 ? limit : 0;
+  });
+}
+
+int mx_test_bounded_wait(mx_handle h, int limit, int blocks) {
+  return guard([&] {
+    MX_REQUIRE(h, MX_EINVAL, "null handle");
+    MX_REQUIRE(limit >= 1 && limit <= (1 << 20), MX_EINVAL, "limit must be in 1..2^20");
+    MX_REQUIRE(blocks >= 1 && blocks <= 1024, MX_EINVAL, "blocks must be in 1..1024");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    const int32_t timeouts = wait_probe(P, limit, blocks);
+    MX_REQUIRE(timeouts == 0, MX_ETIMEOUT, std::to_string(timeouts) + " bounded waits ran out (probe)");
   });
 }
 
@@ -405,6 +466,8 @@ int mx_info(mx_handle h, mx_problem_info* out) {
       out->factor_bytes += (int64_t)Q->factors.bytes() + (int64_t)Q->dinv.bytes() + (int64_t)Q->panels.bytes();
     out->coarse_band = P.coarse_band;
     out->precision = P.precision;
+    out->growth_subdomain = P.growth_worst;
+    out->max_growth = P.max_growth;
   });
 }
 

@@ -587,7 +587,11 @@ struct ImpArgs {
   const int64_t* moff;
   void* out;
   int32_t* bad;  // entries outside the planned band or columns outside the box (none expected)
+  uint32_t* amax;  // [n_sub] largest |entry| written, as FP32 bits
 };
+
+__device__ inline uint32_t abs_bits_imp(float2 v) { return __float_as_uint(sqrtf(v.x * v.x + v.y * v.y)); }
+__device__ inline uint32_t abs_bits_imp(double2 v) { return __float_as_uint((float)sqrt(v.x * v.x + v.y * v.y)); }
 
 // One thread per (subdomain, local row): the row of the box's Galerkin matrix with the
 // impedance term on the box surface, written into the band storage at the local columns.
@@ -612,6 +616,7 @@ __global__ void k_extract_imp(ImpArgs a) {
     const int bw = a.band[l], ldl = a.ld[l];
     const int64_t off = a.moff[l];
     T2* A = reinterpret_cast<T2*>(a.out);
+    uint32_t amax = 0;
     for (int e = 0; e < R.m; ++e) {
       const int32_t cd = R.cols[e];
       int j = -1;
@@ -624,8 +629,11 @@ __global__ void k_extract_imp(ImpArgs a) {
         continue;
       }
       const double K = a.sK * (double)R.ik[e], M = a.sM * (double)R.im[e], B = a.sB * (double)R.ib[e];
-      A[bidx(off, ldl, bw, i, j)] = conv<T2>(make_double2(K - a.k2 * M, -a.xi * M - a.c * B));
+      const T2 v = conv<T2>(make_double2(K - a.k2 * M, -a.xi * M - a.c * B));
+      A[bidx(off, ldl, bw, i, j)] = v;
+      amax = max(amax, abs_bits_imp(v));
     }
+    if (a.amax) atomicMax(a.amax + l, amax);
   }
 }
 
@@ -637,7 +645,7 @@ void extract_imp(Problem& P) {
   MX_CUDA(cudaMemsetAsync(bad.p, 0, 4, s));
   ImpArgs a{P.n, P.n_sub, P.sum_local, 2.0 / (3.0 * h), h / 120.0, 1.0 / 24.0, P.k * P.k, P.xi_prec,
             imp_coef(P, P.xi_prec), dbox.p, P.offsets.p, P.lists.p, P.fine.dof_key.p, P.fine.tet2dof.p,
-            P.inv_ptr.p, P.inv_pos.p, P.band.p, P.ld.p, P.mat_off.p, P.factors.p, bad.p};
+            P.inv_ptr.p, P.inv_pos.p, P.band.p, P.ld.p, P.mat_off.p, P.factors.p, bad.p, P.amax.p};
   ProfScope ps(K_EXTRACT, s);
   if (P.precision == MX_MIXED)
     MX_LAUNCH(k_extract_imp<float2><<<grid_for(P.sum_local, 128), 128, 0, s>>>(a));

@@ -48,7 +48,13 @@ struct ExtractArgs {
   const int32_t* ld;
   const int64_t* moff;
   void* out;
+  uint32_t* amax;  // [n_sub] largest |entry| written, as FP32 bits (write pass)
 };
+
+// modulus as FP32 bits: for non-negative floats the bit patterns order like the values, so
+// an unsigned atomicMax over them takes the maximum in any arrival order
+__device__ inline uint32_t abs_bits(float2 v) { return __float_as_uint(sqrtf(v.x * v.x + v.y * v.y)); }
+__device__ inline uint32_t abs_bits(double2 v) { return __float_as_uint((float)sqrt(v.x * v.x + v.y * v.y)); }
 
 template <typename T2, bool WRITE>
 __global__ void k_extract(ExtractArgs a) {
@@ -62,6 +68,7 @@ __global__ void k_extract(ExtractArgs a) {
     int bw = 0;
     int ldl = 0;
     int64_t off = 0;
+    uint32_t amax = 0;
     if (WRITE) { bw = a.band[l]; ldl = a.ld[l]; off = a.moff[l]; }
     for (int32_t e = a.rowptr[g]; e < a.rowptr[g + 1]; ++e) {
       const int32_t c = a.col[e];
@@ -77,10 +84,13 @@ __global__ void k_extract(ExtractArgs a) {
         const double re = a.K[e] - a.sr * a.M[e];
         const double im = -a.si * a.M[e];
         T2* A = reinterpret_cast<T2*>(a.out);
-        A[bidx(off, ldl, bw, i, j)] = conv<T2>(make_double2(re, im));
+        const T2 v = conv<T2>(make_double2(re, im));
+        A[bidx(off, ldl, bw, i, j)] = v;
+        amax = max(amax, abs_bits(v));
       }
     }
     if (!WRITE) atomicMax(&a.band[l], bmax);
+    else if (a.amax) atomicMax(a.amax + l, amax);
   }
 }
 
@@ -118,9 +128,17 @@ __global__ void k_lu_diag(BandBatch B, T2* A, int k0, int32_t* status) {
     }
     __syncthreads();
   }
+  uint32_t um = 0;
   for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
     const int i = t % kb, j = t / kb;
-    if (abs(i - j) <= b) A[bidx(off, ld, b, k0 + i, k0 + j)] = s[i][j];
+    if (abs(i - j) <= b) {
+      A[bidx(off, ld, b, k0 + i, k0 + j)] = s[i][j];
+      if (i <= j) um = max(um, abs_bits(s[i][j]));
+    }
+  }
+  if (B.umax) {  // every thread of the block gets here (the early returns are block-uniform)
+    um = __reduce_max_sync(0xffffffffu, um);
+    if ((threadIdx.x & 31) == 0) atomicMax(B.umax + m, um);
   }
 }
 
@@ -148,10 +166,12 @@ __global__ void k_lu_panel(BandBatch B, T2* A, int k0) {
   __syncthreads();
   const bool rows = (int)blockIdx.y < chunks;
   const int idx = ((rows ? blockIdx.y : blockIdx.y - chunks) * blockDim.x) + threadIdx.x;
-  if (idx >= span) return;
+  uint32_t um = 0;  // largest |U12| entry of this thread's column
   // loops fully unrolled over NB (entries k >= kb are zero and unused), so x stays in registers
   T2 x[NB];
-  if (rows) {
+  if (idx >= span) {
+    // past the band: nothing to compute; stays for the block's growth reduction below
+  } else if (rows) {
     const int i = k1 + idx;
 #pragma unroll
     for (int k = 0; k < NB; ++k)
@@ -184,7 +204,14 @@ __global__ void k_lu_panel(BandBatch B, T2* A, int k0) {
     }
 #pragma unroll
     for (int k = 0; k < NB; ++k)
-      if (k < kb && j - (k0 + k) <= b) A[bidx(off, ld, b, k0 + k, j)] = x[k];
+      if (k < kb && j - (k0 + k) <= b) {
+        A[bidx(off, ld, b, k0 + k, j)] = x[k];
+        um = max(um, abs_bits(x[k]));
+      }
+  }
+  if (B.umax && !rows) {  // block-uniform branch: all 256 threads take part
+    um = __reduce_max_sync(0xffffffffu, um);
+    if ((threadIdx.x & 31) == 0 && um) atomicMax(B.umax + m, um);
   }
 }
 
@@ -384,6 +411,9 @@ void extract_minors(Problem& P) {
   a.ld = P.ld.p;
   a.moff = P.mat_off.p;
   a.out = P.factors.p;
+  P.amax.alloc(P.n_sub);
+  MX_CUDA(cudaMemsetAsync(P.amax.p, 0, P.amax.bytes(), s));
+  a.amax = P.amax.p;
   if (P.bc == MX_BC_IMPEDANCE)
     extract_imp(P);  // ImpRAS: Galerkin matrices of the closed boxes, not minors of A
   else if (P.precision == MX_MIXED)
@@ -458,7 +488,9 @@ void factor_local(Problem& P) {
 // queue the batched LU and the diagonal-block inversion (no host wait)
 void factor_local_launch(Problem& P) {
   if (!P.minors_ready) extract_minors(P);
-  BandBatch B{P.n_sub, P.nl.p, P.band.p, P.ld.p, P.mat_off.p};
+  P.umax.alloc(P.n_sub);
+  MX_CUDA(cudaMemsetAsync(P.umax.p, 0, P.umax.bytes(), P.stream));
+  BandBatch B{P.n_sub, P.nl.p, P.band.p, P.ld.p, P.mat_off.p, P.umax.p};
   int max_span = 0;
   for (int l = 0; l < P.n_sub; ++l) max_span = std::max(max_span, std::min(P.h_band[l], P.h_nl[l]));
   // offsets of the inverted diagonal blocks

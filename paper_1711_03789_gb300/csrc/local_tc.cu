@@ -535,6 +535,33 @@ static void launch_tc(const TcArgs& a, int n_sub, cudaStream_t s, double alg_byt
   MX_CHECK_LAUNCH();
 }
 
+// Failure-path probe. Thread 0 of every block initialises an mbarrier that nothing ever
+// arrives on and waits on it with the bounded wait of the tensor-core kernels (`limit`
+// polls); the wait runs out and the block adds one to status[2], as a timed-out wait in a
+// real kernel does, then returns. The block holds no tensor memory and has no copies in
+// flight, so nothing is left to drain.
+__global__ void k_wait_probe(int limit, int32_t* status) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t a = tc::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(a, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(a, 0, limit)) atomicAdd(status + 2, 1);
+}
+
+int32_t wait_probe(Problem& P, int limit, int blocks) {
+  cudaStream_t s = P.stream;
+  MX_CUDA(cudaMemsetAsync(P.status.p + 2, 0, sizeof(int32_t), s));
+  MX_LAUNCH(k_wait_probe<<<blocks, 32, 0, s>>>(limit, P.status.p));
+  MX_CHECK_LAUNCH();
+  int32_t timeouts = 0;
+  MX_CUDA(cudaMemcpyAsync(&timeouts, P.status.p + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  return timeouts;
+}
+
 // z_l = (A^l)^{-1} R^l v on the tensor cores (mixed form; panels built)
 void local_solves_tc(Problem& P, const void* v, int vtype, void* loc, int nrhs, double alg_bytes, double alg_flops) {
   MX_REQUIRE(P.panels_ok, MX_EINVAL, "tensor-core local solve without panel images");

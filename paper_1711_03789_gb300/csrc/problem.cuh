@@ -48,6 +48,7 @@ struct BandBatch {
   const int32_t* b;    // [count] half-bandwidth
   const int32_t* ld;   // [count] leading dimension (>= 2 b + 1)
   const int64_t* off;  // [count] element offsets
+  uint32_t* umax;      // [count] largest |U_ij| met by the factorisation, as FP32 bits (or null)
 };
 
 __host__ __device__ inline int64_t bidx(int64_t off, int ld, int b, int i, int j) {
@@ -133,6 +134,11 @@ struct Problem {
   DevBuf<float2> A0inv;
   DevBuf<float2> c_part;  // split-K partial products of the dense coarse apply
   DevBuf<int32_t> status; // [4] device error words: 0 local pivot, 1 coarse pivot, 2 timeout
+  // pivot growth of the local LU: largest |A^l_ij| and |U_ij| per subdomain (FP32 bits)
+  DevBuf<uint32_t> amax, umax;
+  double growth_limit = 0;   // 0: default (1e6 for c64 factors, 1e12 for c128)
+  double max_growth = 0;     // max over subdomains of max|U| / max|A^l| after the last factor
+  int growth_worst = -1;     // the subdomain that reached it
   bool coarse_factored = false;  // direct coarse factors built
   // inexact coarse solve (Sec. 6.4): an inner GMRES on A^0 y = R^0 v, preconditioned by
   // one-level Schwarz on subdomains of the coarse mesh -- a problem of its own, built on
@@ -213,6 +219,9 @@ void build_panels(Problem& P);
 int64_t panel_bytes_planned(const Problem& P);
 // the local solves of local_solves() on the tensor cores (requires P.panels_ok)
 void local_solves_tc(Problem& P, const void* v, int vtype, void* loc, int nrhs, double alg_bytes, double alg_flops);
+// bounded waits on an mbarrier nothing arrives on, in `blocks` blocks; returns how many ran
+// out (read back through status[2], as after the local solves)
+int32_t wait_probe(Problem& P, int limit, int blocks);
 
 // ---- coarse.cu ----------------------------------------------------------------------
 void factor_coarse(Problem& P);

@@ -46,6 +46,8 @@ int main(void) {
   expect(mx_factor(NULL) == MX_EINVAL, "mx_factor(NULL)");
   expect(mx_set_tuning(NULL, MX_TUNE_LOCAL_TENSOR, 1) == MX_EINVAL, "mx_set_tuning(NULL)");
   expect(mx_set_preconditioner(NULL, MX_PREC_RAS) == MX_EINVAL, "mx_set_preconditioner(NULL)");
+  expect(mx_set_growth_limit(NULL, 10.0) == MX_EINVAL, "mx_set_growth_limit(NULL)");
+  expect(mx_test_bounded_wait(NULL, 16, 1) == MX_EINVAL, "mx_test_bounded_wait(NULL)");
   mx_destroy(NULL);
 
   mx_server srv = NULL;
@@ -78,6 +80,8 @@ int main(void) {
   OFF(mx_problem_info, factor_bytes);
   OFF(mx_problem_info, coarse_band);
   OFF(mx_problem_info, precision);
+  OFF(mx_problem_info, growth_subdomain);
+  OFF(mx_problem_info, max_growth);
   SIZE(mx_rhs_stats);
   OFF(mx_rhs_stats, iterations);
   OFF(mx_rhs_stats, converged);
