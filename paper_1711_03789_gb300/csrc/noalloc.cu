@@ -3,15 +3,20 @@
 //
 // Who needs it: code that runs where cudaMalloc is off limits, for instance a host
 // framework that owns all device memory through its own pool and forbids side
-// allocations, or a process that records its work into CUDA graphs and must not
-// allocate between recordings. mx_dots allocates its block partial sums per call;
-// this variant keeps them in one fixed array in the library's device image instead.
+// allocations (a side cudaMalloc would escape its accounting or fail under its fixed
+// budget), or an embedding with no allocator to hand the library. mx_dots allocates its
+// block partial sums per call; this variant keeps them in one fixed array in the
+// library's device image instead.
 //
 // The scratch is the file-scope array below (4 MiB). Every GPU that loads the library
 // holds it until the process exits. Its device address is looked up once per device
 // with cudaGetSymbolAddress (the array's name is only a host-side stand-in in host code);
 // the first call on a device performs that look-up, so make the first call before any
-// stream capture. All calls on a device share the array: calls that overlap on the GPU
+// stream capture. The address is kept for the life of the process, which assumes the
+// device is not reset (cudaDeviceReset) in between. The call synchronises its stream
+// before it returns, like mx_dots. When nvec * nrhs is above about 860 the array holds
+// fewer than 2 x SM-count partial-sum blocks, so the summation order (and the last bits
+// of the result) differ from mx_dots. All calls on a device share the array: calls that overlap on the GPU
 // (different streams or threads without ordering) race on it. Each call rewrites every
 // scratch word it later reads (partials, result, flags), so nothing has to start at zero.
 #include <mutex>
@@ -20,7 +25,8 @@
 
 namespace mx {
 
-// 4 MiB of complex128 scratch: flags (first 16 entries = 32 int32), result, partials.
+// 4 MiB of complex128 scratch: flags (the first 16 entries, 256 B: room for 64 int32, of
+// which the first nrhs <= 32 are used), then the result, then the block partials.
 constexpr int64_t NOALLOC_ENTRIES = 262144;
 constexpr int64_t NOALLOC_FLAG_ENTRIES = 16;
 static __device__ __align__(256) double2 g_dots_scratch[NOALLOC_ENTRIES];
