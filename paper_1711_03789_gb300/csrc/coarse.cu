@@ -365,8 +365,10 @@ static void coarse_solve_inner(Problem& P, const void* v, int vtype, double2* yc
 void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
   cudaStream_t s = P.stream;
   const int64_t nc = P.n_c;
-  // R^0 (12 B per entry) and one gather of v per entry (worst case), output once
-  const double rb = 12.0 * P.R0.nnz + 4.0 * nc + 16.0 * (double)P.R0.nnz * nrhs + 16.0 * nc * nrhs;
+  // unique bytes: R^0 (12 B per entry, row pointers), the input block read once (every fine
+  // DOF has a nonzero column in R^0) and the output once; the repeated gathers of v hit L2
+  const double vb = vtype == 1 ? 8.0 : 16.0, ob = P.precision == MX_MIXED ? 8.0 : 16.0;
+  const double rb = 12.0 * P.R0.nnz + 4.0 * (nc + 1) + vb * (double)P.fine.n_dof * nrhs + ob * nc * nrhs;
   if (P.coarse_inner) {
     coarse_solve_inner(P, v, vtype, yc, nrhs, rb);
     return;

@@ -147,9 +147,26 @@ def test_default_solve_benchmark_line(fakes, monkeypatch):
     r = line["roofline"]
     assert r["kernel"] == "local_solve" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert list(line["kernels"]) == ["local_solve", "spmv"]
-    # 3 warm-up + 2 timed + 2 end-to-end steps, each: build, factor, load, solve
+    # 3 warm-up + 2 timed + 2 end-to-end steps, then one untimed + one timed step of each
+    # of the three variant legs; every step: build, factor, load, solve
+    problems = [e for e in FakeProblem.log if e[0] == "Problem"]
+    assert len(problems) == 13
+    assert sum(1 for e in FakeProblem.log if e[0] == "solve") == 13
+    # the plain FP64 leg, then xi = k^1.5 on both sides, then the literal xi_prob = 0 setting
+    k15 = 30.0 ** 1.5
+    assert [e[8] for e in problems[7:9]] == [L.MX_PLAIN_FP64] * 2
+    assert [(e[3], e[4]) for e in problems[9:11]] == [(k15, k15)] * 2
+    assert [(e[3], e[4]) for e in problems[11:13]] == [(0.0, k15)] * 2
+    assert [e[3] for e in FakeProblem.log if e[0] == "solve"][-1] == 400  # max_it of the literal leg
+    assert line["plain_fp64"]["value"] == pytest.approx(0.6) and line["mixed_speedup"] == pytest.approx(2.0)
+    assert set(line["xi_variants"]) == {"xi_k1.5", "config5_literal"}
+    assert line["xi_variants"]["config5_literal"]["max_it"] == 400
+
+
+def test_no_variants_runs_only_the_timed_workload(fakes, monkeypatch):
+    line = _run(monkeypatch, ["--steps", "2", "--warmup", "3", "--no-cpu-baseline", "--no-variants"])
     assert sum(1 for e in FakeProblem.log if e[0] == "Problem") == 7
-    assert sum(1 for e in FakeProblem.log if e[0] == "solve") == 7
+    assert "plain_fp64" not in line and "xi_variants" not in line
 
 
 def test_autotune_path_searches_then_hits_the_cache(fakes, monkeypatch, tmp_path):
