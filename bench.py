@@ -731,8 +731,10 @@ def main():
     ap.add_argument("--coarse-tol", type=float, default=0.1)
     ap.add_argument("--coarse-max-it", type=int, default=100)
     ap.add_argument("--coarse-inner", default="ras", choices=["ras", "as"])
-    ap.add_argument("--lu-tensor", type=int, default=None, choices=[0, 1, 3],
-                    help="local LU trailing update: 0 CUDA cores, 1 TF32, 3 split 3 x TF32 tensor cores")
+    ap.add_argument("--lu-tensor", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="local LU: 0 (library default) or 2 one persistent launch with 3 x TF32 tensor-core "
+                         "updates; one launch per step with 1 TF32, 3 split 3 x TF32 tensor-core or 4 FP32 CUDA-core "
+                         "updates")
     ap.add_argument("--local-tensor", type=int, default=None, choices=[0, 1],
                     help="local solves on the tensor cores (1) or CUDA cores (0); default: library default")
     ap.add_argument("--autotune", default=None, metavar="CACHE.json",

@@ -138,9 +138,12 @@ MX_API int mx_set_dense_local(mx_handle h, int dense);
  *   MX_TUNE_LOCAL_RHS_GROUP: most right-hand sides one local-solve block handles
  *   (power of two, 1..16; default 16). Smaller groups run more blocks per subdomain. */
 #define MX_TUNE_LOCAL_RHS_GROUP 1
-/*   MX_TUNE_LU_TENSOR: trailing update of the MX_MIXED local LU; 3 = tcgen05 tensor cores
- *   with three TF32 products per term (hi*hi + hi*lo + lo*hi, close to FP32), 1 = one TF32
- *   product, 0 (default) = FP32 CUDA cores. MX_PLAIN_FP64 always uses FP64 CUDA cores. */
+/*   MX_TUNE_LU_TENSOR: the MX_MIXED local LU. 0 (default) or 2 = one persistent launch, one
+ *   CTA per subdomain running all of its block steps with the trailing updates on tcgen05
+ *   tensor cores, three TF32 products per term (hi*hi + hi*lo + lo*hi, close to FP32); the
+ *   subdomain's trailing window stays in L2 between its steps. One launch per block step for
+ *   the whole batch: 3 = tcgen05 with three TF32 products, 1 = one TF32 product, 4 = FP32
+ *   CUDA cores. MX_PLAIN_FP64 always uses FP64 CUDA cores. */
 #define MX_TUNE_LU_TENSOR 2
 /*   MX_TUNE_COARSE_BLOCKS: thread blocks of the cooperative coarse sweep (0 = sized by the
  *   band work, at most one per SM); fewer blocks make its grid-wide barriers cheaper. */

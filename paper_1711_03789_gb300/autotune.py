@@ -49,7 +49,7 @@ def candidates(info, cfg, name, allow_reduced=False):
     coarse = info["n_coarse"] > 0
     if name == "lu_tensor":
         # 1 (a single TF32 product) changes the factors' accuracy: only on request
-        return ([0, 3, 1] if allow_reduced else [0, 3]) if mixed else []
+        return ([0, 3, 4, 1] if allow_reduced else [0, 3, 4]) if mixed else []
     if name == "coarse_inverse":
         return [1, 0] if (mixed and coarse) else []
     if name == "local_tensor":

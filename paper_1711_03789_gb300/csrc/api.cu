@@ -313,7 +313,7 @@ int mx_set_tuning(mx_handle h, int key, int value) {
       MX_REQUIRE(value >= 0 && value <= 4096, MX_EINVAL, "coarse blocks must be in 0..4096");
       P.tune_coarse_blocks = value;
     } else if (key == MX_TUNE_LU_TENSOR) {
-      MX_REQUIRE(value == 0 || value == 1 || value == 3, MX_EINVAL, "LU tensor mode must be 0, 1 or 3");
+      MX_REQUIRE(value >= 0 && value <= 4, MX_EINVAL, "LU tensor mode must be in 0..4");
       P.tune_lu_tc = value;
     } else if (key == MX_TUNE_COARSE_INVERSE) {
       MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "coarse inverse mode must be 0 or 1");

@@ -87,7 +87,8 @@ struct Problem {
   // (plain), matrix l at mat_off[l] elements.
   bool dense_local = false;        // force b_l = n_l - 1 (full dense storage)
   int tune_local_group = 0;        // cap on right-hand sides per local-solve block (0 = 16)
-  int tune_lu_tc = 0;              // FP32 LU trailing update: 0 CUDA cores, 1 TF32, 3 split 3 x TF32
+  int tune_lu_tc = 0;              // FP32 local LU: 0 / 2 persistent 3 x TF32 tensor-core LU, per-step
+                                   // launches with 1 TF32 or 3 split 3 x TF32 tensor-core updates, 4 FP32 CUDA cores
   int tune_coarse_blocks = 0;      // blocks of the cooperative coarse sweep (0 = by work)
   std::vector<int32_t> h_band;     // [n_sub] half-bandwidths
   int64_t band_entries = 0;        // sum over subdomains of entries with |i - j| <= b_l
@@ -203,6 +204,10 @@ void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status
              const int32_t* hn, const int32_t* hb, int kid_update, int tc_split);
 // one tcgen05 trailing-update step of the FP32 band LU (lu_tc.cu); split 1 or 3 TF32 products
 void lu_update_tc(const BandBatch& B, float2* A, int k0, int max_span, int split, int32_t* status, cudaStream_t s);
+// the whole FP32 band LU of every matrix of the batch in one persistent launch, one CTA per
+// matrix, tcgen05 trailing updates (lu_fused.cu); bytes / flops: algorithmic, for the profiler
+void band_lu_fused(const BandBatch& B, float2* A, int split, int32_t* status, cudaStream_t s, double bytes,
+                   double flops);
 template <typename T2>
 void invert_diag_blocks(const BandBatch& B, const T2* A, const int64_t* doff, T2* Dinv, int max_n, cudaStream_t s);
 // z_l = (A^l)^{-1} R^l v for every l, written at the subdomain positions of `loc`

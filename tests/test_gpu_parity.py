@@ -240,10 +240,12 @@ def test_batched_dots(nvec, n, nrhs):
     assert np.array_equal(hd.cpu().numpy(), h)
 
 
-@pytest.mark.parametrize("mode,tol", [(0, 2e-5), (3, 2e-5), (1, 5e-3)])
+@pytest.mark.parametrize("mode,tol", [(4, 2e-5), (3, 2e-5), (1, 5e-3), (2, 2e-5), (0, 2e-5)])
 def test_local_factor_tensor_core_modes(mode, tol):
-    """FP32 local LU with the trailing update on CUDA cores (0), tcgen05 3 x TF32 (3) and
-    tcgen05 TF32 (1): L U reproduces the minor to the precision of each mode."""
+    """FP32 local LU, one launch per block step with the trailing update on CUDA cores (4),
+    tcgen05 3 x TF32 (3) or tcgen05 TF32 (1), and the persistent one-CTA-per-subdomain LU with
+    3 x TF32 tcgen05 updates (2, and the default 0): L U reproduces the minor to the
+    precision of each mode."""
     n, k, xi = 10, 4.0, 16.0
     m = KuhnMesh(n)
     Ko, Mo = fem.assemble_KM(m)
@@ -257,6 +259,32 @@ def test_local_factor_tensor_core_modes(mode, tol):
             L = np.tril(F, -1) + np.eye(F.shape[0])
             Al = S.minor(l).toarray()
             assert np.abs(L @ np.triu(F) - Al).max() <= tol * np.abs(Al).max()
+
+
+def test_fused_local_factor_full_boxes():
+    """The persistent tensor-core LU (MX_TUNE_LU_TENSOR = 2, the default) on 20^3 cells: interior boxes of
+    7^3 cells (n_l = 1981, half-bandwidth about 350, so three 128-row tiles per window and a
+    ragged last tile) and boundary boxes; L U against the oracle's minors, and the factors
+    against those of the per-step CUDA-core LU of the same c64 minor."""
+    n, k, xi = 20, 10.0, 100.0
+    m = KuhnMesh(n)
+    Ko, Mo = fem.assemble_KM(m)
+    A = fem.a_xi(Ko, Mo, k, xi)
+    S = dd.Schwarz(m, A, 5, 1)
+    subs = (0, 21, 63)
+    out = {}
+    for mode in (2, 4):
+        with _handle(n, k, 0.0, xi, 5, 1, prec=mx.MX_MIXED) as P:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_TENSOR, mode)
+            P.factor()
+            out[mode] = {l: mx.mx_get_local(P.h, l, len(S.idx[l])) for l in subs}
+    for l in subs:
+        F = out[2][l]
+        Al = S.minor(l).toarray()
+        L = np.tril(F, -1) + np.eye(F.shape[0])
+        assert np.abs(L @ np.triu(F) - Al).max() <= 2e-5 * np.abs(Al).max(), l
+        G = out[4][l]
+        assert np.abs(F - G).max() <= 2e-5 * np.abs(G).max(), l
 
 
 @pytest.mark.parametrize("n,nrhs,after", [(10, 1, False), (10, 16, True), (20, 16, False), (20, 20, False),
@@ -285,6 +313,24 @@ def test_local_solves_tensor_cores(n, nrhs, after):
         zc = P.precond(v, levels=1)
     assert_close(z, ze, TF32_SOLVE_TOL, what="tensor-core local solves")
     assert_close(zc, ze, MIXED_APPLY_TOL, what="CUDA-core c64 local solves")
+
+
+def test_gmres_with_the_fused_tensor_core_factorisation():
+    """Mixed-form GMRES on factors from the persistent tensor-core LU reaches the oracle's
+    solution (both to 1e-10)."""
+    n, k, nrhs = 10, 6.0, 2
+    c, p = inputs.bump_batch(4, nrhs)
+    O = OracleProblem(n, k, k, k, 5, 1, coarse_m=5)
+    O.factor()
+    fo = O.load_vector(c, p, 0.1)
+    xo, ost = O.solve(fo, tol=1e-10, restart=0, max_it=300)
+    with _handle(n, k, k, k, 5, 1, cm=5, prec=mx.MX_MIXED) as P:
+        mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_TENSOR, 2)
+        P.factor()
+        f = P.load_vector(c, p, 0.1)
+        x, st, rc = P.solve(f, tol=1e-10, restart=0, max_it=300)
+    assert rc == mx.MX_OK and all(v["converged"] for v in st)
+    assert_close(x, xo.T, 1e-8, what="GMRES solution, fused tensor-core LU")
 
 
 def test_gmres_tensor_core_local_solves():
