@@ -151,6 +151,8 @@ def run_ours(args, W, rank, world):
             mx.mx_set_tuning(P.h, mx.MX_TUNE_LOCAL_TENSOR, args.local_tensor)
         if args.lu_tensor is not None:
             mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_TENSOR, args.lu_tensor)
+        if args.lu_grid is not None:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_GRID, args.lu_grid)
         if args.weighted:
             mx.mx_set_weighted_gmres(P.h, 1)
         if args.precond != "as":
@@ -735,6 +737,8 @@ def main():
                     help="local LU: 0 (library default) or 2 one persistent launch with 3 x TF32 tensor-core "
                          "updates; one launch per step with 1 TF32, 3 split 3 x TF32 tensor-core or 4 FP32 CUDA-core "
                          "updates")
+    ap.add_argument("--lu-grid", type=int, default=None,
+                    help="CTAs of the persistent local LU (0: one per subdomain); default: library default")
     ap.add_argument("--local-tensor", type=int, default=None, choices=[0, 1],
                     help="local solves on the tensor cores (1) or CUDA cores (0); default: library default")
     ap.add_argument("--autotune", default=None, metavar="CACHE.json",

@@ -139,9 +139,10 @@ MX_API int mx_set_dense_local(mx_handle h, int dense);
  *   (power of two, 1..16; default 16). Smaller groups run more blocks per subdomain. */
 #define MX_TUNE_LOCAL_RHS_GROUP 1
 /*   MX_TUNE_LU_TENSOR: the MX_MIXED local LU. 0 (default) or 2 = one persistent launch, one
- *   CTA per subdomain running all of its block steps with the trailing updates on tcgen05
- *   tensor cores, three TF32 products per term (hi*hi + hi*lo + lo*hi, close to FP32); the
- *   subdomain's trailing window stays in L2 between its steps. One launch per block step for
+ *   CTA per subdomain running all of its block steps, with the panels (from the inverted
+ *   diagonal blocks) and the trailing updates on tcgen05 tensor cores, three TF32 products
+ *   per term (hi*hi + hi*lo + lo*hi, about 1.2e-6 relative error per product against 6e-8 for
+ *   FP32; FP32 accumulation); the subdomain's trailing window stays in L2 between its steps. One launch per block step for
  *   the whole batch: 3 = tcgen05 with three TF32 products, 1 = one TF32 product, 4 = FP32
  *   CUDA cores. MX_PLAIN_FP64 always uses FP64 CUDA cores. */
 #define MX_TUNE_LU_TENSOR 2
@@ -160,6 +161,10 @@ MX_API int mx_set_dense_local(mx_handle h, int dense);
  *   identity) and every apply is one dense product, 0 = band triangular sweeps. Takes
  *   effect at the next mx_factor. */
 #define MX_TUNE_COARSE_INVERSE 5
+/*   MX_TUNE_LU_GRID: CTAs of the persistent local LU (MX_TUNE_LU_TENSOR 0 or 2), each taking
+ *   subdomains blockIdx, blockIdx + grid, ...; 0 (default) = one CTA per subdomain. A grid
+ *   below the SM count keeps fewer trailing windows resident, so that they share L2. */
+#define MX_TUNE_LU_GRID 6
 MX_API int mx_set_tuning(mx_handle h, int key, int value);
 
 /* Preconditioner variant (Sec. 6.3), applied by mx_solve and mx_precond:

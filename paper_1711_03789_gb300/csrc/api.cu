@@ -315,6 +315,9 @@ int mx_set_tuning(mx_handle h, int key, int value) {
     } else if (key == MX_TUNE_LU_TENSOR) {
       MX_REQUIRE(value >= 0 && value <= 4, MX_EINVAL, "LU tensor mode must be in 0..4");
       P.tune_lu_tc = value;
+    } else if (key == MX_TUNE_LU_GRID) {
+      MX_REQUIRE(value >= 0 && value <= 65536, MX_EINVAL, "LU grid must be in 0..65536");
+      P.tune_lu_grid = value;
     } else if (key == MX_TUNE_COARSE_INVERSE) {
       MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "coarse inverse mode must be 0 or 1");
       P.tune_coarse_inverse = value;

@@ -500,7 +500,7 @@ void factor_local_launch(Problem& P) {
   MX_CUDA(cudaMemcpyAsync(P.dinv_off.p, doff.data(), doff.size() * 8, cudaMemcpyHostToDevice, P.stream));
   const size_t esz = P.precision == MX_MIXED ? sizeof(float2) : sizeof(double2);
   P.dinv.alloc((size_t)doff[P.n_sub] * esz);
-  if (P.precision == MX_MIXED && (P.tune_lu_tc == 0 || P.tune_lu_tc == 2)) {
+  if (P.precision == MX_MIXED && (P.tune_lu_tc == 0 || P.tune_lu_tc == 2) && band_lu_fused_fits(max_span)) {
     // one persistent launch, one CTA per subdomain, tensor-core trailing updates; booked with
     // every band entry read and written once and the flops of the blocked LU
     double flops = 0;
@@ -510,10 +510,8 @@ void factor_local_launch(Problem& P) {
         const double span = std::max(0, std::min(P.h_nl[l] - k0 - (int)kb, P.h_band[l]));
         flops += 8.0 * span * span * kb + 8.0 * span * kb * kb + 8.0 / 3.0 * kb * kb * kb;
       }
-    band_lu_fused(B, reinterpret_cast<float2*>(P.factors.p), 3, P.status.p, P.stream,
-                  2.0 * sizeof(float2) * (double)P.band_entries, flops);
-    invert_diag_blocks<float2>(B, reinterpret_cast<float2*>(P.factors.p), P.dinv_off.p,
-                               reinterpret_cast<float2*>(P.dinv.p), P.max_local, P.stream);
+    band_lu_fused(B, reinterpret_cast<float2*>(P.factors.p), P.dinv_off.p, reinterpret_cast<float2*>(P.dinv.p), 3,
+                  P.tune_lu_grid, P.status.p, P.stream, 2.0 * sizeof(float2) * (double)P.band_entries, flops);
   } else if (P.precision == MX_MIXED) {
     band_lu<float2>(B, reinterpret_cast<float2*>(P.factors.p), P.max_local, max_span, P.status.p, P.stream,
                     P.h_nl.data(), P.h_band.data(), -1, P.tune_lu_tc == 4 ? 0 : P.tune_lu_tc);

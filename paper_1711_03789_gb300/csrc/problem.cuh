@@ -87,6 +87,7 @@ struct Problem {
   // (plain), matrix l at mat_off[l] elements.
   bool dense_local = false;        // force b_l = n_l - 1 (full dense storage)
   int tune_local_group = 0;        // cap on right-hand sides per local-solve block (0 = 16)
+  int tune_lu_grid = 0;            // CTAs of the persistent LU (0: one per subdomain)
   int tune_lu_tc = 0;              // FP32 local LU: 0 / 2 persistent 3 x TF32 tensor-core LU, per-step
                                    // launches with 1 TF32 or 3 split 3 x TF32 tensor-core updates, 4 FP32 CUDA cores
   int tune_coarse_blocks = 0;      // blocks of the cooperative coarse sweep (0 = by work)
@@ -206,8 +207,11 @@ void band_lu(const BandBatch& B, T2* A, int max_n, int max_span, int32_t* status
 void lu_update_tc(const BandBatch& B, float2* A, int k0, int max_span, int split, int32_t* status, cudaStream_t s);
 // the whole FP32 band LU of every matrix of the batch in one persistent launch, one CTA per
 // matrix, tcgen05 trailing updates (lu_fused.cu); bytes / flops: algorithmic, for the profiler
-void band_lu_fused(const BandBatch& B, float2* A, int split, int32_t* status, cudaStream_t s, double bytes,
-                   double flops);
+// also writes the inverted diagonal blocks (dinv at doff, as invert_diag_blocks does); needs
+// every half-bandwidth within band_lu_fused_fits
+void band_lu_fused(const BandBatch& B, float2* A, const int64_t* doff, float2* dinv, int split, int grid,
+                   int32_t* status, cudaStream_t s, double bytes, double flops);
+bool band_lu_fused_fits(int max_span);
 template <typename T2>
 void invert_diag_blocks(const BandBatch& B, const T2* A, const int64_t* doff, T2* Dinv, int max_n, cudaStream_t s);
 // z_l = (A^l)^{-1} R^l v for every l, written at the subdomain positions of `loc`

@@ -264,8 +264,11 @@ def test_local_factor_tensor_core_modes(mode, tol):
 def test_fused_local_factor_full_boxes():
     """The persistent tensor-core LU (MX_TUNE_LU_TENSOR = 2, the default) on 20^3 cells: interior boxes of
     7^3 cells (n_l = 1981, half-bandwidth about 350, so three 128-row tiles per window and a
-    ragged last tile) and boundary boxes; L U against the oracle's minors, and the factors
-    against those of the per-step CUDA-core LU of the same c64 minor."""
+    ragged last tile) and boundary boxes; L U against the oracle's minors (backward error 2e-5,
+    as for the per-step LU), and the factors against those of the per-step CUDA-core LU of the
+    same c64 minor. The two orders of FP32 arithmetic (panels from inverted diagonal blocks
+    against substitution) give factors that differ by rounding carried along the elimination,
+    a few times 1e-5 of the largest entry here; bound 2e-4."""
     n, k, xi = 20, 10.0, 100.0
     m = KuhnMesh(n)
     Ko, Mo = fem.assemble_KM(m)
@@ -279,12 +282,17 @@ def test_fused_local_factor_full_boxes():
             P.factor()
             out[mode] = {l: mx.mx_get_local(P.h, l, len(S.idx[l])) for l in subs}
     for l in subs:
-        F = out[2][l]
         Al = S.minor(l).toarray()
-        L = np.tril(F, -1) + np.eye(F.shape[0])
-        assert np.abs(L @ np.triu(F) - Al).max() <= 2e-5 * np.abs(Al).max(), l
-        G = out[4][l]
-        assert np.abs(F - G).max() <= 2e-5 * np.abs(G).max(), l
+        for mode in (2, 4):
+            F = out[mode][l]
+            L = np.tril(F, -1) + np.eye(F.shape[0])
+            be = np.abs(L @ np.triu(F) - Al).max() / np.abs(Al).max()
+            print(f"subdomain {l} mode {mode}: backward error {be:.2e}")
+            assert be <= 2e-5, (l, mode, be)
+        F, G = out[2][l], out[4][l]
+        d = np.abs(F - G).max() / np.abs(G).max()
+        print(f"subdomain {l}: factor difference {d:.2e}")
+        assert d <= 2e-4, (l, d)
 
 
 @pytest.mark.parametrize("n,nrhs,after", [(10, 1, False), (10, 16, True), (20, 16, False), (20, 20, False),
