@@ -649,7 +649,9 @@ def load_solution_fixture(path=SOLUTION_FIXTURE):
     for line in open(path):
         t = line.split()
         if line.startswith("# n="):
-            meta = dict(kv.split("=") for kv in t[1:])
+            meta.update(kv.split("=") for kv in t[1:])
+        elif line.startswith("# n_dof "):
+            meta["n_dof"] = t[2]
         elif line.startswith("# rhs "):
             rhs[int(t[2])] = {t[i]: float(t[i + 1]) for i in range(3, len(t) - 1, 2)}
         elif not line.startswith("#") and t:
@@ -671,7 +673,8 @@ def error_vs_oracle(W, args, x_sample, stats, rank):
             and xi_value(W["xi_prec"], k) == float(meta["xi_prec"]) and W["core"] == int(meta["core"])
             and W["overlap"] == int(meta["overlap"]) and W["coarse"] == int(meta["coarse"])
             and args.bc == meta["bc"] and args.precond == meta["precond"] and not args.weighted
-            and not args.coarse_gmres and rhs_seed(rank) == int(meta["seed"]) and x_sample.shape[0] >= len(rhs))
+            and not args.coarse_gmres and rhs_seed(rank) == int(meta["seed"]) and x_sample.shape[0] >= len(rhs)
+            and x_sample.shape[1] == int(meta["n_dof"]))
     if not same:
         return None
     out = {"fixture": os.path.relpath(SOLUTION_FIXTURE, ROOT), "dofs": int(len(dofs)), "oracle_tol": float(meta["tol"]),

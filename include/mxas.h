@@ -364,8 +364,13 @@ MX_API int mx_test_bounded_wait(mx_handle h, int limit, int blocks);
 /* ---- Serving --------------------------------------------------------------------------
  * A request loop for many solves with different operators and right-hand-side counts on
  * one GPU. Worker threads (each with its own CUDA stream) take the oldest pending request
- * together with every pending request of the same operator and solver settings (continuous
- * batching, at most 32 right-hand sides per batch); batches of different operators run
+ * together with every pending request of the same operator and solver settings as one batch
+ * of right-hand-side slots (twice the starting count rounded up to 8, at most 32). Continuous
+ * batching: at every GMRES restart boundary of a running batch, requests whose right-hand
+ * sides have all finished are returned at once, and pending requests of the same operator and
+ * settings are admitted into free slots and solved in the same run (mx_server_info.joined
+ * counts them); each slot keeps its own arithmetic, so a result does not depend on the
+ * requests it was batched with. Batches of different operators run
  * concurrently. Factorisations stay resident in HBM, cached by the preconditioner key
  * (n_cells, k, xi_prec, subdomains, coarse mesh, precision, boundary condition,
  * preconditioner variant; xi_prob does not enter it, since
@@ -398,6 +403,7 @@ typedef struct {
 typedef struct {
   int64_t batches, factorisations, evictions, completed, cached_bytes;
   int32_t cached_operators, pending;
+  int64_t joined;          /* requests admitted into a batch that was already running */
 } mx_server_info;
 
 #define MX_PENDING 1       /* mx_server_poll without wait: result not ready yet */

@@ -805,8 +805,13 @@ void batched_dots(const double2* V, const double2* w, int64_t n, int nrhs, int n
   MX_CHECK_LAUNCH();
 }
 
+__global__ void k_zero_cols(int64_t nv, int nrhs, const int32_t* mask, double2* x) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nv; t += (int64_t)gridDim.x * blockDim.x)
+    if (mask[t % nrhs]) x[t] = make_double2(0, 0);
+}
+
 int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, int restart, int max_it,
-                mx_rhs_stats* stats) {
+                mx_rhs_stats* stats, SlotHook* hook) {
   MX_REQUIRE(P.factored, MX_ENOTFACTORED, "mx_solve before mx_factor");
   MX_REQUIRE(nrhs >= 1 && nrhs <= 32, MX_EINVAL, "nrhs must be in 1..32 per batch");
   MX_REQUIRE(max_it >= 1, MX_EINVAL, "max_it must be >= 1");
@@ -821,7 +826,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
   const int ztype = mixed ? 1 : 0;
   const size_t zsz = W.zsz;
   int64_t launches = 0;
-  std::vector<int32_t> its(nrhs, 0), done(nrhs, 0), kcols(nrhs, 0);
+  std::vector<int32_t> its(nrhs, 0), done(nrhs, 0), kcols(nrhs, 0), reported(nrhs, 0);
   std::vector<double> rel(nrhs, 1.0), estv(nrhs, 1.0), bn(nrhs, 0.0);
   DevBuf<int32_t> dk(nrhs);
   DevBuf<double> beta(nrhs);
@@ -1010,6 +1015,40 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
         act[r] = 1;
         any = true;
       }
+    }
+    // continuous batching: report finished columns, take new right-hand sides into free ones
+    while (hook && !P.weighted) {
+      std::vector<int> fin;
+      for (int r = 0; r < nrhs; ++r)
+        if (done[r] && !reported[r]) {
+          reported[r] = 1;
+          fin.push_back(r);
+        }
+      const std::vector<int> filled = hook->at_restart(W.x.p, W.b.p, fin, its, rel, estv);
+      if (filled.empty()) break;
+      std::vector<int32_t> mask(nrhs, 0);
+      for (int r : filled) mask[r] = 1;
+      DevBuf<int32_t> dmask(nrhs);
+      MX_CUDA(cudaMemcpyAsync(dmask.p, mask.data(), nrhs * 4, cudaMemcpyHostToDevice, s));
+      MX_LAUNCH(k_zero_cols<<<gv, 256, 0, s>>>(nv, nrhs, dmask.p, W.x.p));
+      MX_CHECK_LAUNCH();
+      true_residual(P, W, s);  // new columns: r = b
+      MX_LAUNCH(k_restart<<<1, 32, 0, s>>>(W.nblk, nrhs, m, W.npart.p, W.bnorm.p, -1.0, W.active.p, beta.p, W.g.p));
+      MX_CHECK_LAUNCH();
+      launches += 4;
+      MX_CUDA(cudaMemcpyAsync(W.h_small, beta.p, nrhs * 8, cudaMemcpyDeviceToHost, s));
+      MX_CUDA(cudaStreamSynchronize(s));
+      for (int r : filled) {
+        bn[r] = W.h_small[r];
+        its[r] = 0;
+        reported[r] = 0;
+        estv[r] = bn[r] > 0 ? 1.0 : 0.0;
+        rel[r] = estv[r];
+        done[r] = bn[r] > 0 ? 0 : 1;  // a zero right-hand side is done at once (x = 0)
+        act[r] = !done[r];
+        any = any || act[r];
+      }
+      MX_CUDA(cudaMemcpyAsync(W.bnorm.p, bn.data(), nrhs * 8, cudaMemcpyHostToDevice, s));
     }
     if (!any) break;
     ++restarts;

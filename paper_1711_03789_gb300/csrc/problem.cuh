@@ -245,8 +245,20 @@ void spmv(const Problem& P, double xi, const void* x, int xtype, double2* y, int
 // complex double-float (vtype 3, float4 {re_hi, im_hi, re_lo, im_lo})
 void precond_apply(Problem& P, const void* v, void* z, int ztype, int nrhs, int levels, double2* zc = nullptr,
                    int vtype = 0);
+// Restart-boundary hook of gmres_solve (continuous batching in the server). At every restart
+// boundary the solver reports the columns that finished since the last call (their x in x_dev,
+// internal [n][nrhs] layout, is final; its / rel / est hold their statistics); the hook returns
+// the columns into which it wrote new right-hand sides (b_dev, same layout), which then start
+// from x = 0 with their own ||b|| and iteration count. Columns keep their own arithmetic, so a
+// right-hand side gets the same iterates whichever columns it shares the batch with.
+struct SlotHook {
+  virtual ~SlotHook() = default;
+  virtual std::vector<int> at_restart(const double2* x_dev, double2* b_dev, const std::vector<int>& finished,
+                                      const std::vector<int32_t>& its, const std::vector<double>& rel,
+                                      const std::vector<double>& est) = 0;
+};
 int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, int restart,
-                int max_it, mx_rhs_stats* stats);
+                int max_it, mx_rhs_stats* stats, SlotHook* hook = nullptr);
 void free_workspace(Problem& P);
 
 // ---- krylov_df.cu: double-float Krylov kernels of the mixed form --------------------

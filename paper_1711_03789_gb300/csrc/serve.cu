@@ -4,9 +4,15 @@
 // - Requests are queued on submit. A pool of worker threads, each with its own CUDA stream,
 //   takes work: the oldest pending request and every other pending request with the same
 //   operator (mesh, k, xi_prob, xi_prec, subdomains, coarse mesh, precision) and the same
-//   solver settings are solved together as one batch of right-hand sides (at most 32).
-//   Requests that arrive while batches run join the next batch of their operator, and
-//   batches of different operators run concurrently on the workers' streams.
+//   solver settings are solved together as one batch of right-hand sides, in a block of
+//   slots with room to spare (twice the starting right-hand sides rounded up to 8, at most 32).
+// - Continuous batching: at every GMRES restart boundary of a running batch its worker
+//   retires the requests whose right-hand sides have all finished (results returned at once)
+//   and admits pending requests of the same operator and settings into free slots (a
+//   contiguous run per request); their right-hand sides start from x = 0 in the same solve.
+//   Each slot keeps its own arithmetic, so a request's result does not depend on the requests
+//   it shares the batch with. Batches of different operators run concurrently on the workers'
+//   streams.
 // - Factorisations are cached by the preconditioner key (everything but xi_prob: the
 //   preconditioner is built from A_{xi_prec} only, Sec. 6.2), so requests that differ in
 //   xi_prob share factors; the operator A_{xi_prob} is set per batch.
@@ -37,6 +43,22 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// columns [c0, c0 + nr) of a solver block [n][cap] <-> a user block [nr][n]
+__global__ void k_put_cols(int64_t n, int cap, int c0, int nr, const double2* user, double2* in) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nr; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nr);
+    const int64_t i = t / nr;
+    in[i * cap + c0 + r] = user[(int64_t)r * n + i];
+  }
+}
+__global__ void k_get_cols(int64_t n, int cap, int c0, int nr, const double2* in, double2* user) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nr; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % nr);
+    const int64_t i = t / nr;
+    user[(int64_t)r * n + i] = in[i * cap + c0 + r];
+  }
+}
+
 struct Key {
   int n, core, overlap, coarse, precision, bc, prec;
   double k, xi_prec;
@@ -58,6 +80,7 @@ struct Req {
   int rc = MX_OK;
   std::string err;
   bool done = false, taken = false;
+  int slot0 = -1, left = 0;  // first slot in the running batch, right-hand sides not finished
   Clock::time_point t_submit, t_start, t_done;
 };
 
@@ -85,7 +108,7 @@ struct Server {
   int64_t cached_bytes = 0;
   int device = 0;
   // statistics
-  int64_t batches = 0, factorisations = 0, evictions = 0, completed = 0;
+  int64_t batches = 0, factorisations = 0, evictions = 0, completed = 0, joined = 0;
 
   static bool same_batch(const Req& a, const Req& b) {
     return a.key == b.key && a.xi_prob == b.xi_prob && a.tol == b.tol && a.restart == b.restart &&
@@ -111,6 +134,111 @@ struct Server {
     }
     return true;
   }
+
+  // Restart-boundary hook of a running batch: records finished right-hand sides, returns the
+  // requests whose right-hand sides have all finished, and admits pending requests of the same
+  // operator and settings into free runs of slots.
+  struct BatchHook : SlotHook {
+    Server& S;
+    Problem& P;
+    cudaStream_t s;
+    int64_t n;
+    int cap;
+    const Req tmpl;  // the settings every request of the batch shares
+    double2* tmp;    // [32][n] user-layout scratch
+    std::vector<Req*>& live;
+    std::vector<Req*> owner;  // per slot
+
+    BatchHook(Server& S_, Problem& P_, cudaStream_t s_, int64_t n_, int cap_, const Req& t, double2* tmp_,
+              std::vector<Req*>& live_)
+        : S(S_), P(P_), s(s_), n(n_), cap(cap_), tmpl(copy_settings(t)), tmp(tmp_), live(live_), owner(cap_, nullptr) {}
+
+    static Req copy_settings(const Req& r) {
+      Req t;
+      t.key = r.key;
+      t.xi_prob = r.xi_prob;
+      t.tol = r.tol;
+      t.restart = r.restart;
+      t.max_it = r.max_it;
+      return t;
+    }
+
+    void own(Req* r, int c0) {
+      r->slot0 = c0;
+      r->left = r->nrhs;
+      r->stats.assign(r->nrhs, mx_rhs_stats{});
+      for (int c = c0; c < c0 + r->nrhs; ++c) owner[c] = r;
+    }
+
+    std::vector<int> at_restart(const double2* x_dev, double2* b_dev, const std::vector<int>& finished,
+                                const std::vector<int32_t>& its, const std::vector<double>& rel,
+                                const std::vector<double>& est) override {
+      std::vector<Req*> complete;
+      for (int c : finished) {
+        Req* r = owner[c];
+        if (!r) continue;  // a free slot
+        mx_rhs_stats& st = r->stats[c - r->slot0];
+        st.iterations = its[c];
+        st.converged = rel[c] <= tmpl.tol ? 1 : 0;
+        st.rel_residual = rel[c];
+        st.rel_estimate = est[c];
+        if (--r->left == 0) complete.push_back(r);
+      }
+      for (Req* r : complete) {  // results out, slots free
+        MX_LAUNCH(k_get_cols<<<grid_for(n * r->nrhs, 256), 256, 0, s>>>(n, cap, r->slot0, r->nrhs, x_dev, tmp));
+        MX_CHECK_LAUNCH();
+        r->x.resize((size_t)n * r->nrhs);
+        MX_CUDA(cudaMemcpyAsync(r->x.data(), tmp, sizeof(double2) * n * r->nrhs, cudaMemcpyDeviceToHost, s));
+        MX_CUDA(cudaStreamSynchronize(s));
+        for (int c = r->slot0; c < r->slot0 + r->nrhs; ++c) owner[c] = nullptr;
+      }
+      std::vector<Req*> adm;
+      {
+        std::lock_guard<std::mutex> g(S.mu);
+        const auto now = Clock::now();
+        for (Req* r : complete) {
+          // the worker lets go of the request before it is marked done: a poll may free it
+          live.erase(std::remove(live.begin(), live.end(), r), live.end());
+          r->rc = std::all_of(r->stats.begin(), r->stats.end(), [](const mx_rhs_stats& x) { return x.converged != 0; })
+                      ? MX_OK
+                      : MX_ENOCONV;
+          r->t_done = now;
+          r->done = true;
+          ++S.completed;
+        }
+        for (int64_t id : S.pending) {
+          if (S.stop) break;  // the server is shutting down: pending requests are dropped
+          Req* q = S.reqs[id].get();
+          if (q->taken || !same_batch(*q, tmpl)) continue;
+          int run = 0, start = -1;
+          for (int c = 0; c < cap && start < 0; ++c) {
+            run = owner[c] ? 0 : run + 1;
+            if (run == q->nrhs) start = c - q->nrhs + 1;
+          }
+          if (start < 0) continue;
+          own(q, start);
+          q->taken = true;
+          q->t_start = now;
+          ++S.joined;
+          adm.push_back(q);
+        }
+        if (!adm.empty())
+          S.pending.erase(std::remove_if(S.pending.begin(), S.pending.end(),
+                                         [&](int64_t id) { return S.reqs[id]->taken; }),
+                          S.pending.end());
+      }
+      if (!complete.empty()) S.cv_done.notify_all();
+      std::vector<int> filled;
+      for (Req* q : adm) {
+        live.push_back(q);
+        load_vector(P, q->nrhs, q->nbumps, q->centres.data(), q->pol.data(), q->width, tmp);
+        MX_LAUNCH(k_put_cols<<<grid_for(n * q->nrhs, 256), 256, 0, s>>>(n, cap, q->slot0, q->nrhs, tmp, b_dev));
+        MX_CHECK_LAUNCH();
+        for (int c = q->slot0; c < q->slot0 + q->nrhs; ++c) filled.push_back(c);
+      }
+      return filled;
+    }
+  };
 
   void work(int wid) {
     cudaSetDevice(device);
@@ -162,14 +290,19 @@ struct Server {
       int64_t charged = 0;  // bytes admitted into the budget for a new factorisation
       int nrhs = 0;
       for (Req* r : batch) nrhs += r->nrhs;
+      // slots of the batch: room for as many right-hand sides again, rounded up to 8, at most 32
+      const int cap = std::min(32, std::max(nrhs, ((2 * nrhs + 7) / 8) * 8));
+      std::vector<Req*> live(batch.begin(), batch.end());  // grows with requests admitted on the way
+      int64_t n_batch = 0;
       const auto t_start = Clock::now();
+      for (Req* r : batch) r->t_start = t_start;
       try {
         if (create) {
           std::unique_ptr<Problem> P(create_problem(key.n, key.k, batch[0]->xi_prob, key.xi_prec, key.core,
                                                     key.overlap, key.coarse, key.precision, s, key.bc));
           P->prec_kind = key.prec;
           const int m = batch[0]->restart > 0 ? std::min(batch[0]->restart, batch[0]->max_it) : batch[0]->max_it;
-          const int64_t need = local_factor_bytes(*P) + workspace_bytes(key, P->fine.n_dof, nrhs, m);
+          const int64_t need = local_factor_bytes(*P) + workspace_bytes(key, P->fine.n_dof, cap, m);
           // admission: memory budget (after evictions) and the device's free memory
           MX_REQUIRE(need <= budget, MX_ENOMEM,
                      "request needs " + std::to_string(need) + " bytes, more than the whole budget");
@@ -204,27 +337,19 @@ struct Server {
         P.stream = s;
         P.xi_prob = batch[0]->xi_prob;
         const int64_t n = P.fine.n_dof;
-        DevBuf<double2> f((size_t)n * nrhs), bi((size_t)n * nrhs), xi((size_t)n * nrhs);
-        // load vectors of every request, stacked as one block of right-hand sides
+        n_batch = n;
+        DevBuf<double2> f((size_t)n * cap), bi((size_t)n * cap), xi((size_t)n * cap), tmp((size_t)n * 32);
+        MX_CUDA(cudaMemsetAsync(f.p, 0, f.bytes(), s));  // free slots: zero right-hand sides
+        // load vectors of the starting requests, stacked as one block of right-hand sides
+        BatchHook hook(*this, P, s, n, cap, *batch[0], tmp.p, live);
         int r0 = 0;
         for (Req* r : batch) {
           load_vector(P, r->nrhs, r->nbumps, r->centres.data(), r->pol.data(), r->width, f.p + (int64_t)r0 * n);
+          hook.own(r, r0);
           r0 += r->nrhs;
         }
-        transpose_to_internal(f.p, bi.p, n, nrhs, s);
-        std::vector<mx_rhs_stats> st(nrhs);
-        const int c = gmres_solve(P, bi.p, xi.p, nrhs, batch[0]->tol, batch[0]->restart, batch[0]->max_it, st.data());
-        transpose_to_user(xi.p, f.p, n, nrhs, s);
-        r0 = 0;
-        for (Req* r : batch) {
-          r->x.resize((size_t)n * r->nrhs);
-          MX_CUDA(cudaMemcpyAsync(r->x.data(), f.p + (int64_t)r0 * n, sizeof(double2) * n * r->nrhs,
-                                  cudaMemcpyDeviceToHost, s));
-          r->stats.assign(st.begin() + r0, st.begin() + r0 + r->nrhs);
-          r0 += r->nrhs;
-        }
-        MX_CUDA(cudaStreamSynchronize(s));
-        if (c != MX_OK) rc = c;
+        transpose_to_internal(f.p, bi.p, n, cap, s);
+        (void)gmres_solve(P, bi.p, xi.p, cap, batch[0]->tol, batch[0]->restart, batch[0]->max_it, nullptr, &hook);
       } catch (const Error& e) {
         rc = e.code;
         err = e.what();
@@ -241,14 +366,14 @@ struct Server {
         entry->last_used = ++clock;
       }
       const auto t_done = Clock::now();
-      for (Req* r : batch) {
-        r->rc = (rc == MX_ENOCONV) ? (std::all_of(r->stats.begin(), r->stats.end(),
-                                                  [](const mx_rhs_stats& x) { return x.converged != 0; })
-                                          ? MX_OK
-                                          : MX_ENOCONV)
-                                   : rc;
+      for (Req* r : live) {  // requests no restart boundary completed
+        if (r->done) continue;
+        if (rc == MX_OK) {  // only when every right-hand side of the batch was zero: x = 0
+          r->x.assign((size_t)r->nrhs * n_batch, double2{0, 0});
+          r->stats.assign(r->nrhs, mx_rhs_stats{0, 1, 0.0, 0.0});
+        }
+        r->rc = rc;
         r->err = err;
-        r->t_start = t_start;
         r->t_done = t_done;
         r->done = true;
         ++completed;
@@ -373,6 +498,7 @@ MX_API int mx_server_stats(mx_server sv, mx_server_info* out) {
   out->cached_bytes = S->cached_bytes;
   out->cached_operators = (int32_t)S->cache.size();
   out->pending = (int32_t)S->pending.size();
+  out->joined = S->joined;
   return MX_OK;
 }
 

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import inputs
+from parity import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +42,7 @@ def test_same_result_alone_and_in_the_mix():
         for tk, nr in zip(tickets, [3, 2, 1, 4, 5]):
             out[tk] = mx.mx_server_poll(s, tk, _n_dof(10), nr)
         x_mix = out[tickets[1]][0]
-        err = np.linalg.norm(x_mix - x_alone) / np.linalg.norm(x_alone)
-        assert err <= 1e-7, err
+        assert_close(x_mix, x_alone, 1e-7, what="request in the mix against alone")
         info = mx.mx_server_stats(s)
         assert info["completed"] == 6 and info["pending"] == 0
         # three preconditioner keys: (k=6, xi=6, one level), (k=4, xi=4), (k=6, xi=6, coarse 5)
@@ -80,5 +80,45 @@ def test_request_too_large_for_budget_fails_cleanly():
         with pytest.raises(mx.MxError) as e:
             mx.mx_server_poll(s, t, _n_dof(10), 1)
         assert e.value.code == mx.MX_ENOMEM
+    finally:
+        mx.mx_server_destroy(s)
+
+
+def _mixed_req(s, seed, nrhs, n=20, k=10.0):
+    c, p = inputs.bump_batch(seed, nrhs)
+    return mx.mx_server_submit(s, n, k, k * k, k * k, c, p, core_cells=5, overlap_cells=1, coarse_cells=4,
+                               precision=mx.MX_MIXED, tol=1e-11, restart=10, max_it=600)
+
+
+def test_request_joins_a_running_batch_with_the_same_result():
+    """Continuous batching in the mixed form: a request submitted while a batch of its operator
+    is running is admitted into the batch's free slots at the next restart boundary (one
+    worker, so it cannot start a batch of its own), and its solution equals the one it gets
+    alone, element by element (both to 1e-11; each slot keeps its own arithmetic, so only the
+    rounding of the other slots' presence differs)."""
+    import time
+    n = 20
+    nd = 3 * n * (n - 1) ** 2 + 3 * n * n * (n - 1) + n ** 3
+    s = mx.mx_server_create(8 << 30, workers=1)
+    try:
+        x_alone, st_alone, _, rc = mx.mx_server_poll(s, _mixed_req(s, 31, 3), nd, 3)
+        assert rc == mx.MX_OK and all(v["converged"] for v in st_alone)
+        # a long batch first (GMRES(10) to 1e-11 on its operator), then the same request again
+        t_long = _mixed_req(s, 32, 2)
+        t0 = time.perf_counter()
+        while mx.mx_server_stats(s)["pending"] and time.perf_counter() - t0 < 30:
+            time.sleep(0.001)
+        t_join = _mixed_req(s, 31, 3)
+        x_mix, st_mix, tm, rc = mx.mx_server_poll(s, t_join, nd, 3)
+        _, st_long, tm_long, rc_long = mx.mx_server_poll(s, t_long, nd, 2)
+        info = mx.mx_server_stats(s)
+        assert rc == mx.MX_OK and all(v["converged"] for v in st_mix)
+        assert info["joined"] >= 1 and info["batches"] == 2, info  # the first batch, then the one it joined
+        # admitted at a restart boundary of the long batch, not after it
+        print("queue", tm["queue_ms"], "ms; long batch", tm_long["latency_ms"], "ms")
+        assert tm["queue_ms"] < 0.5 * tm_long["latency_ms"], (tm, tm_long)
+        assert_close(x_mix, x_alone, 1e-8, what="request joined into a running batch against alone")
+        for a, b in zip(st_mix, st_alone):
+            assert abs(a["iterations"] - b["iterations"]) <= 1, (st_mix, st_alone)
     finally:
         mx.mx_server_destroy(s)
