@@ -552,6 +552,13 @@ def cpu_baseline_allcore(W, iterations, single, budget_s=12.0):
 
 
 def run_serving(args):
+    """The serving mix as its own benchmark line (bench.py --serving); see serving_mix."""
+    line = serving_mix(args, args.requests, [float(v) for v in args.loads.split(",") if v.strip()],
+                       int(args.budget_gb * 2 ** 30) if args.budget_gb else None)
+    print(json.dumps(line))
+
+
+def serving_mix(args, nreq, loads, budget=None):
     """Serving mix: requests with k in {10, 15, 20, 25} (2k cells per side, 5^3-cell
     subdomains + 1-cell overlap), xi_prec = k, xi_prob in {0, k, k^2/10}, 1..32 seeded
     Gaussian-bump right-hand sides each, through mx_server_*. The requests use the impedance
@@ -570,9 +577,9 @@ def run_serving(args):
 
     torch.cuda.set_device(0)
     mx.use_torch_allocator(0)
+    torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
     rng = np.random.default_rng(4)
-    nreq = args.requests
 
     def draw(i):
         k = float(rng.choice([10, 15, 20, 25]))
@@ -581,8 +588,7 @@ def run_serving(args):
         c, p = inputs.bump_batch(10_000 + i, nrhs)
         return dict(n=int(2 * k), k=k, xp=xp, nrhs=nrhs, c=c, p=p)
 
-    budget = int(args.budget_gb * 2 ** 30) if args.budget_gb else int(0.8 * free)
-    loads = [float(v) for v in args.loads.split(",") if v.strip()]
+    budget = budget or int(0.8 * free)
     if not loads or any(v <= 0 for v in loads):
         raise SystemExit("--loads: comma-separated positive fractions of the closed-loop capacity")
 
@@ -603,7 +609,7 @@ def run_serving(args):
                 while time.perf_counter() < tnext:
                     time.sleep(0.0005)
             tickets.append(mx.mx_server_submit(s, r["n"], r["k"], r["xp"], r["k"], r["c"], r["p"], width=0.1,
-                                               coarse_cells=r["n"] // 5, tol=1e-6, restart=100,
+                                               coarse_cells=r["n"] // 5, tol=1e-6, restart=args.serve_restart,
                                                max_it=args.serve_max_it, bc=mx.MX_BC_IMPEDANCE,
                                                prec_kind=mx.MX_PREC_ADEF1))
         lat, conv, rhs = [], 0, 0
@@ -617,7 +623,8 @@ def run_serving(args):
         info = mx.mx_server_stats(s)
         return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)), wall_s=wall,
                     requests_per_s=len(reqs) / wall, rhs_per_s=rhs / wall, converged_rhs=conv, rhs=rhs,
-                    batches=info["batches"], factorisations=info["factorisations"], evictions=info["evictions"])
+                    batches=info["batches"], factorisations=info["factorisations"], evictions=info["evictions"],
+                    joined=info.get("joined", 0))
 
     reqs = [draw(i) for i in range(nreq)]
     closed = run(reqs, 0.0)
@@ -630,13 +637,13 @@ def run_serving(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c64 factors / f64 Krylov",
             "data": "synthetic (seeded request mix and Gaussian-bump right-hand sides)",
             "config": {"workload": "serving_mix", "requests": nreq, "workers": args.workers,
-                       "max_it": args.serve_max_it, "restart": 100, "tol": 1e-6, "boundary": "impedance",
+                       "max_it": args.serve_max_it, "restart": args.serve_restart, "tol": 1e-6, "boundary": "impedance",
                        "preconditioner": "ADEF1-ImpRAS", "coarse_cells": "n / 5", "budget_bytes": budget,
                        "loads": loads},
             "closed_loop": closed}
     for load, res in runs.items():
         line[f"poisson_{load:g}x"] = res
-    print(json.dumps(line))
+    return line
 
 
 SOLUTION_FIXTURE = os.path.join(ROOT, "tests", "golden", "solution60_k30.txt")
@@ -750,10 +757,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the plain-FP64 and xi-variant legs that follow the timed steps")
+    ap.add_argument("--no-serving-leg", dest="serving_leg", action="store_false",
+                    help="skip the bounded serving leg (64 requests) that follows the timed steps")
+    ap.add_argument("--serving-leg-requests", type=int, default=64)
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead of the solve benchmark")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--workers", type=int, default=3)
     ap.add_argument("--serve-max-it", type=int, default=200)
+    ap.add_argument("--serve-restart", type=int, default=30,
+                    help="serving: GMRES restart length of the requests (their batches admit new requests at "
+                         "restart boundaries)")
     ap.add_argument("--loads", default="0.8",
                     help="serving: offered loads of the Poisson runs as fractions of the closed-loop capacity")
     ap.add_argument("--budget-gb", type=float, default=None,
@@ -878,6 +891,12 @@ def main():
     err = error_vs_oracle(W, args, r["x_sample"], r["stats"], rank)
     if err is not None:
         line["error_vs_oracle"] = err
+    if world == 1 and args.serving_leg and args.variants:
+        # p50 / p99 latency and solves per second of the serving mix (continuous batching),
+        # a bounded run beside the solve benchmark: closed loop for capacity, then Poisson
+        # arrivals at 0.8 x that capacity
+        sv = serving_mix(args, args.serving_leg_requests, [0.8])
+        line["serving"] = {kk: sv[kk] for kk in ("config", "closed_loop", "poisson_0.8x")}
     if world == 1 and not args.no_cpu_baseline and args.bc == "pec":
         # a failure of the CPU baselines is recorded in their keys, not allowed to drop the line
         try:

@@ -161,12 +161,16 @@ def test_default_solve_benchmark_line(fakes, monkeypatch):
     assert line["plain_fp64"]["value"] == pytest.approx(0.6) and line["mixed_speedup"] == pytest.approx(2.0)
     assert set(line["xi_variants"]) == {"xi_k1.5", "config5_literal"}
     assert line["xi_variants"]["config5_literal"]["max_it"] == 400
+    # the bounded serving leg: closed loop and Poisson arrivals at 0.8 x capacity
+    sv = line["serving"]
+    assert sv["config"]["requests"] == 64 and sv["config"]["restart"] == 30
+    assert sv["closed_loop"]["p99_ms"] >= sv["closed_loop"]["p50_ms"] > 0 and "p99_ms" in sv["poisson_0.8x"]
 
 
 def test_no_variants_runs_only_the_timed_workload(fakes, monkeypatch):
     line = _run(monkeypatch, ["--steps", "2", "--warmup", "3", "--no-cpu-baseline", "--no-variants"])
     assert sum(1 for e in FakeProblem.log if e[0] == "Problem") == 7
-    assert "plain_fp64" not in line and "xi_variants" not in line
+    assert "plain_fp64" not in line and "xi_variants" not in line and "serving" not in line
 
 
 def test_autotune_path_searches_then_hits_the_cache(fakes, monkeypatch, tmp_path):
