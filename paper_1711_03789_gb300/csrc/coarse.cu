@@ -129,6 +129,52 @@ __global__ void k_coarse_restrict(int64_t nc, int64_t n, int nrhs, const int32_t
   }
 }
 
+// R^0 v with one block per coarse row (grid-stride): thread (g, q) sums the entries
+// rowptr[p] + g, + G, ... of right-hand side q (G = blockDim / nrhs groups), and the G
+// partial sums are added in group order (deterministic). A coarse row has several hundred
+// entries, so its gathers of v are spread over the whole block instead of one thread.
+template <typename T2, typename AT>
+__global__ void __launch_bounds__(256) k_coarse_restrict_rows(int64_t nc, int nrhs, const int32_t* __restrict__ rowptr,
+                                                              const int32_t* __restrict__ col,
+                                                              const AT* __restrict__ val, const void* v, int vtype,
+                                                              T2* r0) {
+  using A2 = typename cplx<AT>::type;
+  __shared__ A2 part[256];
+  const int G = blockDim.x / nrhs;
+  const int q = threadIdx.x % nrhs, g = threadIdx.x / nrhs;
+  for (int64_t p = blockIdx.x; p < nc; p += gridDim.x) {
+    A2 acc = czero<A2>();
+    if (g < G)
+      for (int32_t e = rowptr[p] + g; e < rowptr[p + 1]; e += G) {
+        const int64_t idx = (int64_t)col[e] * nrhs + q;
+        A2 x;
+        if (vtype == 0) {
+          const double2 d = reinterpret_cast<const double2*>(v)[idx];
+          x = mk((AT)d.x, (AT)d.y);
+        } else if (vtype == 3) {
+          const float4 d = reinterpret_cast<const float4*>(v)[idx];
+          x = mk((AT)d.x, (AT)d.y);
+        } else {
+          const float2 d = reinterpret_cast<const float2*>(v)[idx];
+          x = mk((AT)d.x, (AT)d.y);
+        }
+        acc.x = fma(val[e], x.x, acc.x);
+        acc.y = fma(val[e], x.y, acc.y);
+      }
+    if (g < G) part[g * nrhs + q] = acc;
+    __syncthreads();
+    if (threadIdx.x < nrhs) {
+      A2 s = czero<A2>();
+      for (int gg = 0; gg < G; ++gg) {
+        s.x += part[gg * nrhs + threadIdx.x].x;
+        s.y += part[gg * nrhs + threadIdx.x].y;
+      }
+      r0[p * nrhs + threadIdx.x] = conv<T2>(make_double2(s.x, s.y));
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_to_f32v(int64_t n, const double* a, float* b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -381,12 +427,13 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
   float2* rin = dense ? rf + nc * nrhs : rf;
   {
     ProfScope ps(K_COARSE_RESTRICT, s, 1, rb, 4.0 * P.R0.nnz * nrhs);
+    const unsigned rows_grid = (unsigned)std::min<int64_t>(nc, 152LL * 8);
     if (mixed) {
-      MX_LAUNCH(k_coarse_restrict<float2, float><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
-          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, r0_valf(P), v, vtype, rin));
+      MX_LAUNCH(k_coarse_restrict_rows<float2, float><<<rows_grid, 256, 0, s>>>(
+          nc, nrhs, P.R0.rowptr.p, P.R0.col.p, r0_valf(P), v, vtype, rin));
     } else {
-      MX_LAUNCH(k_coarse_restrict<double2, double><<<grid_for(nc * nrhs, 256), 256, 0, s>>>(
-          nc, P.fine.n_dof, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, yc));
+      MX_LAUNCH(k_coarse_restrict_rows<double2, double><<<rows_grid, 256, 0, s>>>(
+          nc, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, yc));
     }
     MX_CHECK_LAUNCH();
   }

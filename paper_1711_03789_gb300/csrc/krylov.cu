@@ -126,6 +126,93 @@ __global__ void k_scatter(int64_t n, int nrhs, const int32_t* __restrict__ inv_p
   }
 }
 
+// The mixed form with an even number of right-hand sides: one thread per (DOF, pair of
+// right-hand sides) with 16-byte loads of the c64 local and coarse solutions. The first 8
+// inverse-map positions and the first 8 entries of the DOF's R^0 column are fetched before the
+// loads that depend on them, so those loads are in flight together (a DOF lies in at most 8
+// boxes when the overlap is below the core size; the loops continue past 8 otherwise). Same
+// order of summation as k_scatter.
+template <typename ZT>
+__global__ void k_scatter2(int64_t n, int nrhs, const int32_t* __restrict__ inv_ptr, const int32_t* __restrict__ inv_pos,
+                           const int32_t* __restrict__ own, const float4* __restrict__ loc,
+                           const int32_t* __restrict__ tptr, const int32_t* __restrict__ tcol,
+                           const float* __restrict__ tval, const float4* __restrict__ y0, int use_local,
+                           ZT* __restrict__ z, double2* __restrict__ zc) {
+  const int half = nrhs / 2;
+  const int64_t work = n * half;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r2 = (int)(t % half);
+    const int64_t i = t / half;
+    float4 acc = zero;  // (re, im) of right-hand sides 2 r2 and 2 r2 + 1
+    if (use_local && own) {
+      acc = loc[(int64_t)own[i] * half + r2];  // restricted: the owner's solution only
+    } else if (use_local) {
+      const int32_t q0 = inv_ptr[i], q1 = inv_ptr[i + 1];
+      int32_t pos[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) pos[k] = q0 + k < q1 ? inv_pos[q0 + k] : -1;
+      float4 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = pos[k] >= 0 ? loc[(int64_t)pos[k] * half + r2] : zero;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (pos[k] >= 0) {
+          acc.x += v[k].x;
+          acc.y += v[k].y;
+          acc.z += v[k].z;
+          acc.w += v[k].w;
+        }
+      for (int32_t q = q0 + 8; q < q1; ++q) {
+        const int32_t p = inv_pos[q];
+        if (p < 0) continue;
+        const float4 u = loc[(int64_t)p * half + r2];
+        acc.x += u.x;
+        acc.y += u.y;
+        acc.z += u.z;
+        acc.w += u.w;
+      }
+    }
+    if (tptr) {
+      const int32_t e0 = tptr[i], e1 = tptr[i + 1];
+      int32_t c[8];
+      float w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        c[k] = e0 + k < e1 ? tcol[e0 + k] : -1;
+        w[k] = e0 + k < e1 ? tval[e0 + k] : 0.f;
+      }
+      float4 y[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) y[k] = c[k] >= 0 ? y0[(int64_t)c[k] * half + r2] : zero;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (c[k] >= 0) {
+          acc.x = fmaf(w[k], y[k].x, acc.x);
+          acc.y = fmaf(w[k], y[k].y, acc.y);
+          acc.z = fmaf(w[k], y[k].z, acc.z);
+          acc.w = fmaf(w[k], y[k].w, acc.w);
+        }
+      for (int32_t e = e0 + 8; e < e1; ++e) {
+        const float4 u = y0[(int64_t)tcol[e] * half + r2];
+        const float wv = tval[e];
+        acc.x = fmaf(wv, u.x, acc.x);
+        acc.y = fmaf(wv, u.y, acc.y);
+        acc.z = fmaf(wv, u.z, acc.z);
+        acc.w = fmaf(wv, u.w, acc.w);
+      }
+    }
+    const int64_t o = i * nrhs + 2 * r2;
+    const ZT za = cvt2<ZT>(make_float2(acc.x, acc.y)), zb = cvt2<ZT>(make_float2(acc.z, acc.w));
+    z[o] = za;
+    z[o + 1] = zb;
+    if (zc) {
+      zc[o] = to_c128(za);
+      zc[o + 1] = to_c128(zb);
+    }
+  }
+}
+
 __global__ void k_to_f32(int64_t n, const double* a, float* b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -242,8 +329,23 @@ static void scatter(Problem& P, Workspace& W, void* z, int ztype, int nrhs, bool
       MX_LAUNCH(k_to_f32<<<grid_for(P.R0T.nnz, 256), 256, 0, s>>>(P.R0T.nnz, P.R0T.val.p, P.R0T_valf.p));
       MX_CHECK_LAUNCH();
     }
-    if (ztype == 0) MX_SCATTER(float2, float2, double2, float, P.R0T_valf.p);
-    else MX_SCATTER(float2, float2, float2, float, P.R0T_valf.p);
+    if (nrhs % 2 == 0) {
+      const unsigned grid2 = grid_for(P.fine.n_dof * (nrhs / 2), 256, 152LL * 32);
+      const float4* l4 = reinterpret_cast<const float4*>(W.loc.p);
+      const float4* y4 = reinterpret_cast<const float4*>(W.yc.p);
+      if (ztype == 0)
+        MX_LAUNCH(k_scatter2<double2><<<grid2, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p, own, l4, tp,
+                                                            P.R0T.col.p, P.R0T_valf.p, y4, local ? 1 : 0,
+                                                            (double2*)z, zc));
+      else
+        MX_LAUNCH(k_scatter2<float2><<<grid2, 256, 0, s>>>(P.fine.n_dof, nrhs, P.inv_ptr.p, P.inv_pos.p, own, l4, tp,
+                                                           P.R0T.col.p, P.R0T_valf.p, y4, local ? 1 : 0,
+                                                           (float2*)z, zc));
+    } else if (ztype == 0) {
+      MX_SCATTER(float2, float2, double2, float, P.R0T_valf.p);
+    } else {
+      MX_SCATTER(float2, float2, float2, float, P.R0T_valf.p);
+    }
   } else {
     if (ztype == 0) MX_SCATTER(double2, double2, double2, double, P.R0T.val.p);
     else MX_SCATTER(double2, double2, float2, double, P.R0T.val.p);
