@@ -30,6 +30,7 @@ from . import _lib as L
 # knob name -> mx_set_tuning key; the order is the order of the coordinate search
 KNOBS = {
     "lu_tensor": L.MX_TUNE_LU_TENSOR,
+    "lu_grid": L.MX_TUNE_LU_GRID,
     "coarse_inverse": L.MX_TUNE_COARSE_INVERSE,
     "local_tensor": L.MX_TUNE_LOCAL_TENSOR,
     "local_rhs_group": L.MX_TUNE_LOCAL_RHS_GROUP,
@@ -37,9 +38,10 @@ KNOBS = {
 }
 
 # library defaults, written out so that a cached choice never depends on "0 = default"
-DEFAULTS = {"lu_tensor": 0, "coarse_inverse": 1, "local_tensor": 1, "local_rhs_group": 16, "coarse_blocks": 0}
+DEFAULTS = {"lu_tensor": 0, "lu_grid": 0, "coarse_inverse": 1, "local_tensor": 1, "local_rhs_group": 16,
+            "coarse_blocks": 0}
 
-FORMAT = 1
+FORMAT = 2
 
 
 def candidates(info, cfg, name, allow_reduced=False):
@@ -50,6 +52,10 @@ def candidates(info, cfg, name, allow_reduced=False):
     if name == "lu_tensor":
         # 1 (a single TF32 product) changes the factors' accuracy: only on request
         return ([0, 3, 4, 1] if allow_reduced else [0, 3, 4]) if mixed else []
+    if name == "lu_grid":
+        # CTAs of the persistent LU (0: one per subdomain); only with the persistent LU
+        persistent = cfg.get("lu_tensor", 0) in (0, 2)
+        return [0, 152, 114, 76] if (mixed and persistent and info["n_sub"] > 152) else []
     if name == "coarse_inverse":
         return [1, 0] if (mixed and coarse) else []
     if name == "local_tensor":

@@ -28,6 +28,10 @@ def test_candidates_per_problem_kind():
     assert _applicable(mixed_coarse) == {"lu_tensor", "coarse_inverse", "local_tensor", "local_rhs_group"}
     # the cooperative sweep only runs when the explicit inverse is off
     assert "coarse_blocks" in _applicable(mixed_coarse, {"coarse_inverse": 0})
+    # the persistent LU's grid: only for the persistent LU and more subdomains than SMs
+    many = dict(mixed_coarse, n_sub=1728)
+    assert "lu_grid" in _applicable(many) and "lu_grid" not in _applicable(many, {"lu_tensor": 4})
+    assert at.candidates(many, at.DEFAULTS, "lu_grid")[0] == 0
     # the single-TF32 LU update changes the factors' accuracy: only on request
     assert 1 not in at.candidates(mixed_coarse, at.DEFAULTS, "lu_tensor")
     assert 1 in at.candidates(mixed_coarse, at.DEFAULTS, "lu_tensor", allow_reduced=True)
