@@ -41,6 +41,199 @@ __global__ void k_to_c64(int64_t n, const double2* a, float2* b) {
     b[i] = to_c64(a[i]);
 }
 
+// Band LU without pivoting of the single coarse matrix A^0 (Eq. 3.3, l = 0) in one cooperative
+// launch instead of three launches per block column. Per block column [k0, k0 + kb): block 0
+// factors the diagonal block in shared memory; after a grid-wide barrier every block takes
+// rows of L21 = A21 U11^{-1} and columns of U12 = L11^{-1} A12 (one thread each, the 32
+// unknowns in registers); after a second barrier the blocks share the 64 x 64 tiles of the
+// trailing window A22 -= L21 U12; a third barrier closes the step. The arithmetic of every
+// entry is that of the batched per-step kernels (same operations in the same order).
+// LU of the kb x kb diagonal block at (k0, k0) by one block in shared memory (no pivoting),
+// written back to the band storage; a zero or non-finite pivot counts in *status.
+template <typename T2>
+__device__ void coarse_diag_block(T2 (*s)[LU_NB + 1], T2* A, int n, int b, int ld, int k0, int32_t* status) {
+  constexpr int NB = LU_NB;
+  const int tid = threadIdx.x;
+  const int kb = min(NB, n - k0);
+  for (int t = tid; t < NB * NB; t += blockDim.x) {
+    const int i = t % NB, j = t / NB;
+    T2 v = czero<T2>();
+    if (i < kb && j < kb && abs(i - j) <= b) v = A[bidx(0, ld, b, k0 + i, k0 + j)];
+    s[i][j] = v;
+  }
+  __syncthreads();
+  for (int k = 0; k < kb; ++k) {
+    const T2 piv = s[k][k];
+    const auto p2 = cabs2(piv);
+    if (tid == 0 && !(p2 > 0 && p2 < INFINITY)) atomicAdd(status, 1);
+    const T2 inv = crcp(piv);
+    __syncthreads();
+    for (int i = k + 1 + tid; i < kb; i += blockDim.x) s[i][k] = cmul(s[i][k], inv);
+    __syncthreads();
+    const int w = kb - k - 1;
+    for (int t = tid; t < w * w; t += blockDim.x) {
+      const int i = k + 1 + t % w, j = k + 1 + t / w;
+      T2 v = s[i][j];
+      cfms(v, s[i][k], s[k][j]);
+      s[i][j] = v;
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < kb * kb; t += blockDim.x) {
+    const int i = t % kb, j = t / kb;
+    if (abs(i - j) <= b) A[bidx(0, ld, b, k0 + i, k0 + j)] = s[i][j];
+  }
+  __syncthreads();
+}
+
+// Band LU without pivoting of the single coarse matrix A^0 (Eq. 3.3, l = 0) in one cooperative
+// launch instead of three launches per block column. Per block column [k0, k0 + kb): every
+// block takes rows of L21 = A21 U11^{-1} and columns of U12 = L11^{-1} A12 (one thread each,
+// the 32 unknowns in registers); after a grid-wide barrier the blocks share the 64 x 64 tiles
+// of the trailing window A22 -= L21 U12, and the next diagonal block -- which lies inside tile
+// (0, 0) only -- is factored by block 0 as soon as that tile is done, while the other blocks
+// are still updating (look-ahead); a second barrier closes the step. Every entry goes through
+// the operations of the batched per-step kernels in the same order.
+template <typename T2>
+__global__ void __launch_bounds__(256) k_coarse_lu_coop(int n, int b, int ld, T2* A, int32_t* status) {
+  constexpr int NB = LU_NB;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char csm[];
+  T2(*s)[NB + 1] = reinterpret_cast<T2(*)[NB + 1]>(csm);            // diagonal block
+  T2(*sl)[64 + 1] = reinterpret_cast<T2(*)[64 + 1]>(csm);           // update tiles (same space)
+  T2(*su)[64 + 1] = reinterpret_cast<T2(*)[64 + 1]>(csm + NB * 65 * sizeof(T2));
+  const int tid = threadIdx.x;
+  if (blockIdx.x == 0) coarse_diag_block<T2>(s, A, n, b, ld, 0, status);
+  grid.sync();
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    const int k1 = k0 + kb;
+    const int span = min(n, k1 + b) - k1;
+    if (span <= 0) break;  // the last block column (same decision in every block)
+    // 1. panels, spread over the grid
+    for (int t = tid; t < NB * NB; t += blockDim.x) {
+      const int i = t % NB, j = t / NB;
+      T2 v = czero<T2>();
+      if (i < kb && j < kb && abs(i - j) <= b) v = A[bidx(0, ld, b, k0 + i, k0 + j)];
+      s[i][j] = v;
+    }
+    __syncthreads();
+    for (int task = blockIdx.x * blockDim.x + tid; task < 2 * span; task += gridDim.x * blockDim.x) {
+      T2 x[NB];
+      if (task < span) {
+        const int i = k1 + task;
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+          x[k] = (k < kb && i - (k0 + k) <= b) ? A[bidx(0, ld, b, i, k0 + k)] : czero<T2>();
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {  // x U11 = a
+          if (k < kb) {
+            T2 v = x[k];
+#pragma unroll
+            for (int j = 0; j < k; ++j) cfms(v, x[j], s[j][k]);
+            x[k] = cmul(v, crcp(s[k][k]));
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+          if (k < kb && i - (k0 + k) <= b) A[bidx(0, ld, b, i, k0 + k)] = x[k];
+      } else {
+        const int j = k1 + task - span;
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+          x[k] = (k < kb && j - (k0 + k) <= b) ? A[bidx(0, ld, b, k0 + k, j)] : czero<T2>();
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {  // L11 y = a (unit lower)
+          if (k < kb) {
+            T2 v = x[k];
+#pragma unroll
+            for (int j2 = 0; j2 < k; ++j2) cfms(v, s[k][j2], x[j2]);
+            x[k] = v;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+          if (k < kb && j - (k0 + k) <= b) A[bidx(0, ld, b, k0 + k, j)] = x[k];
+      }
+    }
+    grid.sync();
+    // 2. trailing update, 64 x 64 tiles spread over the grid (256 threads, 4 x 4 outputs each);
+    // block 0 takes tile 0 first and then factors the next diagonal block
+    __syncthreads();
+    const int tiles = (span + 63) / 64;
+    for (int tile = blockIdx.x; tile < tiles * tiles; tile += gridDim.x) {
+      const int i0 = k1 + 64 * (tile % tiles), j0 = k1 + 64 * (tile / tiles);
+      if (i0 - (j0 + 63) <= b && j0 - (i0 + 63) <= b) {  // tile inside the band (uniform)
+        for (int t = tid; t < NB * 64; t += blockDim.x) {
+          const int r = t % 64, k = t / 64;
+          const int i = i0 + r, kk = k0 + k;
+          sl[k][r] = (k < kb && i < n && i - kk <= b) ? A[bidx(0, ld, b, i, kk)] : czero<T2>();
+          const int j = j0 + r;
+          su[k][r] = (k < kb && j < n && j - kk <= b) ? A[bidx(0, ld, b, kk, j)] : czero<T2>();
+        }
+        __syncthreads();
+        const int tx = tid % 16, ty = tid / 16;
+        T2 acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] = czero<T2>();
+        for (int k = 0; k < kb; ++k) {
+          T2 lv[4], uv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) lv[a] = sl[k][tx + 16 * a];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) uv[c] = su[k][ty + 16 * c];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cfma(acc[a][c], lv[a], uv[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = j0 + ty + 16 * c;
+          if (j >= n) continue;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = i0 + tx + 16 * a;
+            if (i >= n || abs(i - j) > b) continue;
+            T2* p = A + bidx(0, ld, b, i, j);
+            *p = csub(*p, acc[a][c]);
+          }
+        }
+        __syncthreads();  // the tile buffers are refilled by the next tile
+      }
+      if (tile == 0) coarse_diag_block<T2>(s, A, n, b, ld, k1, status);  // look-ahead (block 0)
+    }
+    grid.sync();
+  }
+}
+
+template <typename T2>
+static void coarse_lu_coop(T2* A, int n, int b, int ld, int32_t* status, cudaStream_t s) {
+  const size_t smem = std::max(sizeof(T2) * LU_NB * (LU_NB + 1), sizeof(T2) * 2 * LU_NB * 65);
+  static bool configured = false;
+  if (!configured) {
+    MX_CUDA(cudaFuncSetAttribute(k_coarse_lu_coop<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  int per_sm = 0;
+  MX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_lu_coop<T2>, 256, smem));
+  MX_REQUIRE(per_sm > 0, MX_ECUDA, "coarse LU kernel cannot be resident");
+  // one block per SM: the 64 x 64 tiles of a step (at most 256) and its 2 span panel tasks
+  const int grid = sm_count();
+  double flops = 0, bytes = 0;
+  for (int k0 = 0; k0 < n; k0 += LU_NB) {
+    const double kb = std::min(LU_NB, n - k0);
+    const double span = std::max(0, std::min(n, k0 + (int)kb + b) - (k0 + (int)kb));
+    flops += 8.0 * span * span * kb + 8.0 * span * kb * kb;
+    bytes += sizeof(T2) * (2.0 * span * span + 6.0 * span * kb);
+  }
+  void* args[] = {(void*)&n, (void*)&b, (void*)&ld, (void*)&A, (void*)&status};
+  ProfScope ps(K_COARSE_LU, s, 1, bytes, flops);
+  MX_LAUNCH(MX_CUDA(cudaLaunchCooperativeKernel((void*)k_coarse_lu_coop<T2>, grid, 256, args, smem, s)));
+}
+
 void factor_coarse(Problem& P) {
   if (!P.coarse_m) return;
   cudaStream_t s = P.stream;
@@ -77,8 +270,7 @@ void factor_coarse(Problem& P) {
     MX_CHECK_LAUNCH();
     MX_CUDA(cudaStreamSynchronize(s));  // the conversion has read A0 before it is released
     P.A0.reset();
-    band_lu<float2>(B, P.A0f.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU,
-                    0);
+    coarse_lu_coop<float2>(P.A0f.p, (int)nc, std::min<int>(b, (int)nc), (int)P.ld_c, P.status.p + 1, s);
     P.c_dinvf.alloc(nq * 2 * CB * CB);
     invert_diag_blocks<float2>(B, P.A0f.p, P.c_off.p, P.c_dinvf.p, (int)nc, s);
     P.A0inv.reset();
@@ -90,8 +282,7 @@ void factor_coarse(Problem& P) {
       coarse_inverse(P, P.A0inv.p);
     }
   } else {
-    band_lu<double2>(B, P.A0.p, (int)nc, std::min<int>(b, (int)nc), P.status.p + 1, s, meta, meta + 1, K_COARSE_LU,
-                     0);
+    coarse_lu_coop<double2>(P.A0.p, (int)nc, std::min<int>(b, (int)nc), (int)P.ld_c, P.status.p + 1, s);
     P.c_dinv.alloc(nq * 2 * CB * CB);
     invert_diag_blocks<double2>(B, P.A0.p, P.c_off.p, P.c_dinv.p, (int)nc, s);
   }
