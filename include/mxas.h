@@ -401,7 +401,8 @@ typedef struct {
 } mx_request_timing;
 
 typedef struct {
-  int64_t batches, factorisations, evictions, completed, cached_bytes;
+  int64_t batches;         /* batches started */
+  int64_t factorisations, evictions, completed, cached_bytes;
   int32_t cached_operators, pending;
   int64_t joined;          /* requests admitted into a batch that was already running */
 } mx_server_info;

@@ -50,6 +50,37 @@ __global__ void k_spmv_df(int64_t rows, int nrhs, const int32_t* __restrict__ ro
   }
 }
 
+// The same product for an even number of right-hand sides: one thread per (row, pair of
+// right-hand sides), so the column index and the coefficients of a nonzero are loaded once for
+// two right-hand sides and z is gathered with 16-byte loads; every right-hand side gets the
+// same operations in the same order as in k_spmv_df.
+__global__ void k_spmv_df2(int64_t rows, int nrhs, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const float4* __restrict__ coef, const float4* __restrict__ z, float4* __restrict__ w) {
+  const int half = nrhs / 2;
+  const int64_t work = rows * half;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r2 = (int)(t % half);
+    const int64_t i = t / half;
+    df::Acc re0, im0, re1, im1;
+    const int32_t e1 = rowptr[i + 1];
+    for (int32_t e = rowptr[i]; e < e1; ++e) {
+      const float4 x = z[(int64_t)col[e] * half + r2];  // (re, im) of right-hand sides 2 r2, 2 r2 + 1
+      const float4 c = coef[e];
+      df::add_prod(re0, c.x, c.y, x.x);
+      df::add_prod(re0, c.z, c.w, -x.y);
+      df::add_prod(im0, c.x, c.y, x.y);
+      df::add_prod(im0, c.z, c.w, x.x);
+      df::add_prod(re1, c.x, c.y, x.z);
+      df::add_prod(re1, c.z, c.w, -x.w);
+      df::add_prod(im1, c.x, c.y, x.w);
+      df::add_prod(im1, c.z, c.w, x.z);
+    }
+    const float2 a0 = df::value(re0), b0 = df::value(im0), a1 = df::value(re1), b1 = df::value(im1);
+    w[i * nrhs + 2 * r2] = make_float4(a0.x, b0.x, a0.y, b0.y);
+    w[i * nrhs + 2 * r2 + 1] = make_float4(a1.x, b1.x, a1.y, b1.y);
+  }
+}
+
 // hpart[blk][i][r] = sum over the block's rows of conj(V_i[x][r]) w[x][r] (i == nvec:
 // |w|^2 when with_norm). Same row split as the update: lanes (xl, r), the block's warps
 // stride over its contiguous rows. A lane keeps DOTS_U steps of w in registers and streams
@@ -599,8 +630,12 @@ void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s) {
   // coefficients (16 B) and column indices once, z (c64) once, w (16 B) once
   ProfScope ps(K_SPMV, s, 1, 20.0 * P.A.nnz + 4.0 * (P.A.rows + 1) + 24.0 * (double)P.A.rows * nrhs,
                8.0 * (double)P.A.nnz * nrhs);
-  MX_LAUNCH(k_spmv_df<<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p,
-                                                                      coef, z, w));
+  if (nrhs % 2 == 0)
+    MX_LAUNCH(k_spmv_df2<<<grid_for(work / 2, 256, 152LL * 32), 256, 0, s>>>(
+        P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p, coef, reinterpret_cast<const float4*>(z), w));
+  else
+    MX_LAUNCH(k_spmv_df<<<grid_for(work, 256, 152LL * 32), 256, 0, s>>>(P.A.rows, nrhs, P.A.rowptr.p, P.A.col.p,
+                                                                        coef, z, w));
   MX_CHECK_LAUNCH();
 }
 

@@ -273,6 +273,7 @@ struct Server {
       }
       if (stop) return;
       for (Req* r : batch) r->taken = true;
+      ++batches;  // counted when it starts: its requests may complete before the batch returns
       pending.erase(std::remove_if(pending.begin(), pending.end(),
                                    [&](int64_t id) { return reqs[id]->taken; }),
                     pending.end());
@@ -378,7 +379,6 @@ struct Server {
         r->done = true;
         ++completed;
       }
-      ++batches;
       cv_done.notify_all();
       cv_work.notify_all();
     }
