@@ -40,9 +40,10 @@ WORKLOADS = {
     # k = 20, 40^3 cells, 8^3 subdomains, one level, one right-hand side
     "maxwell40_k20_1lvl": dict(n=40, k=20.0, xi_prob=20.0, xi_prec="k", core=5, overlap=1, coarse=0,
                                nrhs=1, restart=100, max_it=600, tol=1e-6, ref_iterations=600),
-    # k = 20 two-level with a 10^3 coarse mesh and a batch of right-hand sides
+    # k = 20 two-level with a 10^3 coarse mesh and 64 right-hand sides (mx_solve runs them as
+    # two resident batches of 32, the width of its batched Krylov kernels)
     "maxwell40_k20_2lvl": dict(n=40, k=20.0, xi_prob=20.0, xi_prec="k", core=5, overlap=1, coarse=10,
-                               nrhs=32, restart=100, max_it=600, tol=1e-6, ref_iterations=600),
+                               nrhs=64, restart=100, max_it=600, tol=1e-6, ref_iterations=600),
     # profiling case of the same structure, a few GB on the device: k = 15, 30^3 cells,
     # 6^3 subdomains, 6^3 coarse mesh, 16 right-hand sides, xi = k^2
     "maxwell30_k15_2lvl": dict(n=30, k=15.0, xi_prob="k2", xi_prec="k2", core=5, overlap=1, coarse=6,
@@ -153,6 +154,8 @@ def run_ours(args, W, rank, world):
             mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_TENSOR, args.lu_tensor)
         if args.lu_grid is not None:
             mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_GRID, args.lu_grid)
+        if args.dots is not None:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_DOTS, args.dots)
         if args.weighted:
             mx.mx_set_weighted_gmres(P.h, 1)
         if args.precond != "as":
@@ -749,6 +752,8 @@ def main():
                          "updates")
     ap.add_argument("--lu-grid", type=int, default=None,
                     help="CTAs of the persistent local LU (0: one per subdomain); default: library default")
+    ap.add_argument("--dots", type=int, default=None, choices=[0, 1],
+                    help="second Gram-Schmidt pass: 0 staged kernel, 1 lane-parallel; default: library default")
     ap.add_argument("--local-tensor", type=int, default=None, choices=[0, 1],
                     help="local solves on the tensor cores (1) or CUDA cores (0); default: library default")
     ap.add_argument("--autotune", default=None, metavar="CACHE.json",

@@ -165,6 +165,12 @@ MX_API int mx_set_dense_local(mx_handle h, int dense);
  *   subdomains blockIdx, blockIdx + grid, ...; 0 (default) = one CTA per subdomain. A grid
  *   below the SM count keeps fewer trailing windows resident, so that they share L2. */
 #define MX_TUNE_LU_GRID 6
+/*   MX_TUNE_DOTS: second Gram-Schmidt pass of the MX_MIXED form (double-float inner
+ *   products); 0 (default) = staged kernel (basis tiles of 8 vectors brought into a ring of
+ *   shared-memory stages by bulk copies, one thread per row and pair of right-hand sides; 2, 4,
+ *   8, 16 or 32 right-hand sides, otherwise the lane-parallel kernel), 1 = lane-parallel
+ *   kernel. Same arithmetic per product, different summation order. */
+#define MX_TUNE_DOTS 7
 MX_API int mx_set_tuning(mx_handle h, int key, int value);
 
 /* Preconditioner variant (Sec. 6.3), applied by mx_solve and mx_precond:

@@ -22,7 +22,7 @@ from ._lib import (  # noqa: F401
     mx_set_coarse_solver, MX_COARSE_DIRECT, MX_COARSE_GMRES, mx_get_boundary_mass, MX_BC_PEC, MX_BC_IMPEDANCE,
     mx_set_growth_limit, mx_test_bounded_wait,
     mx_set_tuning, MX_TUNE_LOCAL_RHS_GROUP, MX_TUNE_LU_TENSOR, MX_TUNE_COARSE_BLOCKS, MX_TUNE_LOCAL_TENSOR, MX_TUNE_COARSE_INVERSE,
-    MX_TUNE_LU_GRID,
+    MX_TUNE_LU_GRID, MX_TUNE_DOTS,
     mx_server_create, mx_server_submit, mx_server_poll, mx_server_stats, mx_server_destroy, MX_PENDING,
 )
 from .problem import Problem  # noqa: F401

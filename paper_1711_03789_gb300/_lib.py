@@ -168,6 +168,7 @@ MX_TUNE_COARSE_BLOCKS = 3
 MX_TUNE_LOCAL_TENSOR = 4
 MX_TUNE_COARSE_INVERSE = 5
 MX_TUNE_LU_GRID = 6
+MX_TUNE_DOTS = 7
 
 
 def mx_set_tuning(h, key, value):

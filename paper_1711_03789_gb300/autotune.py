@@ -31,6 +31,7 @@ from . import _lib as L
 KNOBS = {
     "lu_tensor": L.MX_TUNE_LU_TENSOR,
     "lu_grid": L.MX_TUNE_LU_GRID,
+    "dots": L.MX_TUNE_DOTS,
     "coarse_inverse": L.MX_TUNE_COARSE_INVERSE,
     "local_tensor": L.MX_TUNE_LOCAL_TENSOR,
     "local_rhs_group": L.MX_TUNE_LOCAL_RHS_GROUP,
@@ -38,10 +39,10 @@ KNOBS = {
 }
 
 # library defaults, written out so that a cached choice never depends on "0 = default"
-DEFAULTS = {"lu_tensor": 0, "lu_grid": 0, "coarse_inverse": 1, "local_tensor": 1, "local_rhs_group": 16,
+DEFAULTS = {"lu_tensor": 0, "lu_grid": 0, "dots": 0, "coarse_inverse": 1, "local_tensor": 1, "local_rhs_group": 16,
             "coarse_blocks": 0}
 
-FORMAT = 2
+FORMAT = 3
 
 
 def candidates(info, cfg, name, allow_reduced=False):
@@ -56,6 +57,10 @@ def candidates(info, cfg, name, allow_reduced=False):
         # CTAs of the persistent LU (0: one per subdomain); only with the persistent LU
         persistent = cfg.get("lu_tensor", 0) in (0, 2)
         return [0, 152, 114, 76] if (mixed and persistent and info["n_sub"] > 152) else []
+    if name == "dots":
+        # the staged second pass applies to 2, 4, 8, 16 or 32 right-hand sides; the cost
+        # measures it at the tuning batch's count, which the cache key records
+        return [0, 1] if mixed else []
     if name == "coarse_inverse":
         return [1, 0] if (mixed and coarse) else []
     if name == "local_tensor":

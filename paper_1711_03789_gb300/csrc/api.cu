@@ -321,6 +321,9 @@ int mx_set_tuning(mx_handle h, int key, int value) {
     } else if (key == MX_TUNE_COARSE_INVERSE) {
       MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "coarse inverse mode must be 0 or 1");
       P.tune_coarse_inverse = value;
+    } else if (key == MX_TUNE_DOTS) {
+      MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "dots mode must be 0 or 1");
+      P.tune_dots = value;
     } else if (key == MX_TUNE_LOCAL_TENSOR) {
       MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "local tensor mode must be 0 or 1");
       P.tune_local_tc = value;

@@ -21,6 +21,7 @@
 //   B_F[(pq),(rs)] = (1 / 24) [ same bracket as M_e with the projected g ],
 // independent of h. The same row gather restricted to a box (tetrahedra inside it,
 // triangles on its surface) gives the ImpRAS local matrices (Sec. 6.3).
+#include "df64.cuh"
 #include "problem.cuh"
 
 namespace mx {
@@ -261,7 +262,8 @@ void assemble_KM(const MeshDev& m, CsrKM& A, cudaStream_t s, bool boundary) {
 struct QuadRule {
   double xi[27][3];
   double w[27];
-  double cw[27][4];  // w_q h^2 lambda_k(xi_q): weight, Jacobian 6|T| = h^3 and the 1/h of the gradients
+  double cw[27][4];   // w_q h^2 lambda_k(xi_q): weight, Jacobian 6|T| = h^3 and the 1/h of the gradients
+  float2 cwd[27][4];  // cw as double-floats (hi = FP32 rounding, lo = remainder)
 };
 
 static QuadRule make_rule(double h) {
@@ -279,7 +281,11 @@ static QuadRule make_rule(double h) {
         r.xi[q][2] = (1.0 - u) * (1.0 - v) * w;
         r.w[q] = wt[a] * wt[b] * wt[c] * (1.0 - u) * (1.0 - u) * (1.0 - v);
         const double lam[4] = {1.0 - r.xi[q][0] - r.xi[q][1] - r.xi[q][2], r.xi[q][0], r.xi[q][1], r.xi[q][2]};
-        for (int k = 0; k < 4; ++k) r.cw[q][k] = r.w[q] * h * h * lam[k];
+        for (int k = 0; k < 4; ++k) {
+          r.cw[q][k] = r.w[q] * h * h * lam[k];
+          const float hi = (float)r.cw[q][k];
+          r.cwd[q][k] = make_float2(hi, (float)(r.cw[q][k] - (double)hi));
+        }
       }
   return r;
 }
@@ -291,7 +297,9 @@ struct LoadArgs {
   const double* centres;  // [nrhs][nbumps][3]
   const double2* pol;     // [nrhs][nbumps][3]
   const double* etab;     // [nrhs][nbumps][3][n][81] per-axis Gaussian factors
-  double2* contrib;       // [ntet][6][nrhs]
+  float2* etab2;          // the same as double-floats (mixed form; written by k_load_table)
+  const float4* pit;      // [nrhs][nbumps][6][4] p_b . g_k per path order, double-float re and im
+  double2* contrib;       // [nrhs][ntet][6]
 };
 
 // The Gaussian bump is a product of one-dimensional factors, and inside cube i (per axis)
@@ -312,7 +320,28 @@ __global__ void k_load_table(LoadArgs a, double* etab) {
     const double s = tt == 0 ? a.rule.xi[q][0] + a.rule.xi[q][1] + a.rule.xi[q][2]
                              : (tt == 1 ? a.rule.xi[q][1] + a.rule.xi[q][2] : a.rule.xi[q][2]);
     const double d = (i + s) * a.h - a.centres[rest * 3 + ax];
-    etab[t] = exp(-d * d * a.inv_w2);
+    const double v = exp(-d * d * a.inv_w2);
+    if (etab) etab[t] = v;
+    if (a.etab2) {
+      const float hi = __double2float_rn(v);
+      a.etab2[t] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+  }
+}
+
+// pit[r][b][p][k] = p_b . g_k for path order p (g_0 = -e_s0, g_1 = e_s0 - e_s1, g_2 = e_s1 - e_s2,
+// g_3 = e_s2; the same combinations k_load_tets forms per tetrahedron), split into double-floats
+__global__ void k_load_pi(LoadArgs a, float4* pit) {
+  const int total = a.nrhs * a.nbumps * 24;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int k = t % 4, p = (t / 4) % 6, rb = t / 24;
+    const double2* q = a.pol + (int64_t)rb * 3;
+    const double2 q0 = q[a_perms[p][0]], q1 = q[a_perms[p][1]], q2 = q[a_perms[p][2]];
+    const double2 v = k == 0 ? make_double2(-q0.x, -q0.y)
+                             : (k == 1 ? make_double2(q0.x - q1.x, q0.y - q1.y)
+                                       : (k == 2 ? make_double2(q1.x - q2.x, q1.y - q2.y) : q2));
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    pit[t] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
   }
 }
 
@@ -321,13 +350,15 @@ __global__ void k_load_table(LoadArgs a, double* etab) {
 // bump b), the integral is sum_b (L_bP (p_b . g_Q) - L_bQ (p_b . g_P)) with the four
 // weighted moments L_bk = sum_q w_q h^2 lam_k(xi_q) G_b(x_q) and g the integer gradients
 // (grad lam = g / h): four FP64 FMAs per point and bump instead of a basis evaluation.
+// Threads take (right-hand side, tetrahedron), tetrahedron fastest: a warp's tetrahedra lie in a
+// few neighbouring cubes, so their table rows are shared or adjacent.
 __global__ void k_load_tets(LoadArgs a) {
   const int64_t ntet = 6LL * a.n * a.n * a.n;
   const int64_t work = ntet * a.nrhs;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t % a.nrhs);
-    const int64_t tet = t / a.nrhs;
+    const int r = (int)(t / ntet);
+    const int64_t tet = t % ntet;
     const int64_t cube = tet / 6;
     const int p = (int)(tet % 6);
     const int cx = (int)(cube % a.n), cy = (int)((cube / a.n) % a.n), cz = (int)(cube / ((int64_t)a.n * a.n));
@@ -365,7 +396,68 @@ __global__ void k_load_tets(LoadArgs a) {
       }
     }
 #pragma unroll
-    for (int e = 0; e < 6; ++e) a.contrib[(tet * 6 + e) * a.nrhs + r] = acc[e];
+    for (int e = 0; e < 6; ++e) a.contrib[((int64_t)r * ntet + tet) * 6 + e] = acc[e];
+  }
+}
+
+// k_load_tets in double-float arithmetic on the FP32 units (mixed form): the same moments
+// L_bk and edge combinations, with the Gaussian factors, weights and p_b . g_k as (hi, lo)
+// FP32 pairs, products formed exactly by FMA (the lo * lo term dropped) and sums carried
+// with their rounding errors. About 2^-44 relative error per moment against 2^-52 in FP64;
+// the FP64 units of this GPU issue at about 1/64 of the FP32 rate.
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return make_float2(p, e);
+}
+__global__ void k_load_tets_df(LoadArgs a) {
+  const int64_t ntet = 6LL * a.n * a.n * a.n;
+  const int64_t work = ntet * a.nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / ntet);
+    const int64_t tet = t % ntet;
+    const int64_t cube = tet / 6;
+    const int p = (int)(tet % 6);
+    const int cx = (int)(cube % a.n), cy = (int)((cube / a.n) % a.n), cz = (int)(cube / ((int64_t)a.n * a.n));
+    const int s0 = a_perms[p][0], s1 = a_perms[p][1], s2 = a_perms[p][2];
+    auto corner = [&](int ax) { return ax == 0 ? cx : (ax == 1 ? cy : cz); };
+    const int64_t row0 = ((int64_t)s0 * a.n + corner(s0)) * 81;
+    const int64_t row1 = ((int64_t)s1 * a.n + corner(s1)) * 81 + 1;
+    const int64_t row2 = ((int64_t)s2 * a.n + corner(s2)) * 81 + 2;
+    const float2* E = a.etab2 + (int64_t)r * a.nbumps * 3 * a.n * 81;
+    df::Acc acc_re[6], acc_im[6];
+    for (int b = 0; b < a.nbumps; ++b) {
+      const float2* Eb = E + (int64_t)b * 3 * a.n * 81;
+      df::Acc L[4];
+#pragma unroll 3
+      for (int q = 0; q < 27; ++q) {
+        const float2 e = df_mul(df_mul(Eb[row0 + 3 * q], Eb[row1 + 3 * q]), Eb[row2 + 3 * q]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) df::add_prod2(L[k], a.rule.cwd[q][k].x, a.rule.cwd[q][k].y, e.x, e.y);
+      }
+      float2 Lv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Lv[k] = df::value(L[k]);
+      const float4* pi = a.pit + (((int64_t)r * a.nbumps + b) * 6 + p) * 4;
+      float4 pv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) pv[k] = pi[k];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const int P0 = e < 3 ? 0 : (e < 5 ? 1 : 2), Q0 = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+        // L_P (p . g_Q) - L_Q (p . g_P)
+        df::add_prod2(acc_re[e], Lv[P0].x, Lv[P0].y, pv[Q0].x, pv[Q0].y);
+        df::add_prod2(acc_re[e], Lv[Q0].x, Lv[Q0].y, -pv[P0].x, -pv[P0].y);
+        df::add_prod2(acc_im[e], Lv[P0].x, Lv[P0].y, pv[Q0].z, pv[Q0].w);
+        df::add_prod2(acc_im[e], Lv[Q0].x, Lv[Q0].y, -pv[P0].z, -pv[P0].w);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+      a.contrib[((int64_t)r * ntet + tet) * 6 + e] = make_double2(df::to_double(acc_re[e]), df::to_double(acc_im[e]));
   }
 }
 
@@ -375,17 +467,18 @@ __global__ void k_load_gather(int n, int64_t n_dof, int nrhs, const int32_t* dof
   const int64_t work = n_dof * nrhs;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < work;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t % nrhs);
-    const int64_t i = t / nrhs;
+    const int r = (int)(t / n_dof);
+    const int64_t i = t % n_dof;
     int c[3], d;
     key_to_coords(dof_key[i], n, c, d);
     int64_t tets[6];
     int loc[6];
     const int blo[3] = {0, 0, 0}, bhi[3] = {n, n, n};
     const int nt = edge_tets(n, c, d, tets, loc, blo, bhi);
+    const double2* cr = contrib + (int64_t)r * 36 * n * n * n;  // 6 n^3 tetrahedra x 6 edges
     double2 s = make_double2(0, 0);
     for (int k = 0; k < nt; ++k) {
-      const double2 v = contrib[(tets[k] * 6 + loc[k]) * nrhs + r];
+      const double2 v = cr[tets[k] * 6 + loc[k]];
       s.x += v.x;
       s.y += v.y;
     }
@@ -403,8 +496,12 @@ void load_vector(const Problem& P, int nrhs, int nbumps, const double* h_centres
   DevBuf<double2> dp((size_t)nrhs * nbumps * 3);
   MX_CUDA(cudaMemcpyAsync(dc.p, h_centres, dc.bytes(), cudaMemcpyHostToDevice, s));
   MX_CUDA(cudaMemcpyAsync(dp.p, h_pol, dp.bytes(), cudaMemcpyHostToDevice, s));
+  // the mixed form takes the double-float moments (k_load_tets_df), the FP64 form FP64 ones
+  const bool df = P.precision == MX_MIXED;
   DevBuf<double2> contrib(ntet * 6 * chunk);
-  DevBuf<double> etab((size_t)chunk * nbumps * 3 * n * 81);
+  DevBuf<double> etab(df ? 0 : (size_t)chunk * nbumps * 3 * n * 81);
+  DevBuf<float2> etab2(df ? (size_t)chunk * nbumps * 3 * n * 81 : 0);
+  DevBuf<float4> pit(df ? (size_t)chunk * nbumps * 24 : 0);
   for (int r0 = 0; r0 < nrhs; r0 += chunk) {
     const int nr = std::min(chunk, nrhs - r0);
     LoadArgs a;
@@ -414,11 +511,22 @@ void load_vector(const Problem& P, int nrhs, int nbumps, const double* h_centres
     a.rule = make_rule(1.0 / n);
     a.centres = dc.p + (int64_t)r0 * nbumps * 3;
     a.pol = dp.p + (int64_t)r0 * nbumps * 3;
+    // bytes: the tetrahedron contributions written and gathered, f written; flops: 27 points x
+    // (2 products + 4 FMAs) and 6 edges x 2 complex products per tetrahedron and bump
+    ProfScope ps(K_LOAD, s, df ? 4 : 3, (double)ntet * 6 * 16 * 2 * nr + 16.0 * P.fine.n_dof * nr,
+                 (double)ntet * nr * nbumps * (27 * 10 + 48));
     a.contrib = contrib.p;
-    a.etab = etab.p;
-    MX_LAUNCH(k_load_table<<<grid_for((int64_t)nr * nbumps * 3 * n * 81, 256), 256, 0, s>>>(a, etab.p));
+    a.etab = df ? nullptr : etab.p;
+    a.etab2 = df ? etab2.p : nullptr;
+    a.pit = df ? pit.p : nullptr;
+    MX_LAUNCH(k_load_table<<<grid_for((int64_t)nr * nbumps * 3 * n * 81, 256), 256, 0, s>>>(a, df ? nullptr : etab.p));
     MX_CHECK_LAUNCH();
-    MX_LAUNCH(k_load_tets<<<grid_for(ntet * nr, 128), 128, 0, s>>>(a));
+    if (df) {
+      MX_LAUNCH(k_load_pi<<<grid_for((int64_t)nr * nbumps * 24, 256), 256, 0, s>>>(a, pit.p));
+      MX_LAUNCH(k_load_tets_df<<<grid_for(ntet * nr, 128), 128, 0, s>>>(a));
+    } else {
+      MX_LAUNCH(k_load_tets<<<grid_for(ntet * nr, 128), 128, 0, s>>>(a));
+    }
     MX_CHECK_LAUNCH();
     MX_LAUNCH(k_load_gather<<<grid_for(P.fine.n_dof * nr, 256), 256, 0, s>>>(
         n, P.fine.n_dof, nr, P.fine.dof_key.p, contrib.p, f + (int64_t)r0 * P.fine.n_dof));

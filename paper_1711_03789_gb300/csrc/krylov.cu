@@ -836,13 +836,13 @@ static float2* basis_hi(Workspace& W) { return reinterpret_cast<float2*>(W.V.p);
 static float2* basis_lo(Workspace& W) { return reinterpret_cast<float2*>(W.V.p) + (int64_t)(W.m + 1) * W.n * W.nrhs; }
 
 // mixed form: double-float passes over the basis, FP64 reduction of the block partials
-static void dots_mixed(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s,
+static void dots_mixed(Workspace& W, int64_t n, int nvec, int with_norm, cudaStream_t s, int32_t* timeout,
                        const double2* target = nullptr, const double2* extra = nullptr) {
-  // one resident wave: the dots kernel holds 64 KB of accumulators per block (3 per SM)
-  const int nb = std::min(W.nblk, 3 * sm_count());
-  dots_df(nb, n, W.nrhs, nvec, with_norm, basis_hi(W), basis_lo(W),
-          reinterpret_cast<const float4*>(target ? target : W.w.p), W.active.p, W.hpart.p, s,
-          reinterpret_cast<const float4*>(extra));
+  // one resident wave: the lane-parallel kernels hold 64 KB of accumulators per block (3 per
+  // SM), the staged one 108 KB of stages (2 per SM)
+  const int nb = dots_df(std::min(W.nblk, 3 * sm_count()), n, W.nrhs, nvec, with_norm, basis_hi(W), basis_lo(W),
+                         reinterpret_cast<const float4*>(target ? target : W.w.p), W.active.p, W.hpart.p, s,
+                         reinterpret_cast<const float4*>(extra), timeout);
   const int total = nvec + with_norm;
   ProfScope ps(K_ARNOLDI_SMALL, s);
   MX_LAUNCH(k_reduce_dots<<<grid_for((int64_t)total * W.nrhs * 32, 256), 256, 0, s>>>(nb, total, W.nrhs, W.hpart.p,
@@ -982,7 +982,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
           else spmv_km(P, -P.k * P.k, 0.0, in, 0, out, nrhs, s);
         };
         auto wdots = [&]() {  // h = V^H (D w), entry j+1 = w^H D w
-          if (mixed) dots_mixed(W, n, j + 1, 1, s, W.r.p, W.w.p);
+          if (mixed) dots_mixed(W, n, j + 1, 1, s, nullptr, W.r.p, W.w.p);
           else dots(W, n, j + 1, 1, s, W.r.p, W.w.p);
         };
         auto update = [&]() {
@@ -1029,7 +1029,7 @@ int gmres_solve(Problem& P, const double2* b, double2* x, int nrhs, double tol, 
         }
         orth_update_df(W.nblk, n, nrhs, j + 1, Vh, basis_lo(W), W.h2.p, W.hs.p, W.active.p,
                        reinterpret_cast<float4*>(W.w.p), W.npart.p, s);
-        dots_mixed(W, n, j + 1, 0, s);
+        dots_mixed(W, n, j + 1, 0, s, P.tune_dots == 0 ? P.status.p + 2 : nullptr);
         {
           ProfScope ps(K_ARNOLDI_SMALL, s);
           MX_LAUNCH(k_cgs2_finish<<<1, 32, 0, s>>>(W.nblk, nrhs, j, m, 1, W.h2.p, W.npart.p, W.H.p, W.active.p,

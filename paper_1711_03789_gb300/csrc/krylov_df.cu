@@ -14,6 +14,7 @@
 // ||w''||^2 = ||w'||^2 - |h2|^2 (k_update2_normalize).
 #include "df64.cuh"
 #include "problem.cuh"
+#include "tc.cuh"
 
 namespace mx {
 
@@ -185,6 +186,9 @@ __global__ void __launch_bounds__(256, 3) k_dots_df(int64_t n, int nrhs, int nve
 // Lanes (xl, rp), rp = pair index fastest; XL2 = 32 / (RP / 2) rows per warp step.
 constexpr int DOTS_U2 = 4;
 
+// named barrier of the staged kernel's four consumer warps (the producer warp does not join)
+__device__ __forceinline__ void bar_consumers() { tc::bar_sync(1, 128); }
+
 // a += the accumulator of lane (lane ^ o), compensated
 __device__ __forceinline__ void fold_lanes(df::Acc& a, int o) {
   float sm, e;
@@ -294,6 +298,174 @@ __global__ void __launch_bounds__(256, 3) k_dots_df2(int64_t n, int nrhs, int nv
       if (rr < nrhs) hpart[((int64_t)blockIdx.x * total + ic + k) * nrhs + rr] = make_double2(sx, sy);
     }
     __syncthreads();
+  }
+}
+
+// Staged form of the double-float inner products (no norm entry) for nrhs in {2, 4, 8, 16, 32}.
+// A producer warp streams the basis through a ring of DS_STAGES shared-memory stages with bulk
+// copies, so the loads are in flight while four consumer warps compute. A stage holds DS_VG
+// basis vectors (both planes) over XS = 128 / (nrhs / 2) consecutive rows: 32 KB in 2 KB
+// copies. Consumer thread (xs, p) takes row xs of every stage and right-hand sides 2p, 2p+1,
+// and keeps the 4 * DS_VG compensated accumulators of its chunk of vectors in registers over
+// all of its block's rows (w straight from global memory, one row ahead); the row lanes are
+// folded once per chunk, not once per row step as in the lane-parallel kernels. Vectors beyond
+// DS_VG: the rows are swept again for the next chunk (w read once per chunk). Writes the same
+// per-block partials as k_dots_df.
+constexpr int DS_VG = 8;                          // basis vectors per stage
+constexpr int DS_STAGES = 3;                      // ring depth
+constexpr int DS_CONSUMERS = 128;                 // 4 warps
+constexpr int DS_THREADS = DS_CONSUMERS + 32;     // + the producer warp
+constexpr int DS_TILE = DS_CONSUMERS * 2 * 8;     // one plane of one vector: XS rows x nrhs x 8 B
+constexpr int DS_STAGE_BYTES = 2 * DS_VG * DS_TILE;
+constexpr int DS_WAIT_LIMIT = 1 << 22;
+
+__global__ void __launch_bounds__(DS_THREADS, 2) k_dots_df_staged(int64_t n, int nrhs, int nvec,
+                                                                const float2* __restrict__ Vh,
+                                                                const float2* __restrict__ Vl,
+                                                                const float4* __restrict__ w,
+                                                                const int32_t* __restrict__ active,
+                                                                double2* __restrict__ hpart, int32_t* timeout) {
+  extern __shared__ __align__(128) unsigned char ds_smem[];
+  __shared__ __align__(8) uint64_t full[DS_STAGES], empty[DS_STAGES];
+  __shared__ double2 red[DS_CONSUMERS / 32][DS_VG][16][2];  // per-warp folded partials
+  __shared__ volatile int stop;
+  const int np = nrhs / 2, xsn = DS_CONSUMERS / np;  // pairs per row, rows per stage
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t x0 = min(n, (int64_t)blockIdx.x * chunk), x1 = min(n, x0 + chunk);
+  const int64_t nv = n * nrhs;
+  const uint32_t base = tc::smem_u32(ds_smem);
+  const uint32_t full_a = tc::smem_u32(&full[0]), empty_a = tc::smem_u32(&empty[0]);
+  if (tid == 0) {
+    for (int i = 0; i < DS_STAGES; ++i) {
+      tc::mbar_init(full_a + 8 * i, 1);
+      tc::mbar_init(empty_a + 8 * i, DS_CONSUMERS / 32);
+    }
+    tc::mbar_fence_init();
+    stop = 0;
+  }
+  __syncthreads();
+
+  if (warp == DS_CONSUMERS / 32) {
+    // producer: stages in the consumers' order (chunk of vectors, row step)
+    int64_t st = 0;  // stages issued
+    bool ok = true;
+    for (int k0 = 0; k0 < nvec && ok; k0 += DS_VG) {
+      const int nk = min(DS_VG, nvec - k0);
+      for (int64_t x = x0; x < x1 && ok; x += xsn, ++st) {
+        const int slot = (int)(st % DS_STAGES), use = (int)(st / DS_STAGES);
+        const uint32_t rb = (uint32_t)min((int64_t)xsn, x1 - x) * nrhs * 8;
+        if (lane == 0) {
+          if (use > 0 && !tc::mbar_wait_flag(empty_a + 8 * slot, (use - 1) & 1, DS_WAIT_LIMIT, &stop)) {
+            atomicAdd(timeout, 1);
+            stop = 1;
+          }
+          if (!stop) tc::mbar_expect_tx(full_a + 8 * slot, 2 * nk * rb);
+        }
+        ok = __shfl_sync(0xffffffffu, stop == 0, 0);
+        if (!ok) break;
+        if (lane < 2 * nk) {
+          const int plane = lane / nk, v = lane % nk;
+          const float2* src = (plane ? Vl : Vh) + (int64_t)(k0 + v) * nv + x * nrhs;
+          tc::bulk_g2s(base + (uint32_t)slot * DS_STAGE_BYTES + (uint32_t)(plane * DS_VG + v) * DS_TILE, src, rb,
+                       full_a + 8 * slot);
+        }
+      }
+    }
+    // every copy this block issued lands before the block's shared memory is released: wait
+    // for the last phase each slot was given
+    if (lane == 0)
+      for (int i = 0; i < DS_STAGES && i < st; ++i) {
+        const int last = (int)((st - 1 - i) / DS_STAGES);
+        if (!tc::mbar_wait(full_a + 8 * i, last & 1, DS_WAIT_LIMIT)) atomicAdd(timeout, 1);
+      }
+    return;
+  }
+
+  // consumers: thread (xs, p) = (row xs of each stage, right-hand sides 2p and 2p+1)
+  const int xs = tid / np, p = tid % np, r0 = 2 * p;
+  const bool on0 = active[r0] != 0, on1 = active[r0 + 1] != 0;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  int64_t st = 0;
+  // A wait that runs out (or `stop` set by another warp) marks the warp failed: it computes
+  // nothing more but keeps the loop and barrier sequence of the others, whose waits then
+  // return at once, so the block still reaches its end.
+  bool failed = false;
+  for (int k0 = 0; k0 < nvec; k0 += DS_VG) {
+    const int nk = min(DS_VG, nvec - k0);
+    df::Acc acc[DS_VG][4];  // re0, im0, re1, im1 per vector
+    auto load_w = [&](int64_t x, float4& a, float4& b) {
+      const bool row = x + xs < x1;
+      a = (row && on0) ? w[(x + xs) * nrhs + r0] : zero;
+      b = (row && on1) ? w[(x + xs) * nrhs + r0 + 1] : zero;
+    };
+    float4 c0, c1, n0, n1;
+    load_w(x0, n0, n1);
+    for (int64_t x = x0; x < x1; x += xsn, ++st) {
+      c0 = n0;
+      c1 = n1;
+      if (x + xsn < x1) load_w(x + xsn, n0, n1);
+      const int slot = (int)(st % DS_STAGES), use = (int)(st / DS_STAGES);
+      if (!failed) {
+        const bool landed = tc::mbar_wait_flag(full_a + 8 * slot, use & 1, DS_WAIT_LIMIT, &stop);
+        if (!__all_sync(0xffffffffu, landed)) {
+          failed = true;
+          if (lane == 0) {
+            atomicAdd(timeout, 1);
+            stop = 1;
+          }
+        }
+      }
+      if (failed) continue;
+      const float4* ht = reinterpret_cast<const float4*>(ds_smem + (size_t)slot * DS_STAGE_BYTES) + tid;
+      const float4* lt = ht + DS_VG * (DS_TILE / 16);
+      if (x + xs < x1) {
+        float4 h[DS_VG], l[DS_VG];
+#pragma unroll
+        for (int v = 0; v < DS_VG; ++v) {
+          h[v] = v < nk ? ht[v * (DS_TILE / 16)] : zero;
+          l[v] = v < nk ? lt[v * (DS_TILE / 16)] : zero;
+        }
+#pragma unroll
+        for (int v = 0; v < DS_VG; ++v) {
+          // conj(a) c = (a.re c.re + a.im c.im) + i (a.re c.im - a.im c.re); a = V entry
+          const float4 a0 = make_float4(h[v].x, h[v].y, l[v].x, l[v].y);
+          const float4 a1 = make_float4(h[v].z, h[v].w, l[v].z, l[v].w);
+          df::add_prod2(acc[v][0], a0.x, a0.z, c0.x, c0.z);
+          df::add_prod2(acc[v][0], a0.y, a0.w, c0.y, c0.w);
+          df::add_prod2(acc[v][1], a0.x, a0.z, c0.y, c0.w);
+          df::add_prod2(acc[v][1], -a0.y, -a0.w, c0.x, c0.z);
+          df::add_prod2(acc[v][2], a1.x, a1.z, c1.x, c1.z);
+          df::add_prod2(acc[v][2], a1.y, a1.w, c1.y, c1.w);
+          df::add_prod2(acc[v][3], a1.x, a1.z, c1.y, c1.w);
+          df::add_prod2(acc[v][3], -a1.y, -a1.w, c1.x, c1.z);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(empty_a + 8 * slot);
+    }
+    // fold the row lanes of each warp (lane = xs_in_warp * np + p), then the warps in order
+#pragma unroll
+    for (int v = 0; v < DS_VG; ++v) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        for (int o = np; o < 32; o <<= 1) fold_lanes(acc[v][q], o);
+      if (lane < np)
+        red[warp][v][p][0] = make_double2(df::to_double(acc[v][0]), df::to_double(acc[v][1])),
+        red[warp][v][p][1] = make_double2(df::to_double(acc[v][2]), df::to_double(acc[v][3]));
+    }
+    bar_consumers();
+    for (int t = tid; t < nk * nrhs; t += DS_CONSUMERS) {
+      const int v = t / nrhs, r = t % nrhs;
+      double sx = 0.0, sy = 0.0;
+      for (int wq = 0; wq < DS_CONSUMERS / 32; ++wq) {
+        const double2 m = red[wq][v][r / 2][r & 1];
+        sx += m.x;
+        sy += m.y;
+      }
+      hpart[((int64_t)blockIdx.x * nvec + k0 + v) * nrhs + r] = make_double2(sx, sy);
+    }
+    bar_consumers();
   }
 }
 
@@ -661,9 +833,22 @@ static void dots_rp(int nblk, int64_t n, int nrhs, int nvec, int with_norm, cons
   }
   MX_LAUNCH(k_dots_df<RP><<<nblk, 256, smem, s>>>(n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, extra));
 }
-void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2* Vh, const float2* Vl,
-             const float4* w, const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra) {
+int dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2* Vh, const float2* Vl,
+            const float4* w, const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra,
+            int32_t* timeout) {
   ProfScope ps(K_DOTS, s, 1, 16.0 * (nvec + 1) * (double)n * nrhs, 8.0 * (nvec + with_norm) * (double)n * nrhs);
+  if (timeout && !extra && !with_norm && (nrhs == 2 || nrhs == 4 || nrhs == 8 || nrhs == 16 || nrhs == 32)) {
+    const size_t smem = (size_t)DS_STAGES * DS_STAGE_BYTES;
+    static bool configured = false;
+    if (!configured) {
+      MX_CUDA(cudaFuncSetAttribute(k_dots_df_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      configured = true;
+    }
+    const int nb = std::min(nblk, 2 * sm_count());
+    MX_LAUNCH(k_dots_df_staged<<<nb, DS_THREADS, smem, s>>>(n, nrhs, nvec, Vh, Vl, w, active, hpart, timeout));
+    MX_CHECK_LAUNCH();
+    return nb;
+  }
   if (nrhs <= 1) dots_rp<1>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
   else if (nrhs <= 2) dots_rp<2>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
   else if (nrhs <= 4) dots_rp<4>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
@@ -671,6 +856,7 @@ void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float
   else if (nrhs <= 16) dots_rp<16>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
   else dots_rp<32>(nblk, n, nrhs, nvec, with_norm, Vh, Vl, w, active, hpart, s, extra);
   MX_CHECK_LAUNCH();
+  return nblk;
 }
 
 template <int RP>

@@ -88,6 +88,7 @@ struct Problem {
   bool dense_local = false;        // force b_l = n_l - 1 (full dense storage)
   int tune_local_group = 0;        // cap on right-hand sides per local-solve block (0 = 16)
   int tune_lu_grid = 0;            // CTAs of the persistent LU (0: one per subdomain)
+  int tune_dots = 0;               // second Gram-Schmidt pass (mixed): 0 staged, 1 lane-parallel
   int tune_lu_tc = 0;              // FP32 local LU: 0 / 2 persistent 3 x TF32 tensor-core LU, per-step
                                    // launches with 1 TF32 or 3 split 3 x TF32 tensor-core updates, 4 FP32 CUDA cores
   int tune_coarse_blocks = 0;      // blocks of the cooperative coarse sweep (0 = by work)
@@ -267,8 +268,12 @@ void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s);
 void spmv_df_c128(Problem& P, double xi, const float2* z, double2* y, int nrhs, cudaStream_t s);
 // The basis of the mixed form is two c64 planes: Vh [m+1][n][nrhs] (c64 rounding) and Vl
 // (remainder); vector i at offset i * n * nrhs of each.
-void dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2* Vh, const float2* Vl,
-             const float4* w, const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra = nullptr);
+// Block partials go to hpart[b][i][r] for b < the returned block count (at most nblk). Given
+// `timeout` (a device counter; null selects the lane-parallel kernels), no `extra` and no norm
+// entry, nrhs of 2, 4, 8, 16 or 32 takes the staged kernel, whose bounded waits count into *timeout.
+int dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2* Vh, const float2* Vl,
+            const float4* w, const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra = nullptr,
+            int32_t* timeout = nullptr);
 // first Gram-Schmidt pass: FP32 products of the c64 planes, FP64 partials
 void dots_c64(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float4* w, const int32_t* active,
               double2* hpart, cudaStream_t s);

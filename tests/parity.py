@@ -16,6 +16,11 @@ MIXED_APPLY_TOL = 6e-5
 # Tensor-core local solves: the factors enter the MMA rounded to TF32 (unit roundoff 2^-12);
 # measured worst case 1.8 units, bound 4 units.
 TF32_SOLVE_TOL = 4 * 2.0 ** -12
+# Load vector of the mixed form, which forms the quadrature moments in double-float arithmetic:
+# each of the 27 products per moment carries about 3 * 2^-46 relative error, a moment about
+# 2^-43, and an entry sums at most 6 tetrahedra x 3 bumps x 2 products of a moment with
+# p_b . g_k: 36 * 2^-43 = 4.1e-12 of the largest such product, itself below max |f|.
+LOAD_DF_TOL = 4.1e-12
 
 
 def rel_errors(got, want):

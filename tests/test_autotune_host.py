@@ -23,9 +23,9 @@ def _applicable(info, cfg=None):
 def test_candidates_per_problem_kind():
     assert _applicable(_info(mx.MX_PLAIN_FP64)) == {"local_rhs_group"}
     assert _applicable(_info(mx.MX_PLAIN_FP64, 125)) == {"local_rhs_group", "coarse_blocks"}
-    assert _applicable(_info(mx.MX_MIXED)) == {"lu_tensor", "local_tensor", "local_rhs_group"}
+    assert _applicable(_info(mx.MX_MIXED)) == {"lu_tensor", "dots", "local_tensor", "local_rhs_group"}
     mixed_coarse = _info(mx.MX_MIXED, 125)
-    assert _applicable(mixed_coarse) == {"lu_tensor", "coarse_inverse", "local_tensor", "local_rhs_group"}
+    assert _applicable(mixed_coarse) == {"lu_tensor", "dots", "coarse_inverse", "local_tensor", "local_rhs_group"}
     # the cooperative sweep only runs when the explicit inverse is off
     assert "coarse_blocks" in _applicable(mixed_coarse, {"coarse_inverse": 0})
     # the persistent LU's grid: only for the persistent LU and more subdomains than SMs
@@ -54,11 +54,12 @@ def _separable(target, weights):
 
 def test_search_finds_a_planted_optimum():
     info = _info(mx.MX_MIXED, 125)
-    target = dict(at.DEFAULTS, lu_tensor=3, coarse_inverse=0, local_tensor=0, local_rhs_group=4, coarse_blocks=38)
+    target = dict(at.DEFAULTS, lu_tensor=3, dots=1, coarse_inverse=0, local_tensor=0, local_rhs_group=4,
+                  coarse_blocks=38)
     measure, calls = _separable(target, {k: 10.0 for k in at.KNOBS})
     knobs, cost, base, trials = at.search(info, measure)
     assert knobs == target and cost == 100.0
-    assert base == 100.0 + 10.0 * 5
+    assert base == 100.0 + 10.0 * 6
     # one trial per value: the default, then every other candidate of each knob once
     cfg = dict(at.DEFAULTS)
     expect = 1

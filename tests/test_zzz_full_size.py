@@ -23,6 +23,7 @@ import numpy as np
 import pytest
 
 import inputs
+from parity import LOAD_DF_TOL
 from oracle.mesh import KuhnMesh
 from oracle import fem
 
@@ -137,7 +138,8 @@ def test_benchmark_workload_at_full_size():
 
     dofs = _sample(n, mesh=m, centres=c)
     fs = sampled_load_vector(m, fem.bump_field(c, p, 0.1), dofs)  # [len(dofs), NRHS]
-    assert np.abs(fh[:, dofs].T - fs).max() <= 1e-12 * np.abs(fs).max()
+    # the mixed form's load vector: double-float quadrature moments
+    assert np.abs(fh[:, dofs].T - fs).max() <= LOAD_DF_TOL * np.abs(fs).max()
 
     Km, Mm = fem.assemble_KM(m)
     A = fem.a_xi(Km, Mm, K, XI).tocsr()
