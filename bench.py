@@ -156,6 +156,8 @@ def run_ours(args, W, rank, world):
             mx.mx_set_tuning(P.h, mx.MX_TUNE_LU_GRID, args.lu_grid)
         if args.dots is not None:
             mx.mx_set_tuning(P.h, mx.MX_TUNE_DOTS, args.dots)
+        if args.coarse_inverse is not None:
+            mx.mx_set_tuning(P.h, mx.MX_TUNE_COARSE_INVERSE, args.coarse_inverse)
         if args.weighted:
             mx.mx_set_weighted_gmres(P.h, 1)
         if args.precond != "as":
@@ -752,6 +754,9 @@ def main():
                          "updates")
     ap.add_argument("--lu-grid", type=int, default=None,
                     help="CTAs of the persistent local LU (0: one per subdomain); default: library default")
+    ap.add_argument("--coarse-inverse", type=int, default=None, choices=[0, 1, 2],
+                    help="coarse solve: 1 explicit inverse with a tensor-core product, 2 the same on CUDA cores, "
+                         "0 band sweeps; default: library default")
     ap.add_argument("--dots", type=int, default=None, choices=[0, 1],
                     help="second Gram-Schmidt pass: 0 staged kernel, 1 lane-parallel; default: library default")
     ap.add_argument("--local-tensor", type=int, default=None, choices=[0, 1],

@@ -158,8 +158,9 @@ MX_API int mx_set_dense_local(mx_handle h, int dense);
 #define MX_TUNE_LOCAL_TENSOR 4
 /*   MX_TUNE_COARSE_INVERSE: coarse solve of the MX_MIXED form; 1 (default) = mx_factor
  *   forms the explicit c64 inverse of A^0 (n_c^2 complex entries, by band sweeps on the
- *   identity) and every apply is one dense product, 0 = band triangular sweeps. Takes
- *   effect at the next mx_factor. */
+ *   identity) and every apply is one dense product on the tcgen05 tensor cores (three TF32
+ *   products per term; CUDA cores for an odd n_c), 2 = the same inverse with the product on
+ *   the CUDA cores, 0 = band triangular sweeps. 0 takes effect at the next mx_factor. */
 #define MX_TUNE_COARSE_INVERSE 5
 /*   MX_TUNE_LU_GRID: CTAs of the persistent local LU (MX_TUNE_LU_TENSOR 0 or 2), each taking
  *   subdomains blockIdx, blockIdx + grid, ...; 0 (default) = one CTA per subdomain. A grid

@@ -62,7 +62,7 @@ def candidates(info, cfg, name, allow_reduced=False):
         # measures it at the tuning batch's count, which the cache key records
         return [0, 1] if mixed else []
     if name == "coarse_inverse":
-        return [1, 0] if (mixed and coarse) else []
+        return [1, 2, 0] if (mixed and coarse) else []
     if name == "local_tensor":
         return [1, 0] if mixed else []
     if name == "local_rhs_group":

@@ -15,7 +15,7 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmxas.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
-SOURCES = ["common", "mesh", "assemble", "local", "coarse", "krylov", "krylov_df", "api", "noalloc", "lu_tc", "lu_fused", "local_tc", "serve"]
+SOURCES = ["common", "mesh", "assemble", "local", "coarse", "krylov", "krylov_df", "api", "noalloc", "lu_tc", "lu_fused", "coarse_tc", "local_tc", "serve"]
 
 
 def nvcc():

@@ -319,7 +319,7 @@ int mx_set_tuning(mx_handle h, int key, int value) {
       MX_REQUIRE(value >= 0 && value <= 65536, MX_EINVAL, "LU grid must be in 0..65536");
       P.tune_lu_grid = value;
     } else if (key == MX_TUNE_COARSE_INVERSE) {
-      MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "coarse inverse mode must be 0 or 1");
+      MX_REQUIRE(value >= 0 && value <= 2, MX_EINVAL, "coarse inverse mode must be 0, 1 or 2");
       P.tune_coarse_inverse = value;
     } else if (key == MX_TUNE_DOTS) {
       MX_REQUIRE(value == 0 || value == 1, MX_EINVAL, "dots mode must be 0 or 1");

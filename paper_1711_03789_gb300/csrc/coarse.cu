@@ -628,6 +628,17 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
     }
     MX_CHECK_LAUNCH();
   }
+  if (dense && P.tune_coarse_inverse != 2 && nc % 2 == 0) {
+    // tensor cores (3 x TF32): column pairs of X start 16-byte aligned when n_c is even
+    ProfScope ps(K_COARSE_SWEEP, s, 1, 8.0 * (double)nc * nc + 8.0 * nc * nrhs * 2.0, 8.0 * (double)nc * nc * nrhs);
+    float2* part = nullptr;
+    int ks = 0;
+    if (coarse_dense_tc(P, rin, nrhs, part, ks)) {
+      MX_LAUNCH(k_coarse_sum<<<grid_for(nc * nrhs, 256), 256, 0, s>>>(nc * nrhs, ks, part, rf));
+      MX_CHECK_LAUNCH();
+      return;
+    }
+  }
   if (dense) {
     // split the rows of X among ks chunks so that the grid fits in one wave of two blocks
     // per SM (a second, nearly empty wave would double the time)

@@ -222,6 +222,11 @@ void local_solves(Problem& P, const void* v, int vtype, void* loc, int nrhs);
 // X = (A^0)^{-1} from the c64 coarse band factors (row-major n_c x n_c, c64)
 void coarse_inverse(Problem& P, float2* X);
 
+// ---- coarse_tc.cu -------------------------------------------------------------------
+// part[ks][i][r] = split ks of sum_j X[i][j] rin[j][r] on the tensor cores (3 x TF32), X the
+// explicit c64 coarse inverse; sets the split count. false (nothing launched) for an odd n_c.
+bool coarse_dense_tc(Problem& P, const float2* rin, int nrhs, float2*& part, int& ks);
+
 // ---- local_tc.cu --------------------------------------------------------------------
 // panel images of the c64 factors for the tensor-core solves (after factor_local)
 void build_panels(Problem& P);

@@ -473,22 +473,26 @@ def test_mixed_gmres_tight_tolerance():
 def test_coarse_inverse_apply(n, cm, nrhs):
     """Mixed-form coarse solve with the explicit c64 inverse of A^0 against the oracle's
     pivoted sparse coarse solve (levels = 2: coarse correction only), and against the band
-    sweeps of the same c64 factors. The inverse carries the rounding of the c64 factors and
-    an FP32 dense product: the bound of the other c64 preconditioner parts (MIXED_APPLY_TOL)."""
+    sweeps of the same c64 factors. The inverse carries the rounding of the c64 factors, and
+    the dense product runs on the tensor cores (mode 1: three TF32 products per term; n_c = 6,130
+    with one group of 16 right-hand sides, n_c = 316 with a group of 16 and one of 4; n_c = 665
+    is odd and takes the CUDA cores) or on the CUDA cores (mode 2, FP32): the bound of the other
+    c64 preconditioner parts (MIXED_APPLY_TOL)."""
     k, xi = 6.0, 36.0
     O = OracleProblem(n, k, 0.0, xi, 5, 1, coarse_m=cm)
     O.factor()
     v = inputs.random_complex(21, (nrhs, O.n_dof))
     ze = O.dd.apply(v.T, levels=(0,)).T
     out = {}
-    for mode in (1, 0):
+    for mode in (1, 2, 0):
         with _handle(n, k, 0.0, xi, 5, 1, cm=cm, prec=mx.MX_MIXED) as P:
             mx.mx_set_tuning(P.h, mx.MX_TUNE_COARSE_INVERSE, mode)
             P.factor()
             out[mode] = P.precond(v, levels=2)
-    for mode in (1, 0):
+    for mode in (1, 2, 0):
         assert_close(out[mode], ze, MIXED_APPLY_TOL, what=f"coarse apply, inverse={mode}")
     assert_close(out[1], out[0], MIXED_APPLY_TOL, what="inverse against band sweeps")
+    assert_close(out[1], out[2], MIXED_APPLY_TOL, what="tensor-core against CUDA-core dense product")
 
 
 @pytest.mark.parametrize("prec", [mx.MX_PLAIN_FP64, mx.MX_MIXED])
