@@ -167,13 +167,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_band_lu_tc(BandBatch B, float2* 
         __syncthreads();
         for (int i = k + 1 + tid; i < kb; i += THREADS) s[i][k] = cmul(s[i][k], inv);
         __syncthreads();
-        const int w = kb - k - 1;
-        for (int t = tid; t < w * w; t += THREADS) {
-          const int i = k + 1 + t % w, j = k + 1 + t / w;
-          float2 v = s[i][j];
-          cfms(v, s[i][k], s[k][j]);
-          s[i][j] = v;
-        }
+        // trailing update: warp = column, lane = row (no division by the trailing size)
+        const int i = k + 1 + lane;
+        if (i < kb)
+          for (int j = k + 1 + warp; j < kb; j += THREADS / 32) {
+            float2 v = s[i][j];
+            cfms(v, s[i][k], s[k][j]);
+            s[i][j] = v;
+          }
         __syncthreads();
       }
       // L X = I (unit lower, rows top to bottom) and U Y = I (rows bottom to top) by row
@@ -313,7 +314,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_band_lu_tc(BandBatch B, float2* 
       // [128, 256) of the slot); false if the tensor cores did not finish in time
       auto epilogue = [&](int q) -> bool {
         const int sl = q & 1;
-        if (!wait_bar(sl)) return false;
         const int i0 = k1 + FT * (q / nt), j0 = k1 + FT * (q % nt);
         // warp w: TMEM lanes 32 (w % 4) .. (its rows), complex columns 32 (w / 4) .. of the tile
         const int lg = warp & 3, cq = warp >> 2;
@@ -326,11 +326,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_band_lu_tc(BandBatch B, float2* 
         const int64_t st = ld - 1;
         float2* rp = A + bidx(off, ld, b, row_ok ? i : lim - 1, jb);
         const int nv = row_ok ? min(32, lim - jb) : 0;  // entries of the row inside the window
+        // the first round's loads are in flight while the tile's products finish
+        float2 x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = u < nv ? rp[u * st] : make_float2(0.f, 0.f);
+        if (!wait_bar(sl)) return false;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          float2 x[16];
+          if (h == 1) {
 #pragma unroll
-          for (int u = 0; u < 16; ++u) x[u] = 16 * h + u < nv ? rp[(16 * h + u) * st] : make_float2(0.f, 0.f);
+            for (int u = 0; u < 16; ++u) x[u] = 16 + u < nv ? rp[(16 + u) * st] : make_float2(0.f, 0.f);
+          }
           uint32_t vr[16], vi[16];
           tc::tmem_ld16(base + 16 * h, vr);
           tc::tmem_ld16(base + 128 + 16 * h, vi);
