@@ -72,9 +72,11 @@ typedef struct { int n_cells; } mx_coarse_desc;
 
 /* Precision of the preconditioner and of the Krylov process.
  *   MX_PLAIN_FP64: FP64 throughout (c128 local and coarse factors, FP64 Krylov kernels).
- *   MX_MIXED: c64 local factors (local solves on tcgen05 TF32 with the right-hand-side block
- *     as a TF32 hi + lo pair, or FP32 CUDA cores); c64 coarse band LU and its explicit c64
- *     inverse; FP32 scatter. The Krylov basis V, the products A z_j and both classical
+ *   MX_MIXED: c64 local factors (from a tcgen05 LU with three TF32 products per term; local
+ *     solves on tcgen05 TF32 with the right-hand-side block as a TF32 hi + lo pair, or FP32
+ *     CUDA cores); c64 coarse band LU and its explicit c64 inverse, applied on tcgen05 with
+ *     three TF32 products per term; FP32 scatter; the load vector's quadrature in
+ *     double-float arithmetic. The Krylov basis V, the products A z_j and both classical
  *     Gram-Schmidt passes use double-float arithmetic (pairs of FP32 values, about 48
  *     significant bits; the first pass forms its products from the c64 rounding of V).
  *     FP64 is kept for H, the Givens rotations, the least-squares solve, the solution x
