@@ -244,6 +244,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_band_lu_tc(BandBatch B, float2* 
           put4(dst, PLANE, tc::kmaj(t % FT, 4 * (t / FT), F_LBO, F_SBO), v[it2], SPLIT == 3);
         }
       };
+      // the same tile staged by warps 1-15 only (warp 0 is issuing products meanwhile)
+      constexpr int SW = THREADS - 32;
+      constexpr int ITEMS_W = (FT * (NB / 4) + SW - 1) / SW;
+      auto stage_w = [&](unsigned char* dst, int r0, bool rows) {
+        float2 v[ITEMS_W][4];
+#pragma unroll
+        for (int it2 = 0; it2 < ITEMS_W; ++it2) {
+          const int t = tid - 32 + SW * it2;
+          const int e = r0 + t % FT, g = t / FT;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int kc = 4 * g + u, k = k0 + kc;
+            v[it2][u] = make_float2(0.f, 0.f);
+            if (t < FT * (NB / 4) && kc < kb && e < lim && e - k <= b)
+              v[it2][u] = rows ? A[bidx(off, ld, b, e, k)] : A[bidx(off, ld, b, k, e)];
+          }
+        }
+#pragma unroll
+        for (int it2 = 0; it2 < ITEMS_W; ++it2) {
+          const int t = tid - 32 + SW * it2;
+          if (t < FT * (NB / 4)) put4(dst, PLANE, tc::kmaj(t % FT, 4 * (t / FT), F_LBO, F_SBO), v[it2], SPLIT == 3);
+        }
+      };
       auto wait_bar = [&](int q) -> bool {
         const bool ok = tc::mbar_wait(mb[q], par[q], F_WAIT);
         par[q] ^= 1u;
@@ -252,12 +275,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_band_lu_tc(BandBatch B, float2* 
       };
 
       // ---- 2. panels on the tensor cores: tiles p < nt are rows of L21, nt <= p < 2 nt
-      // columns of U12; two tiles per round (buf[0], buf[1]), accumulators at TMEM columns 64 p
+      // columns of U12, accumulators at TMEM columns 64 p. A two-buffer pipeline: while thread 0
+      // issues the products of tile p (buf[p & 1]), warps 1-15 stage tile p + 1 into the other
+      // buffer once the products of tile p - 1, which read it, are done (mbarrier p & 1, waited
+      // by every thread once per tile, so the per-thread parities stay in step)
       const int nt = (span + FT - 1) / FT;
       const int np = 2 * nt;
-      for (int p0 = 0; p0 < np; p0 += 2) {
-        for (int p = p0; p < min(np, p0 + 2); ++p)
-          stage(buf[p - p0], k1 + FT * (p < nt ? p : p - nt), p < nt);
+      auto panel_row = [&](int p) { return k1 + FT * (p < nt ? p : p - nt); };
+      stage(buf[0], panel_row(0), true);
+      for (int p = 0; p < np; ++p) {
         tc::fence_proxy_async();
         tc::fence_before();
         if (__syncthreads_or(my_fail)) {
@@ -266,16 +292,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_band_lu_tc(BandBatch B, float2* 
         }
         tc::fence_after();
         if (tid == 0) {
-          for (int p = p0; p < min(np, p0 + 2); ++p) {
-            const uint32_t d = tmem + (uint32_t)(64 * p);
-            cgemm<SPLIT>(d, d + 32, buf_s[p - p0], PLANE, buf_s[2] + (p < nt ? 0 : 4 * IPLANE), IPLANE,
-                         tc::idesc_tf32(FT, NB));
-          }
-          tc::mma_commit(mb[2]);
+          const uint32_t d = tmem + (uint32_t)(64 * p);
+          cgemm<SPLIT>(d, d + 32, buf_s[p & 1], PLANE, buf_s[2] + (p < nt ? 0 : 4 * IPLANE), IPLANE,
+                       tc::idesc_tf32(FT, NB));
+          tc::mma_commit(mb[p & 1]);
         }
-        if (!wait_bar(2)) my_fail = 1;  // the buffers are restaged in the next round
+        if (p >= 1 && !wait_bar((p - 1) & 1)) my_fail = 1;  // tile p - 1 done: its buffer is free
+        if (warp > 0 && p + 1 < np && !my_fail) stage_w(buf[(p + 1) & 1], panel_row(p + 1), p + 1 < nt);
       }
       if (failed) break;
+      if (!wait_bar((np - 1) & 1)) my_fail = 1;  // the last tile's products
       // epilogue of the panels: warp w takes TMEM lanes 32 (w % 4) of the tiles p = w / 4 (mod 4)
       {
         const int lg = warp & 3;
