@@ -324,6 +324,13 @@ MX_API int mx_get_coarse_restriction(mx_handle h, int32_t* rowptr, int32_t* col,
 /* y = A_{xi_prob} x (FP64), x and y [nrhs][n_dof] c128, host or device. */
 MX_API int mx_spmv(mx_handle h, const void* x, void* y, int nrhs);
 
+/* y = A_{xi_prob} x as the MX_MIXED Krylov process forms A z_j (Sec. 6.1, flexible GMRES):
+ * x rounded to c64, each product and the sums of a row in double-float arithmetic (the
+ * coefficients of K - (k^2 + i xi) M split into FP32 pairs), y the c128 value hi + lo of each
+ * double-float result. Right-hand sides in pairs for an even nrhs, one at a time otherwise,
+ * as in the solver. Same layouts as mx_spmv; any handle. For verification of that kernel. */
+MX_API int mx_spmv_mixed(mx_handle h, const void* x, void* y, int nrhs);
+
 /* z = B^{-1} v (Eq. 3.4) with the factored preconditioner; levels: bit 0 = local
  * solves (l >= 1), bit 1 = coarse solve (l = 0). v, z [nrhs][n_dof] c128. */
 MX_API int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels);

@@ -15,7 +15,7 @@ from ._lib import (  # noqa: F401
     MX_PLAIN_FP64, MX_MIXED, MxError, lib, lib_path,
     mx_version, mx_last_error, mx_build_problem, mx_set_xi_prob, mx_set_stream, mx_set_dense_local,
     mx_factor, mx_load_vector, mx_solve, mx_num_dofs, mx_info, mx_timings, mx_destroy,
-    mx_get_mesh, mx_get_subdomains, mx_get_csr, mx_get_coarse_restriction, mx_spmv, mx_precond,
+    mx_get_mesh, mx_get_subdomains, mx_get_csr, mx_get_coarse_restriction, mx_spmv, mx_spmv_mixed, mx_precond,
     mx_get_local, mx_set_allocator, use_torch_allocator,
     mx_launch_count, mx_profile, mx_profile_read, mx_profile_name, mx_dots, mx_dots_noalloc,
     mx_set_preconditioner, mx_set_weighted_gmres, MX_PREC_AS, MX_PREC_RAS, MX_PREC_HRAS, MX_PREC_ADEF1,

@@ -86,6 +86,7 @@ _sig = {
     "mx_get_boundary_mass": (C.c_int, [H, C.c_int, P]),
     "mx_get_coarse_restriction": (C.c_int, [H, P, P, P]),
     "mx_spmv": (C.c_int, [H, P, P, C.c_int]),
+    "mx_spmv_mixed": (C.c_int, [H, P, P, C.c_int]),
     "mx_precond": (C.c_int, [H, P, P, C.c_int, C.c_int]),
     "mx_get_local": (C.c_int, [H, C.c_int, P]),
     "mx_dots": (C.c_int, [P, P, C.c_int64, C.c_int, C.c_int, P, C.c_void_p]),
@@ -313,6 +314,16 @@ def mx_spmv(h, x, y=None):
     if y is None:
         y = np.empty_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
     _check(lib.mx_spmv(h, _ptr(x), _ptr(y), nrhs))
+    return y
+
+
+def mx_spmv_mixed(h, x, y=None):
+    """y = A x as the mixed form's Krylov process computes it (c64 x, double-float sums)."""
+    n = mx_num_dofs(h)
+    nrhs = _nrhs(x, n)
+    if y is None:
+        y = np.empty_like(x) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+    _check(lib.mx_spmv_mixed(h, _ptr(x), _ptr(y), nrhs))
     return y
 
 

@@ -572,6 +572,29 @@ int mx_spmv(mx_handle h, const void* x, void* y, int nrhs) {
   });
 }
 
+int mx_spmv_mixed(mx_handle h, const void* x, void* y, int nrhs) {
+  return guard([&] {
+    MX_REQUIRE(h && x && y && nrhs >= 1, MX_EINVAL, "bad arguments");
+    auto& P = *reinterpret_cast<Problem*>(h);
+    const int64_t n = P.fine.n_dof, cnt = n * nrhs;
+    const size_t bytes = (size_t)cnt * sizeof(double2);
+    DevView in(x, bytes, true, P.stream);
+    DevView out(y, bytes, false, P.stream);
+    DevBuf<double2> a((size_t)cnt), b((size_t)cnt);
+    DevBuf<float2> z((size_t)cnt);
+    DevBuf<float4> w((size_t)cnt);
+    MX_LAUNCH(k_to_internal<<<grid_for(cnt, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, (const double2*)in.p, a.p));
+    MX_CHECK_LAUNCH();
+    c128_to_c64(a.p, z.p, cnt, P.stream);
+    spmv_df(P, z.p, w.p, nrhs, P.stream);
+    df_to_c128(w.p, b.p, cnt, P.stream);
+    MX_LAUNCH(k_to_user<<<grid_for(cnt, 256), 256, 0, P.stream>>>(n, nrhs, 0, nrhs, b.p, (double2*)out.p));
+    MX_CHECK_LAUNCH();
+    out.copy_out(bytes, P.stream);
+    MX_CUDA(cudaStreamSynchronize(P.stream));
+  });
+}
+
 int mx_precond(mx_handle h, const void* v, void* z, int nrhs, int levels) {
   return guard([&] {
     MX_REQUIRE(h && v && z && nrhs >= 1 && nrhs <= 32 && levels >= 1 && levels <= 3, MX_EINVAL, "bad arguments");

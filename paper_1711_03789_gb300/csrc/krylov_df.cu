@@ -795,6 +795,26 @@ void spmv_df_c128(Problem& P, double xi, const float2* z, double2* y, int nrhs, 
   MX_CHECK_LAUNCH();
 }
 
+// c128 -> c64 (round to nearest) and complex double-float -> c128 (hi + lo), for mx_spmv_mixed
+__global__ void k_c128_round_c64(int64_t count, const double2* __restrict__ a, float2* __restrict__ b) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    b[t] = make_float2(__double2float_rn(a[t].x), __double2float_rn(a[t].y));
+}
+__global__ void k_df_to_c128(int64_t count, const float4* __restrict__ w, double2* __restrict__ y) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = w[t];
+    y[t] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  }
+}
+void c128_to_c64(const double2* a, float2* b, int64_t count, cudaStream_t s) {
+  MX_LAUNCH(k_c128_round_c64<<<grid_for(count, 256), 256, 0, s>>>(count, a, b));
+  MX_CHECK_LAUNCH();
+}
+void df_to_c128(const float4* w, double2* y, int64_t count, cudaStream_t s) {
+  MX_LAUNCH(k_df_to_c128<<<grid_for(count, 256), 256, 0, s>>>(count, w, y));
+  MX_CHECK_LAUNCH();
+}
+
 // ---- host launchers ----------------------------------------------------------------------
 void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s) {
   const float4* coef = coef_df(P, P.xi_prob, 0, s);

@@ -269,6 +269,9 @@ void free_workspace(Problem& P);
 
 // ---- krylov_df.cu: double-float Krylov kernels of the mixed form --------------------
 void spmv_df(Problem& P, const float2* z, float4* w, int nrhs, cudaStream_t s);
+// conversions around spmv_df for verification: c128 -> c64 (nearest), double-float -> c128
+void c128_to_c64(const double2* a, float2* b, int64_t count, cudaStream_t s);
+void df_to_c128(const float4* w, double2* y, int64_t count, cudaStream_t s);
 // y = A_xi z, z c64, y c128 (double-float accumulation)
 void spmv_df_c128(Problem& P, double xi, const float2* z, double2* y, int nrhs, cudaStream_t s);
 // The basis of the mixed form is two c64 planes: Vh [m+1][n][nrhs] (c64 rounding) and Vl

@@ -55,6 +55,9 @@ class Problem:
     def spmv(self, x, y=None):
         return L.mx_spmv(self.h, x, y)
 
+    def spmv_mixed(self, x, y=None):
+        return L.mx_spmv_mixed(self.h, x, y)
+
     def precond(self, v, z=None, levels=3):
         return L.mx_precond(self.h, v, z, levels)
 

@@ -44,6 +44,7 @@ int main(void) {
   mx_problem_info info;
   expect(mx_info(NULL, &info) == MX_EINVAL, "mx_info(NULL)");
   expect(mx_factor(NULL) == MX_EINVAL, "mx_factor(NULL)");
+  expect(mx_spmv_mixed(NULL, NULL, NULL, 1) == MX_EINVAL, "mx_spmv_mixed(NULL)");
   expect(mx_set_tuning(NULL, MX_TUNE_LOCAL_TENSOR, 1) == MX_EINVAL, "mx_set_tuning(NULL)");
   expect(mx_set_preconditioner(NULL, MX_PREC_RAS) == MX_EINVAL, "mx_set_preconditioner(NULL)");
   expect(mx_set_growth_limit(NULL, 10.0) == MX_EINVAL, "mx_set_growth_limit(NULL)");

@@ -130,6 +130,29 @@ def test_spmv(n, nrhs, xi):
     assert np.array_equal(y, yd)
 
 
+@pytest.mark.parametrize("n,nrhs,xi", [(5, 1, 0.0), (10, 3, 3.0), (10, 2, 1.0), (12, 16, -2.0)])
+def test_spmv_mixed(n, nrhs, xi):
+    """The double-float operator product of the mixed form (one right-hand side per thread for
+    an odd count, pairs for an even one, as in the solver) against the oracle's FP64 operator on
+    the same c64-rounded vectors, element by element. Bound per entry: each product carries the
+    coefficient's split error (2^-48) and the compensated row sum a few units of 2^-48 of every
+    term, so |y - A x|_i <= 2^-44 (|A| |x|)_i; the two FP64 assemblies differ by rounding only."""
+    k = 3.0
+    x = inputs.random_complex(17, (nrhs, KuhnMesh(n).n_dof))
+    x64 = x.astype(np.complex64).astype(np.complex128)
+    with _handle(n, k, xi, 1.0, 5, 1, prec=mx.MX_MIXED) as P:
+        y = P.spmv_mixed(x)
+        yd = P.spmv_mixed(torch.from_numpy(x).cuda()).cpu().numpy()
+    Ko, Mo = fem.assemble_KM(KuhnMesh(n))
+    A = fem.a_xi(Ko, Mo, k, xi).tocsr()
+    ye = (A @ x64.T).T
+    bound = 2.0 ** -44 * (abs(A) @ np.abs(x64).T).T
+    worst = (np.abs(y - ye) / bound).max()
+    print(f"mixed SpMV n={n} nrhs={nrhs}: max |error| / bound = {worst:.3f}")
+    assert worst <= 1.0
+    assert np.array_equal(y, yd)
+
+
 @pytest.mark.parametrize("prec", [mx.MX_PLAIN_FP64, mx.MX_MIXED])
 def test_local_minor_and_factor(prec):
     n, k, xi = 10, 4.0, 4.0
