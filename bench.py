@@ -629,7 +629,7 @@ def serving_mix(args, nreq, loads, budget=None):
         return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)), wall_s=wall,
                     requests_per_s=len(reqs) / wall, rhs_per_s=rhs / wall, converged_rhs=conv, rhs=rhs,
                     batches=info["batches"], factorisations=info["factorisations"], evictions=info["evictions"],
-                    joined=info.get("joined", 0))
+                    joined=info.get("joined", 0), cached_bytes_at_end=info.get("cached_bytes", 0))
 
     reqs = [draw(i) for i in range(nreq)]
     closed = run(reqs, 0.0)

@@ -393,7 +393,9 @@ MX_API int mx_test_bounded_wait(mx_handle h, int limit, int blocks);
  * B^{-1} is built from A_{xi_prec} only, Sec. 6.2). A new factorisation is admitted when its
  * planned factor bytes plus the batch's Krylov workspace fit the budget after evicting idle
  * cached factorisations (least recently used first) and fit the device's free memory;
- * otherwise the request waits. */
+ * otherwise the batch waits, and while it waits no other batch starts and running batches
+ * admit no new requests, so the memory they hold comes free within their iteration limits.
+ * A waiting batch fails with MX_ENOMEM after 30 s in which no other batch held memory. */
 typedef struct mx_server_s* mx_server;
 
 typedef struct {
@@ -421,6 +423,7 @@ typedef struct {
   int64_t factorisations, evictions, completed, cached_bytes;
   int32_t cached_operators, pending;
   int64_t joined;          /* requests admitted into a batch that was already running */
+  int32_t waiting_for_memory; /* batches waiting for their factorisation to fit the budget */
 } mx_server_info;
 
 #define MX_PENDING 1       /* mx_server_poll without wait: result not ready yet */

@@ -433,7 +433,7 @@ class RequestTiming(C.Structure):
 class ServerInfo(C.Structure):
     _fields_ = [("batches", C.c_int64), ("factorisations", C.c_int64), ("evictions", C.c_int64),
                 ("completed", C.c_int64), ("cached_bytes", C.c_int64), ("cached_operators", C.c_int32),
-                ("pending", C.c_int32), ("joined", C.c_int64)]
+                ("pending", C.c_int32), ("joined", C.c_int64), ("waiting_for_memory", C.c_int32)]
 
 
 MX_PENDING = 1

@@ -19,7 +19,11 @@
 // - Admission: a new factorisation is admitted only if its local factors (band storage,
 //   planned before allocation) plus the Krylov workspace of the batch fit in the memory
 //   budget after evicting unused cached factorisations (least recently used first) and in
-//   the device's free memory; otherwise the request waits for memory to free up.
+//   the device's free memory; otherwise the batch waits for memory to free up. While a batch
+//   waits, no other batch starts and running batches admit no new requests, so the batches
+//   that hold memory finish within their own iteration limits and the waiting batch is not
+//   starved by continuous batching. It fails (MX_ENOMEM) only after 30 s in which no other
+//   batch held memory.
 // - Latency is measured per request from submit to completion on the host clock.
 #include <algorithm>
 #include <atomic>
@@ -109,6 +113,7 @@ struct Server {
   int device = 0;
   // statistics
   int64_t batches = 0, factorisations = 0, evictions = 0, completed = 0, joined = 0;
+  int mem_waiters = 0;  // batches waiting for their factorisation to fit the budget
 
   static bool same_batch(const Req& a, const Req& b) {
     return a.key == b.key && a.xi_prob == b.xi_prob && a.tol == b.tol && a.restart == b.restart &&
@@ -208,6 +213,7 @@ struct Server {
         }
         for (int64_t id : S.pending) {
           if (S.stop) break;  // the server is shutting down: pending requests are dropped
+          if (S.mem_waiters > 0) break;  // another batch waits for the memory this one holds
           Req* q = S.reqs[id].get();
           if (q->taken || !same_batch(*q, tmpl)) continue;
           int run = 0, start = -1;
@@ -252,6 +258,7 @@ struct Server {
       while (!stop) {
         batch.clear();
         for (int64_t id : pending) {
+          if (mem_waiters > 0) break;  // a batch waits for memory: it goes first
           Req* r = reqs[id].get();
           if (r->taken) continue;
           auto it = cache.find(r->key);
@@ -307,12 +314,22 @@ struct Server {
           // admission: memory budget (after evictions) and the device's free memory
           MX_REQUIRE(need <= budget, MX_ENOMEM,
                      "request needs " + std::to_string(need) + " bytes, more than the whole budget");
-          bool admitted = false;
-          for (int attempt = 0; attempt < 600 && !admitted; ++attempt) {
+          bool admitted = false, waiting = false;
+          for (int idle = 0; !admitted && idle < 600;) {  // idle: 50 ms waits with no other batch holding memory
+            bool held = false;
             {
               std::lock_guard<std::mutex> g(mu);
+              if (stop) break;
               admitted = make_room(need);
-              if (admitted) cached_bytes += need;
+              if (admitted) {
+                cached_bytes += need;
+                entry->bytes = need;
+              }
+              for (const auto& e : cache) held = held || (e.second.busy && e.second.bytes > 0 && !(e.first == key));
+              if (!admitted && !waiting) {
+                waiting = true;
+                ++mem_waiters;
+              }
             }
             size_t fr = 0, tot = 0;
             // the device's free memory says something only when the library allocates from the
@@ -320,9 +337,24 @@ struct Server {
             if (admitted && !allocator_hooked() && cudaMemGetInfo(&fr, &tot) == cudaSuccess && (int64_t)fr < need) {
               std::lock_guard<std::mutex> g(mu);
               cached_bytes -= need;
+              entry->bytes = 0;
               admitted = false;
+              if (!waiting) {
+                waiting = true;
+                ++mem_waiters;
+              }
             }
-            if (!admitted) std::this_thread::sleep_for(std::chrono::milliseconds(50));
+            if (!admitted) {
+              idle = held ? 0 : idle + 1;
+              std::this_thread::sleep_for(std::chrono::milliseconds(50));
+            }
+          }
+          if (waiting) {
+            {
+              std::lock_guard<std::mutex> g(mu);
+              --mem_waiters;
+            }
+            cv_work.notify_all();  // batches held back while this one waited may start
           }
           MX_REQUIRE(admitted, MX_ENOMEM, "request does not fit the memory budget");
           charged = need;
@@ -498,6 +530,7 @@ MX_API int mx_server_stats(mx_server sv, mx_server_info* out) {
   out->cached_bytes = S->cached_bytes;
   out->cached_operators = (int32_t)S->cache.size();
   out->pending = (int32_t)S->pending.size();
+  out->waiting_for_memory = S->mem_waiters;
   out->joined = S->joined;
   return MX_OK;
 }

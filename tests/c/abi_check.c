@@ -128,6 +128,7 @@ int main(void) {
   OFF(mx_server_info, cached_bytes);
   OFF(mx_server_info, cached_operators);
   OFF(mx_server_info, pending);
+  OFF(mx_server_info, waiting_for_memory);
   OFF(mx_server_info, joined);
 
   printf("failures %d\n", failures);

@@ -122,3 +122,54 @@ def test_request_joins_a_running_batch_with_the_same_result():
             assert abs(a["iterations"] - b["iterations"]) <= 1, (st_mix, st_alone)
     finally:
         mx.mx_server_destroy(s)
+
+
+def test_batch_waiting_for_memory_goes_first():
+    """Under a budget that holds one of two operators, a batch of the second waits for memory
+    while a long batch of the first runs. While it waits, a request of the first operator does
+    not join the running batch (it would keep the memory held). It runs after the waiting batch
+    instead, on a new factorisation: three factorisations, two evictions, nothing joined."""
+    import time
+
+    def long_req(s, seed, nrhs, max_it):
+        # unreachable tolerance: the batch runs its full iteration count
+        c, p = inputs.bump_batch(seed, nrhs)
+        return mx.mx_server_submit(s, 30, 15.0, 225.0, 225.0, c, p, core_cells=5, overlap_cells=1, coarse_cells=6,
+                                   precision=mx.MX_MIXED, tol=1e-15, restart=10, max_it=max_it)
+
+    nd30, nd10 = _n_dof(30), _n_dof(10)
+    s0 = mx.mx_server_create(8 << 30, workers=1)
+    try:
+        mx.mx_server_poll(s0, long_req(s0, 41, 2, 10), nd30, 2)  # same slots and restart: same bytes
+        need_a = mx.mx_server_stats(s0)["cached_bytes"]
+        x_b, st_b, _, rc = mx.mx_server_poll(s0, _req(s0, 10, 6.0, 6.0, 6.0, seed=42, nrhs=1, tol=1e-8), nd10, 1)
+        need_b = mx.mx_server_stats(s0)["cached_bytes"] - need_a
+        assert rc == mx.MX_OK and 0 < need_b < need_a, (need_a, need_b)
+    finally:
+        mx.mx_server_destroy(s0)
+    s = mx.mx_server_create(need_a + need_b // 2, workers=3)
+    try:
+        t_long = long_req(s, 41, 2, 3000)
+        # the long batch holds its memory once admitted (taken from the queue is not enough: a
+        # request submitted before the admission could still take the memory first)
+        t0 = time.perf_counter()
+        while mx.mx_server_stats(s)["cached_bytes"] < need_a and time.perf_counter() - t0 < 30:
+            time.sleep(0.001)
+        assert mx.mx_server_stats(s)["cached_bytes"] == need_a
+        t_b = _req(s, 10, 6.0, 6.0, 6.0, seed=42, nrhs=1, tol=1e-8)
+        t0 = time.perf_counter()
+        while mx.mx_server_stats(s)["waiting_for_memory"] == 0 and time.perf_counter() - t0 < 60:
+            time.sleep(0.001)
+        assert mx.mx_server_stats(s)["waiting_for_memory"] == 1, "the long batch ended before the second waited"
+        t_a2 = long_req(s, 43, 1, 3000)  # same operator and settings as the running batch
+        x, st, _, rc = mx.mx_server_poll(s, t_b, nd10, 1)
+        assert rc == mx.MX_OK and st[0]["converged"]
+        assert_close(x, x_b, 1e-9, what="request that waited for memory against alone")
+        _, st_long, _, _ = mx.mx_server_poll(s, t_long, nd30, 2)
+        _, st_a2, _, _ = mx.mx_server_poll(s, t_a2, nd30, 1)
+        assert all(v["iterations"] == 3000 for v in st_long + st_a2), (st_long, st_a2)
+        info = mx.mx_server_stats(s)
+        assert info["joined"] == 0 and info["factorisations"] == 3 and info["evictions"] == 2, info
+        assert info["waiting_for_memory"] == 0 and info["completed"] == 3 and info["batches"] == 3, info
+    finally:
+        mx.mx_server_destroy(s)
