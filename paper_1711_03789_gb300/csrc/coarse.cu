@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_coarse_lu_coop(int n, int b, int ld, T2
 template <typename T2>
 static void coarse_lu_coop(T2* A, int n, int b, int ld, int32_t* status, cudaStream_t s) {
   const size_t smem = std::max(sizeof(T2) * LU_NB * (LU_NB + 1), sizeof(T2) * 2 * LU_NB * 65);
-  static bool configured = false;
+  static std::atomic<bool> configured{false};
   if (!configured) {
     MX_CUDA(cudaFuncSetAttribute(k_coarse_lu_coop<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = true;

@@ -189,7 +189,7 @@ bool coarse_dense_tc(Problem& P, const float2* rin, int nrhs, float2*& part, int
   const int64_t nc = P.n_c;
   if (nc % 2 != 0 || nc > (1 << 30) / CT_M) return false;
   cudaStream_t s = P.stream;
-  static bool configured = false;
+  static std::atomic<bool> configured{false};
   if (!configured) {
     MX_CUDA(cudaFuncSetAttribute(k_coarse_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, CT_SMEM));
     configured = true;

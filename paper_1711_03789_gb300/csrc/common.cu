@@ -128,14 +128,16 @@ void prof_read(double* ms, int64_t* launches, double* bytes, double* flops) {
 }
 
 int sm_count() {
-  static int cached = 0;
-  if (!cached) {
+  static std::atomic<int> cached{0};  // read by the server's worker threads too
+  int v = cached.load();
+  if (!v) {
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-    if (cached <= 0) cached = 1;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+    cached.store(v);
   }
-  return cached;
+  return v;
 }
 
 // ---- exclusive scan -----------------------------------------------------------------

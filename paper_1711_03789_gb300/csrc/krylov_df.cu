@@ -835,14 +835,14 @@ template <int RP>
 static void dots_rp(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2* Vh, const float2* Vl,
                     const float4* w, const int32_t* active, double2* hpart, cudaStream_t s, const float4* extra) {
   const size_t smem = (size_t)8 * DOTS_IC * RP * sizeof(float4);
-  static bool configured = false;
+  static std::atomic<bool> configured{false};
   if (!configured) {
     MX_CUDA(cudaFuncSetAttribute(k_dots_df<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = true;
   }
   if constexpr (RP >= 2) {
     if (nrhs % 2 == 0) {
-      static bool configured2 = false;
+      static std::atomic<bool> configured2{false};
       if (!configured2) {
         MX_CUDA(cudaFuncSetAttribute(k_dots_df2<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured2 = true;
@@ -859,7 +859,7 @@ int dots_df(int nblk, int64_t n, int nrhs, int nvec, int with_norm, const float2
   ProfScope ps(K_DOTS, s, 1, 16.0 * (nvec + 1) * (double)n * nrhs, 8.0 * (nvec + with_norm) * (double)n * nrhs);
   if (timeout && !extra && !with_norm && (nrhs == 2 || nrhs == 4 || nrhs == 8 || nrhs == 16 || nrhs == 32)) {
     const size_t smem = (size_t)DS_STAGES * DS_STAGE_BYTES;
-    static bool configured = false;
+    static std::atomic<bool> configured{false};
     if (!configured) {
       MX_CUDA(cudaFuncSetAttribute(k_dots_df_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       configured = true;
@@ -883,7 +883,7 @@ template <int RP>
 static void dots_c64_rp(int nblk, int64_t n, int nrhs, int nvec, const float2* Vh, const float4* w,
                         const int32_t* active, double2* hpart, cudaStream_t s) {
   const size_t smem = (size_t)8 * DOTS_IC * RP * sizeof(double2);
-  static bool configured = false;
+  static std::atomic<bool> configured{false};
   if (!configured) {
     MX_CUDA(cudaFuncSetAttribute(k_dots_c64<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = true;

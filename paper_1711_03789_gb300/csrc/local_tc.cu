@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_local_solve_tc(TcArgs a) {
 template <int G>
 static void launch_tc(const TcArgs& a, int n_sub, cudaStream_t s, double alg_bytes, double alg_flops) {
   const size_t smem = TcCfg<G>::SMEM;
-  static bool configured = false;
+  static std::atomic<bool> configured{false};
   if (!configured) {
     MX_CUDA(cudaFuncSetAttribute(k_local_solve_tc<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = true;

@@ -422,7 +422,7 @@ bool band_lu_fused_fits(int max_span) { return max_span <= MAX_SPAN; }
 void band_lu_fused(const BandBatch& B, float2* A, const int64_t* doff, float2* dinv, int split, int grid,
                    int32_t* status, cudaStream_t s, double bytes, double flops) {
   const int nblk = grid > 0 ? std::min(grid, B.count) : B.count;
-  static bool attr1 = false, attr3 = false;
+  static std::atomic<bool> attr1{false}, attr3{false};
   ProfScope ps(K_LU_UPDATE, s, 1, bytes, flops);
   if (split == 3) {
     if (!attr3) {

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256, 1) k_lu_update_tc(BandBatch B, float2* A,
 void lu_update_tc(const BandBatch& B, float2* A, int k0, int max_span, int split, int32_t* status, cudaStream_t s) {
   const int tr = (max_span + TM - 1) / TM, tc = (max_span + TNC - 1) / TNC;
   const int smem = (split == 3 ? 4 : 2) * TILE_BYTES;
-  static bool attr1 = false, attr3 = false;
+  static std::atomic<bool> attr1{false}, attr3{false};
   if (split == 3) {
     if (!attr3) {
       MX_CUDA(cudaFuncSetAttribute(k_lu_update_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
