@@ -320,38 +320,65 @@ __global__ void k_coarse_restrict(int64_t nc, int64_t n, int nrhs, const int32_t
   }
 }
 
+// entry idx of the vector v read by the restriction: VT 0 c128, 1 c64, 3 complex double-float
+// (float4 {re_hi, im_hi, re_lo, im_lo}; its c64 half)
+template <typename AT, int VT>
+__device__ __forceinline__ typename cplx<AT>::type restrict_load(const void* v, int64_t idx) {
+  if constexpr (VT == 0) {
+    const double2 d = reinterpret_cast<const double2*>(v)[idx];
+    return mk((AT)d.x, (AT)d.y);
+  } else if constexpr (VT == 3) {
+    const float4 d = reinterpret_cast<const float4*>(v)[idx];
+    return mk((AT)d.x, (AT)d.y);
+  } else {
+    const float2 d = reinterpret_cast<const float2*>(v)[idx];
+    return mk((AT)d.x, (AT)d.y);
+  }
+}
+
 // R^0 v with one block per coarse row (grid-stride): thread (g, q) sums the entries
 // rowptr[p] + g, + G, ... of right-hand side q (G = blockDim / nrhs groups), and the G
 // partial sums are added in group order (deterministic). A coarse row has several hundred
-// entries, so its gathers of v are spread over the whole block instead of one thread.
-template <typename T2, typename AT>
+// entries, so its gathers of v are spread over the whole block instead of one thread; each
+// thread issues the gathers of four of its entries before their products (the chain of
+// column index and gather is latency-bound otherwise), and adds the products in entry order.
+template <typename T2, typename AT, int VT>
 __global__ void __launch_bounds__(256) k_coarse_restrict_rows(int64_t nc, int nrhs, const int32_t* __restrict__ rowptr,
                                                               const int32_t* __restrict__ col,
-                                                              const AT* __restrict__ val, const void* v, int vtype,
-                                                              T2* r0) {
+                                                              const AT* __restrict__ val, const void* v, T2* r0) {
   using A2 = typename cplx<AT>::type;
+  constexpr int U = 4;
   __shared__ A2 part[256];
   const int G = blockDim.x / nrhs;
   const int q = threadIdx.x % nrhs, g = threadIdx.x / nrhs;
   for (int64_t p = blockIdx.x; p < nc; p += gridDim.x) {
     A2 acc = czero<A2>();
-    if (g < G)
-      for (int32_t e = rowptr[p] + g; e < rowptr[p + 1]; e += G) {
-        const int64_t idx = (int64_t)col[e] * nrhs + q;
-        A2 x;
-        if (vtype == 0) {
-          const double2 d = reinterpret_cast<const double2*>(v)[idx];
-          x = mk((AT)d.x, (AT)d.y);
-        } else if (vtype == 3) {
-          const float4 d = reinterpret_cast<const float4*>(v)[idx];
-          x = mk((AT)d.x, (AT)d.y);
-        } else {
-          const float2 d = reinterpret_cast<const float2*>(v)[idx];
-          x = mk((AT)d.x, (AT)d.y);
+    if (g < G) {
+      const int32_t e1 = rowptr[p + 1];
+      int32_t e = rowptr[p] + g;
+      for (; e + (U - 1) * G < e1; e += U * G) {
+        int32_t c[U];
+        AT w[U];
+        A2 x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          c[u] = col[e + u * G];
+          w[u] = val[e + u * G];
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = restrict_load<AT, VT>(v, (int64_t)c[u] * nrhs + q);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          acc.x = fma(w[u], x[u].x, acc.x);
+          acc.y = fma(w[u], x[u].y, acc.y);
+        }
+      }
+      for (; e < e1; e += G) {
+        const A2 x = restrict_load<AT, VT>(v, (int64_t)col[e] * nrhs + q);
         acc.x = fma(val[e], x.x, acc.x);
         acc.y = fma(val[e], x.y, acc.y);
       }
+    }
     if (g < G) part[g * nrhs + q] = acc;
     __syncthreads();
     if (threadIdx.x < nrhs) {
@@ -364,6 +391,18 @@ __global__ void __launch_bounds__(256) k_coarse_restrict_rows(int64_t nc, int nr
     }
     __syncthreads();
   }
+}
+
+template <typename T2, typename AT>
+static void restrict_rows(int64_t nc, int nrhs, const int32_t* rowptr, const int32_t* col, const AT* val,
+                          const void* v, int vtype, T2* r0, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::min<int64_t>(nc, 152LL * 8);
+  if (vtype == 0)
+    MX_LAUNCH(k_coarse_restrict_rows<T2, AT, 0><<<grid, 256, 0, s>>>(nc, nrhs, rowptr, col, val, v, r0));
+  else if (vtype == 3)
+    MX_LAUNCH(k_coarse_restrict_rows<T2, AT, 3><<<grid, 256, 0, s>>>(nc, nrhs, rowptr, col, val, v, r0));
+  else
+    MX_LAUNCH(k_coarse_restrict_rows<T2, AT, 1><<<grid, 256, 0, s>>>(nc, nrhs, rowptr, col, val, v, r0));
 }
 
 __global__ void k_to_f32v(int64_t n, const double* a, float* b) {
@@ -618,14 +657,10 @@ void coarse_solve(Problem& P, const void* v, int vtype, double2* yc, int nrhs) {
   float2* rin = dense ? rf + nc * nrhs : rf;
   {
     ProfScope ps(K_COARSE_RESTRICT, s, 1, rb, 4.0 * P.R0.nnz * nrhs);
-    const unsigned rows_grid = (unsigned)std::min<int64_t>(nc, 152LL * 8);
-    if (mixed) {
-      MX_LAUNCH(k_coarse_restrict_rows<float2, float><<<rows_grid, 256, 0, s>>>(
-          nc, nrhs, P.R0.rowptr.p, P.R0.col.p, r0_valf(P), v, vtype, rin));
-    } else {
-      MX_LAUNCH(k_coarse_restrict_rows<double2, double><<<rows_grid, 256, 0, s>>>(
-          nc, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, yc));
-    }
+    if (mixed)
+      restrict_rows<float2, float>(nc, nrhs, P.R0.rowptr.p, P.R0.col.p, r0_valf(P), v, vtype, rin, s);
+    else
+      restrict_rows<double2, double>(nc, nrhs, P.R0.rowptr.p, P.R0.col.p, P.R0.val.p, v, vtype, yc, s);
     MX_CHECK_LAUNCH();
   }
   if (dense && P.tune_coarse_inverse != 2 && nc % 2 == 0) {
