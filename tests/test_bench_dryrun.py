@@ -102,7 +102,7 @@ def fakes(monkeypatch):
 
     fake.mx_server_submit = submit
     fake.mx_server_poll = lambda s, t, n, nrhs: (None, [dict(converged=True)] * nrhs, dict(latency_ms=10.0 + t), 0)
-    fake.mx_server_stats = lambda s: dict(batches=3, factorisations=4, evictions=0)
+    fake.mx_server_stats = lambda s: dict(batches=3, factorisations=4, evictions=0, cached_bytes=5 << 30)
     monkeypatch.setitem(sys.modules, "paper_1711_03789_gb300", fake)
 
     empty = torch.empty
@@ -187,6 +187,7 @@ def test_serving_line_with_a_load_sweep(fakes, monkeypatch):
     assert line["config"]["loads"] == [0.5, 0.8, 1.2] and line["config"]["budget_bytes"] == 40 * 2 ** 30
     for key in ("closed_loop", "poisson_0.5x", "poisson_0.8x", "poisson_1.2x"):
         assert line[key]["converged_rhs"] == line[key]["rhs"], key
+        assert line[key]["cached_bytes_at_end"] == 5 << 30, key  # the server's cache when the run ends
     assert line["value"] == pytest.approx(line["poisson_0.8x"]["p99_ms"] / 1e3)
 
 
